@@ -1,0 +1,246 @@
+/*
+ * ORACLE -- test infrastructure, not part of the product.
+ *
+ * Plain, slow, obviously correct CPU definitions of what the CUDA path
+ * computes.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load this library.  It shares no code, header, table or
+ * constant with the CUDA path; it reads the same packed inputs (the C-ABI's
+ * text formats) and nothing else.
+ *
+ * Definitions followed (QuadRank paper, arXiv 2602.04103):
+ *   rank(q, c) = #{ i < q : t_i = c },  0 <= q <= n          (Sec. 1, rank definition)
+ *   rank(q)    = rank(q, 1) for the binary alphabet          (Sec. 1, Sec. 3)
+ *   rank_4(q)  = (rank(q,0), rank(q,1), rank(q,2), rank(q,3)) (Sec. 4, rank_4)
+ *   count(P)   = number of positions i with T[i .. i+|P|) = P, the quantity a
+ *                count-only FM-index returns (App. E); equivalently the size
+ *                of the suffix-array interval of suffixes of T$ prefixed by P.
+ * The suffix array is the textbook one: all suffixes of T$ sorted, with the
+ * sentinel $ smaller than every symbol (App. E stores one sentinel).
+ *
+ * Formats: bit text  bit i = (w[i/64] >> (i%64)) & 1;
+ *          DNA text  char i = (w[i/32] >> (2*(i%32))) & 3 (A=0,C=1,G=2,T=3);
+ *          DNA codes one byte per char.
+ *
+ * Parity pins live in tests/test_oracle_*.py.  Single-threaded on purpose.
+ */
+#define _GNU_SOURCE
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ERANGE = 4, OR_ENOMEM = 2 };
+
+/* Symbol t_i of a packed text. */
+static uint64_t text_char(const uint64_t* text, int sigma, uint64_t i) {
+    if (sigma == 2) return (text[i / 64] >> (i % 64)) & 1;
+    return (text[i / 32] >> (2 * (i % 32))) & 3;
+}
+
+uint64_t or_char(const uint64_t* text, int sigma, uint64_t i) { return text_char(text, sigma, i); }
+
+/* rank(q, c) by the definition: a loop over t_0 .. t_{q-1}. */
+int or_rank_naive(const uint64_t* text, uint64_t n, int sigma, uint64_t q, int c, uint64_t* out) {
+    if ((sigma != 2 && sigma != 4) || c < 0 || c >= sigma) return OR_EINVAL;
+    if (q > n) return OR_ERANGE;
+    uint64_t r = 0;
+    for (uint64_t i = 0; i < q; i++) r += text_char(text, sigma, i) == (uint64_t)c;
+    *out = r;
+    return OR_OK;
+}
+
+typedef struct { uint64_t q, idx; } qpair;
+
+static int cmp_qpair(const void* a, const void* b) {
+    const qpair* x = (const qpair*)a;
+    const qpair* y = (const qpair*)b;
+    if (x->q != y->q) return x->q < y->q ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/*
+ * Many queries by one sweep: sort the queries by position, then walk the text
+ * once from position 0, keeping the number of occurrences of every symbol in
+ * t_0 .. t_{pos-1}; each query is answered when pos reaches it.
+ *
+ * mode 0: out[k] = rank(q[k], c)              (scalar c; c_arr == NULL)
+ * mode 1: out[k] = rank(q[k], c_arr[k])
+ * mode 2: out[4k + c] = rank(q[k], c), c = 0..sigma-1   (rank_4 for sigma = 4)
+ * Queries with q > n get UINT64_MAX and the call returns OR_ERANGE.
+ */
+int or_rank_sweep(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q, uint64_t m,
+                  int mode, int c, const uint8_t* c_arr, uint64_t* out) {
+    if (sigma != 2 && sigma != 4) return OR_EINVAL;
+    if (mode == 0 && (c < 0 || c >= sigma)) return OR_EINVAL;
+    if (mode == 2 && sigma != 4) return OR_EINVAL;
+    qpair* ord = (qpair*)malloc((m ? m : 1) * sizeof(qpair));
+    if (!ord) return OR_ENOMEM;
+    for (uint64_t k = 0; k < m; k++) { ord[k].q = q[k]; ord[k].idx = k; }
+    qsort(ord, m, sizeof(qpair), cmp_qpair);
+    int rc = OR_OK;
+    uint64_t pos = 0, cnt[4] = {0, 0, 0, 0};
+    for (uint64_t k = 0; k < m; k++) {
+        uint64_t target = ord[k].q, idx = ord[k].idx;
+        if (target > n) {
+            rc = OR_ERANGE;
+            if (mode == 2) { for (int s = 0; s < 4; s++) out[4 * idx + s] = UINT64_MAX; }
+            else out[idx] = UINT64_MAX;
+            continue;
+        }
+        while (pos < target) {
+            if (sigma == 2 && pos % 64 == 0 && pos + 64 <= target) {
+                /* 64 whole bits at once: the number of ones is their popcount */
+                uint64_t ones = (uint64_t)__builtin_popcountll(text[pos / 64]);
+                cnt[1] += ones;
+                cnt[0] += 64 - ones;
+                pos += 64;
+            } else {
+                cnt[text_char(text, sigma, pos)]++;
+                pos++;
+            }
+        }
+        if (mode == 0) out[idx] = cnt[c];
+        else if (mode == 1) {
+            int cc = c_arr[idx];
+            if (cc >= sigma) { out[idx] = UINT64_MAX; rc = OR_EINVAL; }
+            else out[idx] = cnt[cc];
+        } else {
+            for (int s = 0; s < 4; s++) out[4 * idx + s] = cnt[s];
+        }
+    }
+    free(ord);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* FM side: suffix array, BWT and occurrence counts by definition      */
+/* ------------------------------------------------------------------ */
+
+/* Compare suffixes i and j of T$ ($ = end of text, smaller than any symbol). */
+static int cmp_suffix(const uint8_t* t, uint64_t n, uint64_t i, uint64_t j) {
+    if (i == j) return 0;
+    while (i < n && j < n) {
+        if (t[i] != t[j]) return t[i] < t[j] ? -1 : 1;
+        i++; j++;
+    }
+    /* one of them reached $: the one that ended is smaller */
+    if (i == n) return -1;
+    return 1;
+}
+
+typedef struct { const uint8_t* t; uint64_t n; } sa_ctx;
+
+static int cmp_sa(const void* a, const void* b, void* arg) {
+    const sa_ctx* c = (const sa_ctx*)arg;
+    uint64_t i = *(const uint64_t*)a, j = *(const uint64_t*)b;
+    return cmp_suffix(c->t, c->n, i, j);
+}
+
+/* sa[0 .. n] = the suffixes of T$ in lexicographic order (a comparison sort). */
+int or_suffix_array(const uint8_t* codes, uint64_t n, uint64_t* sa) {
+    for (uint64_t i = 0; i <= n; i++) sa[i] = i;
+    sa_ctx c = {codes, n};
+    qsort_r(sa, n + 1, sizeof(uint64_t), cmp_sa, &c);
+    return OR_OK;
+}
+
+/* BWT of T$: bwt[k] = T[sa[k] - 1], and the row whose suffix is the whole text
+ * holds $ -- reported as *dollar_row, with bwt[dollar_row] = 255. */
+int or_bwt(const uint8_t* codes, uint64_t n, const uint64_t* sa, uint8_t* bwt, uint64_t* dollar_row) {
+    for (uint64_t k = 0; k <= n; k++) {
+        if (sa[k] == 0) { bwt[k] = 255; *dollar_row = k; }
+        else bwt[k] = codes[sa[k] - 1];
+    }
+    return OR_OK;
+}
+
+/* Compare the first len chars of suffix s of T$ with pattern p:
+ * < 0 if the suffix sorts before every string starting with p,
+ * = 0 if the suffix starts with p, > 0 if it sorts after. */
+static int cmp_prefix(const uint8_t* t, uint64_t n, uint64_t s, const uint8_t* p, uint64_t len) {
+    for (uint64_t k = 0; k < len; k++) {
+        if (s + k >= n) return -1;               /* reached $ first */
+        if (t[s + k] != p[k]) return t[s + k] < p[k] ? -1 : 1;
+    }
+    return 0;
+}
+
+/* [lo, hi) = the rows of the suffix array whose suffixes start with p. */
+int or_sa_interval(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint8_t* p, uint64_t len,
+                   uint64_t* lo, uint64_t* hi) {
+    uint64_t a = 0, b = n + 1;             /* first row with suffix >= p */
+    while (a < b) {
+        uint64_t mid = a + (b - a) / 2;
+        if (cmp_prefix(codes, n, sa[mid], p, len) < 0) a = mid + 1; else b = mid;
+    }
+    uint64_t l = a;
+    b = n + 1;                             /* first row with suffix > every extension of p */
+    while (a < b) {
+        uint64_t mid = a + (b - a) / 2;
+        if (cmp_prefix(codes, n, sa[mid], p, len) <= 0) a = mid + 1; else b = mid;
+    }
+    *lo = l;
+    *hi = a;
+    return OR_OK;
+}
+
+/* count(P) by direct comparison at every start position (the empty pattern
+ * occurs at each of the n + 1 positions 0..n). */
+uint64_t or_count_brute(const uint8_t* codes, uint64_t n, const uint8_t* p, uint64_t len) {
+    if (len == 0) return n + 1;
+    if (len > n) return 0;
+    uint64_t cnt = 0;
+    for (uint64_t i = 0; i + len <= n; i++)
+        if (codes[i] == p[0] && memcmp(codes + i, p, len) == 0) cnt++;
+    return cnt;
+}
+
+/* count for m patterns (offsets[m+1]) via the suffix-array interval. */
+int or_count_sa(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint8_t* pats,
+                const uint64_t* offsets, uint64_t m, uint64_t* out) {
+    for (uint64_t k = 0; k < m; k++) {
+        uint64_t lo, hi;
+        or_sa_interval(codes, n, sa, pats + offsets[k], offsets[k + 1] - offsets[k], &lo, &hi);
+        out[k] = hi - lo;
+    }
+    return OR_OK;
+}
+
+/* count for m patterns by brute force. */
+int or_count_brute_batch(const uint8_t* codes, uint64_t n, const uint8_t* pats, const uint64_t* offsets,
+                         uint64_t m, uint64_t* out) {
+    for (uint64_t k = 0; k < m; k++)
+        out[k] = or_count_brute(codes, n, pats + offsets[k], offsets[k + 1] - offsets[k]);
+    return OR_OK;
+}
+
+/*
+ * Work of the count-only backward search with a k-character prefix table
+ * (App. E): the table gives the interval of the last k pattern characters
+ * without any rank query, then one LF step (two rank queries) is taken per
+ * remaining character while the interval is non-empty.  A pattern shorter than
+ * k starts from the full interval and steps through all its characters.
+ * steps[j] = LF steps of pattern j; returns the total.
+ */
+uint64_t or_fm_steps(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint8_t* pats,
+                     const uint64_t* offsets, uint64_t m, uint64_t k, uint64_t* steps) {
+    uint64_t total = 0;
+    for (uint64_t j = 0; j < m; j++) {
+        const uint8_t* p = pats + offsets[j];
+        uint64_t len = offsets[j + 1] - offsets[j];
+        /* longest suffix of p (length t) that occurs in T: intervals only shrink as t grows */
+        uint64_t longest = 0;
+        for (uint64_t t = 1; t <= len; t++) {
+            uint64_t lo, hi;
+            or_sa_interval(codes, n, sa, p + (len - t), t, &lo, &hi);
+            if (hi > lo) longest = t; else break;
+        }
+        /* steps t = 1..len run while the interval before step t is non-empty */
+        uint64_t run = longest + 1 < len ? longest + 1 : len;
+        uint64_t s;
+        if (len >= k) s = longest >= k ? run - k : 0;
+        else s = run;
+        if (steps) steps[j] = s;
+        total += s;
+    }
+    return total;
+}

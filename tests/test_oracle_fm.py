@@ -1,0 +1,156 @@
+"""Pins for the FM-side oracle: suffix array, BWT, SA interval counts,
+brute-force counts and the LF-step count.
+
+Ties: a hand-worked fixture (GATTACA), Python's own sort of suffix strings,
+``re`` overlapping-match counts, closed forms on A^n and (ACGT)^r, and the
+extension invariant sum_c count(cP) = count(P) - [T starts with P]
+(QuadRank paper, App. E: count-only FM-index with one sentinel).
+"""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_04103_gb300 import synth
+
+DNA = "ACGT"
+
+
+def enc(s: str) -> np.ndarray:
+    return np.array([DNA.index(ch) for ch in s], dtype=np.uint8)
+
+
+def dec(a) -> str:
+    return "".join(DNA[int(x)] for x in a)
+
+
+def test_golden_gattaca(golden):
+    g = golden("fm_gattaca.txt")
+    t = enc(g["text"])
+    sa = oracle.suffix_array(t)
+    assert sa.tolist() == [int(x) for x in g["sa"].split()]
+    bwt, row = oracle.bwt(t, sa)
+    assert row == int(g["dollar_row"])
+    assert "".join("$" if b == 255 else DNA[b] for b in bwt) == g["bwt"]
+    for line in g["pattern"]:
+        p, cnt, lo, hi = line.split()
+        assert oracle.sa_interval(t, sa, enc(p)) == (int(lo), int(hi))
+        assert oracle.count_brute(t, enc(p)) == int(cnt)
+
+
+@pytest.mark.parametrize("seed,n", [(1, 50), (2, 200), (3, 777)])
+def test_sa_matches_python_sort(seed, n):
+    rng = np.random.default_rng(seed)
+    alpha = 2 if seed == 1 else 4            # a 2-letter text has long repeats
+    t = rng.integers(0, alpha, n).astype(np.uint8)
+    s = dec(t) + "$"                         # '$' < 'A' < 'C' < 'G' < 'T' in ASCII
+    want = sorted(range(n + 1), key=lambda i: s[i:])
+    assert oracle.suffix_array(t).tolist() == want
+
+
+def re_count(text: str, p: str) -> int:
+    return len(re.findall("(?=" + p + ")", text))
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_counts_match_regex(seed):
+    rng = np.random.default_rng(seed)
+    n = 3000
+    t = rng.integers(0, 4, n).astype(np.uint8)
+    s = dec(t)
+    sa = oracle.suffix_array(t)
+    for length in [1, 2, 3, 5, 8, 12]:
+        for _ in range(20):
+            if rng.random() < 0.5:
+                st = int(rng.integers(0, n - length + 1))
+                p = t[st:st + length]
+            else:
+                p = rng.integers(0, 4, length).astype(np.uint8)
+            want = re_count(s, dec(p))
+            assert oracle.count_brute(t, p) == want
+            lo, hi = oracle.sa_interval(t, sa, p)
+            assert hi - lo == want
+
+
+def test_closed_forms():
+    n = 300
+    a = np.zeros(n, dtype=np.uint8)                      # A^n
+    sa = oracle.suffix_array(a)
+    assert sa.tolist() == list(range(n, -1, -1))         # shorter runs of A sort first
+    for k in [0, 1, 7, 8, 150, 300, 301]:
+        want = n - k + 1 if k <= n else 0
+        assert oracle.count_brute(a, np.zeros(k, np.uint8)) == want
+        lo, hi = oracle.sa_interval(a, sa, np.zeros(k, np.uint8))
+        assert hi - lo == want
+    r = 100
+    per = np.tile(np.arange(4, dtype=np.uint8), r)      # (ACGT)^r
+    sa = oracle.suffix_array(per)
+    for p, want in [("ACGT", r), ("CG", r), ("GTA", r - 1), ("TA", r - 1), ("AA", 0), ("ACGTACGT", r - 1)]:
+        lo, hi = oracle.sa_interval(per, sa, enc(p))
+        assert hi - lo == want
+        assert oracle.count_brute(per, enc(p)) == want
+
+
+def test_extension_invariant():
+    rng = np.random.default_rng(9)
+    t = synth.fm_text(77, 4000, repeat_cover=0.3, len_min=50, len_max=200, sub_rate=0.02)
+    sa = oracle.suffix_array(t)
+    for _ in range(200):
+        L = int(rng.integers(0, 10))
+        st = int(rng.integers(0, t.size - L))
+        p = t[st:st + L]
+        cp = oracle.sa_interval(t, sa, p)
+        total = 0
+        for c in range(4):
+            lo, hi = oracle.sa_interval(t, sa, np.concatenate([[c], p]).astype(np.uint8))
+            total += hi - lo
+        starts = int(L <= t.size and np.array_equal(t[:L], p))
+        assert total == (cp[1] - cp[0]) - starts
+
+
+def test_bwt_definition_and_symbol_counts():
+    t = synth.fm_text(3, 2000, repeat_cover=0.2, len_min=100, len_max=300, sub_rate=0.02)
+    sa = oracle.suffix_array(t)
+    bwt, row = oracle.bwt(t, sa)
+    assert sa[row] == 0 and bwt[row] == 255
+    # the BWT is a permutation of T$: same symbol multiset
+    for c in range(4):
+        assert int((bwt == c).sum()) == int((t == c).sum())
+    # the row after the last suffix: LF of the $ row maps to row 0 ($ suffix)
+    assert sa[0] == t.size
+
+
+def test_batch_counts_and_steps():
+    t = synth.fm_text(5, 5000, repeat_cover=0.2, len_min=300, len_max=1000, sub_rate=0.02)
+    sa = oracle.suffix_array(t)
+    pats, off = synth.patterns(6, t, 300, 1, 40, sub_rate=0.01)
+    a = oracle.count_sa(t, sa, pats, off)
+    b = oracle.count_brute_batch(t, pats, off)
+    assert np.array_equal(a, b)
+    s = dec(t)
+    for j in range(0, 300, 37):
+        p = dec(pats[off[j]:off[j + 1]])
+        assert int(a[j]) == re_count(s, p)
+    # LF steps: re-run the loop of a table-then-backward search by brute force
+    total, steps = oracle.fm_steps(t, sa, pats, off, k=8)
+    assert total == int(steps.sum())
+    for j in range(300):
+        p = pats[off[j]:off[j + 1]]
+        L = p.size
+        if L >= 8:
+            nonempty = oracle.count_brute(t, p[L - 8:]) > 0
+            s_ = 0
+            for i in range(L - 9, -1, -1):
+                if not nonempty:
+                    break
+                s_ += 1
+                nonempty = oracle.count_brute(t, p[i:]) > 0
+        else:
+            nonempty, s_ = True, 0
+            for i in range(L - 1, -1, -1):
+                if not nonempty:
+                    break
+                s_ += 1
+                nonempty = oracle.count_brute(t, p[i:]) > 0
+        assert int(steps[j]) == s_, j

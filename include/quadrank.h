@@ -1,0 +1,198 @@
+/*
+ * quadrank.h -- C ABI of libquadrank.so: batched rank queries over BiRank
+ * (binary alphabet) and QuadRank (2-bit DNA alphabet) in the cache-line
+ * interleaved, delta-to-the-middle layout, and the QuadFm count-only
+ * backward search built on QuadRank, on one NVIDIA GB300 (sm_103a).
+ *
+ * Source of the operations: R. Groot Koerkamp, "QuadRank: Engineering a High
+ * Throughput Rank", arXiv 2602.04103 (cited below as "the paper").
+ *
+ * Conventions shared by every entry point
+ *   - Return value: QR_OK (0) or one of the QR_E* codes below; the message of
+ *     the last failure on the calling host thread is qr_last_error().
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Query calls only enqueue work on it and return; their device
+ *     buffers must stay valid until the stream reaches that point.
+ *   - "device pointer" arguments are caller-owned CUDA device (or managed)
+ *     memory; the library never frees them.  Index memory allocated by a
+ *     *_build call is owned by the returned handle and released by *_free.
+ *   - Errors found on the device while a query runs (a position q > n, a
+ *     pattern byte > 3) do not fail the call: they write the documented
+ *     sentinel output and set a bit in the handle's device status word,
+ *     which qr_status / qfm_status read (synchronising) and clear.
+ *   - A handle may be used from one host thread at a time; concurrent query
+ *     calls on different streams with the same handle are allowed.
+ *
+ * Text formats
+ *   bit text (sigma = 2): bit i = (text[i / 64] >> (i % 64)) & 1.
+ *   DNA text (sigma = 4): char i = (text[i / 32] >> (2 * (i % 32))) & 3 with
+ *                         A = 0, C = 1, G = 2, T = 3.
+ *   DNA codes           : one byte per char, values 0..3.
+ *   Bits / chars at positions >= n inside the last word are ignored.
+ */
+#ifndef QUADRANK_H
+#define QUADRANK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QR_OK 0
+#define QR_EINVAL 1    /* bad argument (size, sigma, symbol, null pointer)        */
+#define QR_ENOMEM 2    /* a device or pinned-host allocation failed              */
+#define QR_ECUDA 3     /* a CUDA runtime call failed (message in qr_last_error)  */
+#define QR_ERANGE 4    /* status bit: some query had q > n                        */
+#define QR_ETIMEOUT 16 /* status bit: a bounded device wait gave up               */
+#define QR_EBADSYM 8   /* status bit: some pattern byte was > 3                   */
+
+#define QR_LAYOUT_PAPER 0   /* BiRank16 / QuadRank16 exactly as in the paper      */
+
+typedef struct qr_index qr_index;
+
+/* Sizes of a built rank index. */
+typedef struct {
+    uint64_t n;             /* text length (bits or chars)                           */
+    int32_t sigma;          /* 2 or 4                                                */
+    int32_t layout;         /* QR_LAYOUT_*                                           */
+    uint64_t block_chars;   /* B = 496 (sigma 2) or B4 = 224 (sigma 4)               */
+    uint64_t super_blocks;  /* blocks per superblock: 128 (sigma 2) or 256 (sigma 4) */
+    uint64_t nblocks;       /* floor(n / B) + 1 cache lines of 64 bytes              */
+    uint64_t nsuper;        /* ceil(nblocks / super_blocks) superblock entries        */
+    uint64_t bytes_blocks;  /* 64 * nblocks                                          */
+    uint64_t bytes_super;   /* 4 * nsuper (sigma 2) or 16 * nsuper (sigma 4)          */
+} qr_info_t;
+
+/* Per-handle launch tuning of the rank kernels (chosen by the autotuner). */
+typedef struct {
+    int32_t queries_per_thread;  /* independent queries in flight per thread: 1,2,4,8 */
+    int32_t block_threads;       /* 64..512, multiple of 32                            */
+    int32_t load_mode;           /* 0: whole 64-byte line; 1: only the 32-byte sectors  */
+                                 /*    the query needs                                  */
+    int32_t grid_blocks;         /* 0: SM count x resident blocks per SM                */
+} qr_tuning_t;
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* qr_last_error(void);
+
+/* ABI version of this header (bumped on any signature change). */
+int qr_abi_version(void);
+
+/*
+ * qr_build -- build the rank index of a packed text.
+ * Paper: Sec. 3 (BiRank16: 16-bit delta b_j inlined in each 64-byte line,
+ * B = 496 data bits per block, S = 128 B, shifted 32-bit superblock offsets
+ * s_i = floor(rank(iS) / 2^11), b_j = rank(jB + 240) - 2^11 s_{j/128}; parallel
+ * construction: per-superblock counts, a prefix sum, then independent
+ * superblocks) and Sec. 4 (QuadRank16: four 16-bit deltas b_{j,c} to the
+ * middle of each block, B4 = 224 chars, S4 = 256 B4, s_{i,c} =
+ * floor(rank(iS4, c) / 2^13), transposed negated low/high bit words).
+ *   text           packed text (format above), ceil(n/64) (sigma 2) or ceil(n/32)
+ *                  (sigma 4) uint64 words; host memory if text_on_device == 0,
+ *                  device memory otherwise.  Only read during the call.
+ *   n              text length; n < 2^43 (sigma 2) or n < 2^45 (sigma 4).
+ *   sigma          2 or 4.
+ *   stream         stream the build runs on; the call returns after the build
+ *                  has completed (it synchronises the stream).
+ *   out            receives the handle (owner: caller, release with qr_free).
+ * Errors: QR_EINVAL (sigma, n out of range, null pointers), QR_ENOMEM, QR_ECUDA.
+ */
+int qr_build(const uint64_t* text, uint64_t n, int sigma, int text_on_device, void* stream, qr_index** out);
+
+/* qr_build with an explicit layout (QR_LAYOUT_*). */
+int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device, int layout, void* stream,
+                qr_index** out);
+
+/*
+ * qr_rank -- out[k] = rank(q[k], c) for k < m, one symbol c for all queries.
+ * Paper: Sec. 1 (definition rank(q, c) = #{i < q : t_i = c}, 0 <= q <= n),
+ * Sec. 3 Eq. (1) (BiRank: 2^11 s_{i_q} + b_{j_q} plus or minus the popcount of
+ * at most 256 bits between q and the block middle), Sec. 4 "rank1" and the
+ * App. A listing (QuadRank: 2^13 s_{i,c} + b_{j,c} plus or minus at most 128
+ * chars matched as (lo ^ cl) & (hi ^ ch)).  For sigma 2, c = 1 is rank(q) and
+ * c = 0 is q - rank(q).
+ *   q, out  device pointers to m uint64 values each (may not overlap).
+ *   c       0..sigma-1.
+ * A query with q > n yields out[k] = UINT64_MAX and sets QR_ERANGE in the status.
+ * Errors (returned): QR_EINVAL (null index/pointers with m > 0, c out of range),
+ * QR_ECUDA (launch failure).  m = 0 is a no-op.
+ */
+int qr_rank(const qr_index* idx, const uint64_t* q, uint64_t m, int c, uint64_t* out, void* stream);
+
+/*
+ * qr_rank_c -- out[k] = rank(q[k], c[k]): one symbol per query.
+ * Paper: as qr_rank.  c is a device array of m bytes, each in 0..sigma-1; a
+ * byte >= sigma yields UINT64_MAX and sets QR_EBADSYM in the status.
+ */
+int qr_rank_c(const qr_index* idx, const uint64_t* q, const uint8_t* c, uint64_t m, uint64_t* out, void* stream);
+
+/*
+ * qr_rank4 -- out4[4k + c] = rank(q[k], c) for c = 0..3 (sigma 4 only).
+ * Paper: Sec. 4 "4-way popcount" (rank_4: all four counts of one line; the
+ * sign of (q mod B) - 96 decides add or subtract).
+ *   out4  device pointer to 4 m uint64 values, row-major (query-major).
+ * q > n yields four UINT64_MAX and QR_ERANGE.  Errors: QR_EINVAL (sigma != 4).
+ */
+int qr_rank4(const qr_index* idx, const uint64_t* q, uint64_t m, uint64_t* out4, void* stream);
+
+/*
+ * qr_rank_host / qr_rank4_host -- the same queries with HOST buffers: the
+ * call streams q to the device in chunks, runs the kernel and copies the
+ * results back, overlapping the three on internal streams, and returns when
+ * out (or out4) holds every result.  q and out should be pinned (page-locked)
+ * host memory for full copy bandwidth; pageable memory works but is slower.
+ * c < 0 means per-query symbols in c_host (m bytes); otherwise c is the symbol.
+ * Device staging buffers are allocated on first use and kept by the handle.
+ * Errors: as qr_rank, plus QR_ENOMEM for the staging buffers.
+ */
+int qr_rank_host(qr_index* idx, const uint64_t* q_host, const uint8_t* c_host, uint64_t m, int c,
+                 uint64_t* out_host, void* stream);
+int qr_rank4_host(qr_index* idx, const uint64_t* q_host, uint64_t m, uint64_t* out4_host, void* stream);
+
+/* Sizes of the index.  Errors: QR_EINVAL on null arguments. */
+int qr_info(const qr_index* idx, qr_info_t* info);
+
+/* Device pointers of the 64-byte lines and of the superblock array (for
+ * inspection of the layout; owned by the handle). */
+int qr_layout_ptrs(const qr_index* idx, const void** lines, const void** supers);
+
+/* Copy the layout out for inspection: lines_dst receives bytes_blocks bytes,
+ * supers_dst bytes_super bytes (either may be NULL; host or device memory).
+ * Synchronises stream.  Errors: QR_EINVAL, QR_ECUDA. */
+int qr_copy_layout(const qr_index* idx, void* lines_dst, void* supers_dst, void* stream);
+
+/* Read the launch tuning / set it (values are validated; QR_EINVAL if not). */
+int qr_get_tuning(const qr_index* idx, qr_tuning_t* t);
+int qr_set_tuning(qr_index* idx, const qr_tuning_t* t);
+
+/* Synchronise stream, return the OR of the status bits (QR_ERANGE, QR_EBADSYM,
+ * QR_ETIMEOUT; each >= 4) set by queries since the last call, and clear them;
+ * 0 when all were valid.  A failure of the call itself returns QR_EINVAL or
+ * QR_ECUDA (both < 4). */
+int qr_status(qr_index* idx, void* stream);
+
+/* Release the index (waits for the device to finish using it). NULL is a no-op. */
+int qr_free(qr_index* idx);
+
+/*
+ * qr_probe_gather -- measurement aid: out[k] = XOR of the `bytes`-byte record
+ * at a random record index of buf for m draws, one 16-byte vector load at a
+ * time, with the same threads-and-loads-in-flight scheme as the rank kernels.
+ * It gives the random-access ceiling of this GPU's memory for records of 32,
+ * 64 or 128 bytes, the GPU counterpart of the paper's measured random-access
+ * limit of RAM (Sec. 5.1, "Lower bounds": 2.5 ns per cache line in total).
+ *   buf    device buffer of nrec * bytes bytes, 16-byte aligned.
+ *   seed   splitmix64 seed of the record indices (uniform in [0, nrec)).
+ *   out    device array of m uint64 (one digest per draw, defeats dead-code
+ *          elimination).
+ * Errors: QR_EINVAL (bytes not 16/32/64/128, nrec = 0, no kernel for
+ * (bytes, queries_per_thread) -- 128-byte records allow at most 4 in flight).
+ */
+int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out,
+                    int queries_per_thread, int block_threads, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QUADRANK_H */

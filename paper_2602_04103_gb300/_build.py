@@ -78,7 +78,8 @@ def build_cuda(force: bool = False, verbose_ptxas: bool = False) -> Path:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(cu) + len(cpp), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, cu + cpp))
-    _run([nvcc, *ARCH, "-shared", "-o", str(QR_SO), *map(str, objs), "-lcudart", "-lpthread"])
+    # static CUDA runtime: the library loads (and reports a clean error) on hosts without a driver
+    _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", str(QR_SO), *map(str, objs), "-lpthread"])
     return QR_SO
 
 

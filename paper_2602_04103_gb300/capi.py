@@ -1,0 +1,188 @@
+"""ctypes binding of libquadrank.so (include/quadrank.h), same entry-point names.
+
+Argument marshalling only: every step of the query path runs in the CUDA
+kernels of the library.  Device buffers are torch CUDA tensors (any 8-byte
+integer dtype for uint64 data, uint8 for symbols / patterns); host buffers
+are numpy arrays or CPU tensors (pinned for full copy bandwidth).  Importing
+this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+_SO = Path(__file__).resolve().parent / "_lib" / "libquadrank.so"
+if not _SO.exists():
+    raise ImportError(f"{_SO} is missing: build it with __graft_entry__.build() "
+                      "(nvcc, sm_103a); there is no fallback path")
+lib = C.CDLL(str(_SO))
+
+QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA = 0, 1, 2, 3
+QR_ERANGE, QR_EBADSYM, QR_ETIMEOUT = 4, 8, 16
+QR_LAYOUT_PAPER = 0
+QFM_KEEP_SA = 1
+
+u64, i32, vp = C.c_uint64, C.c_int, C.c_void_p
+
+
+class qr_info_t(C.Structure):
+    _fields_ = [("n", u64), ("sigma", C.c_int32), ("layout", C.c_int32), ("block_chars", u64),
+                ("super_blocks", u64), ("nblocks", u64), ("nsuper", u64), ("bytes_blocks", u64),
+                ("bytes_super", u64)]
+
+
+class qr_tuning_t(C.Structure):
+    _fields_ = [("queries_per_thread", C.c_int32), ("block_threads", C.c_int32), ("load_mode", C.c_int32),
+                ("grid_blocks", C.c_int32)]
+
+
+class QRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib.qr_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with code {code}: {msg}")
+        self.code = code
+
+
+def _sig(name, args, res=i32):
+    f = getattr(lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("qr_last_error", [], C.c_char_p)
+_sig("qr_abi_version", [])
+_sig("qr_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
+_sig("qr_build_ex", [vp, u64, i32, i32, i32, vp, C.POINTER(vp)])
+_sig("qr_rank", [vp, vp, u64, i32, vp, vp])
+_sig("qr_rank_c", [vp, vp, vp, u64, vp, vp])
+_sig("qr_rank4", [vp, vp, u64, vp, vp])
+_sig("qr_rank_host", [vp, vp, vp, u64, i32, vp, vp])
+_sig("qr_rank4_host", [vp, vp, u64, vp, vp])
+_sig("qr_info", [vp, C.POINTER(qr_info_t)])
+_sig("qr_layout_ptrs", [vp, C.POINTER(vp), C.POINTER(vp)])
+_sig("qr_copy_layout", [vp, vp, vp, vp])
+_sig("qr_get_tuning", [vp, C.POINTER(qr_tuning_t)])
+_sig("qr_set_tuning", [vp, C.POINTER(qr_tuning_t)])
+_sig("qr_status", [vp, vp])
+_sig("qr_free", [vp])
+_sig("qr_probe_gather", [vp, u64, i32, u64, u64, vp, i32, i32, vp])
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != QR_OK:
+        raise QRError(rc, where)
+
+
+def ptr(x) -> int | None:
+    """Address of a torch tensor / numpy array (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def stream_ptr(stream=None) -> int | None:
+    """cudaStream_t of a torch stream (default: torch's current stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def numel(x) -> int:
+    return x.numel() if hasattr(x, "numel") else x.size
+
+
+class QRIndex:
+    """Owner of a qr_index* (freed with qr_free)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def free(self) -> None:
+        if self.handle:
+            lib.qr_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return vp(self.handle)
+
+
+def qr_build(text, n: int, sigma: int, stream=None, layout: int = QR_LAYOUT_PAPER) -> QRIndex:
+    on_dev = int(hasattr(text, "is_cuda") and text.is_cuda)
+    h = vp()
+    _check(lib.qr_build_ex(ptr(text), n, sigma, on_dev, layout, stream_ptr(stream), C.byref(h)), "qr_build")
+    return QRIndex(h.value)
+
+
+def qr_rank(idx: QRIndex, q, c: int, out, stream=None) -> None:
+    _check(lib.qr_rank(idx, ptr(q), numel(q), c, ptr(out), stream_ptr(stream)), "qr_rank")
+
+
+def qr_rank_c(idx: QRIndex, q, c, out, stream=None) -> None:
+    _check(lib.qr_rank_c(idx, ptr(q), ptr(c), numel(q), ptr(out), stream_ptr(stream)), "qr_rank_c")
+
+
+def qr_rank4(idx: QRIndex, q, out4, stream=None) -> None:
+    _check(lib.qr_rank4(idx, ptr(q), numel(q), ptr(out4), stream_ptr(stream)), "qr_rank4")
+
+
+def qr_rank_host(idx: QRIndex, q_host, c, out_host, stream=None) -> None:
+    """c: an int symbol, or a host uint8 array of per-query symbols."""
+    if isinstance(c, int):
+        rc = lib.qr_rank_host(idx, ptr(q_host), None, numel(q_host), c, ptr(out_host), stream_ptr(stream))
+    else:
+        rc = lib.qr_rank_host(idx, ptr(q_host), ptr(c), numel(q_host), -1, ptr(out_host), stream_ptr(stream))
+    _check(rc, "qr_rank_host")
+
+
+def qr_rank4_host(idx: QRIndex, q_host, out4_host, stream=None) -> None:
+    _check(lib.qr_rank4_host(idx, ptr(q_host), numel(q_host), ptr(out4_host), stream_ptr(stream)), "qr_rank4_host")
+
+
+def qr_info(idx: QRIndex) -> dict:
+    info = qr_info_t()
+    _check(lib.qr_info(idx, C.byref(info)), "qr_info")
+    return {k: getattr(info, k) for k, _ in qr_info_t._fields_}
+
+
+def qr_layout_ptrs(idx: QRIndex) -> tuple[int, int]:
+    a, b = vp(), vp()
+    _check(lib.qr_layout_ptrs(idx, C.byref(a), C.byref(b)), "qr_layout_ptrs")
+    return a.value, b.value
+
+
+def qr_copy_layout(idx: QRIndex, lines_dst=None, supers_dst=None, stream=None) -> None:
+    _check(lib.qr_copy_layout(idx, ptr(lines_dst), ptr(supers_dst), stream_ptr(stream)), "qr_copy_layout")
+
+
+def qr_get_tuning(idx: QRIndex) -> dict:
+    t = qr_tuning_t()
+    _check(lib.qr_get_tuning(idx, C.byref(t)), "qr_get_tuning")
+    return {k: getattr(t, k) for k, _ in qr_tuning_t._fields_}
+
+
+def qr_set_tuning(idx: QRIndex, queries_per_thread=4, block_threads=256, load_mode=0, grid_blocks=0) -> None:
+    t = qr_tuning_t(queries_per_thread, block_threads, load_mode, grid_blocks)
+    _check(lib.qr_set_tuning(idx, C.byref(t)), "qr_set_tuning")
+
+
+def qr_status(idx: QRIndex, stream=None) -> int:
+    rc = lib.qr_status(idx, stream_ptr(stream))
+    if rc in (QR_EINVAL, QR_ECUDA, QR_ENOMEM):
+        raise QRError(rc, "qr_status")
+    return rc
+
+
+def qr_probe_gather(buf, nrec: int, nbytes: int, m: int, seed: int, out, queries_per_thread=4,
+                    block_threads=256, stream=None) -> None:
+    _check(lib.qr_probe_gather(ptr(buf), nrec, nbytes, m, seed, ptr(out), queries_per_thread, block_threads,
+                               stream_ptr(stream)), "qr_probe_gather")

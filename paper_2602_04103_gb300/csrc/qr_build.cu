@@ -1,0 +1,281 @@
+// Layout builder of BiRank16 and QuadRank16 (paper Sec. 3 "Parallel
+// construction" and Sec. 4): one warp per superblock counts its blocks, an
+// exclusive scan turns superblock counts into absolute ranks, and a second
+// pass writes every 64-byte line (deltas to the block middle + data) and the
+// shifted superblock offsets.
+#include <cuda_runtime.h>
+
+#include "qr_common.cuh"
+#include "qr_scan.cuh"
+
+namespace qr {
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+// 64 bits of a packed bit stream starting at bit o; bits >= nbits are 0 and
+// no word at or beyond ceil(nbits / 64) is read.
+__device__ __forceinline__ uint64_t bits64(const uint64_t* __restrict__ t, uint64_t nbits, uint64_t o) {
+    if (o >= nbits) return 0;
+    const uint64_t w = o >> 6;
+    const uint32_t sh = (uint32_t)(o & 63);
+    const uint64_t nwords = (nbits + 63) >> 6;
+    uint64_t v = t[w] >> sh;
+    if (sh != 0 && w + 1 < nwords) v |= t[w + 1] << (64 - sh);
+    const uint64_t left = nbits - o;
+    if (left < 64) v &= low_mask((uint32_t)left);
+    return v;
+}
+
+// ---------------------------------------------------------------- sigma = 2
+// The 8 words of line j (b_j not yet inserted: word 0 holds data bits
+// [jB, jB + 48) in bits 16..63) and the counts of the whole block and of its
+// first 240 bits.
+struct Line2 {
+    uint64_t w[8];
+    uint32_t cnt, half;
+};
+
+__device__ __forceinline__ Line2 make_line2(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    Line2 L;
+    const uint64_t base = j * kB2;
+    L.w[0] = bits64(t, n, base) << 16;
+#pragma unroll
+    for (int k = 1; k < 8; k++) L.w[k] = bits64(t, n, base + 64 * k - 16);
+    uint32_t h = popc64(L.w[0]) + popc64(L.w[1]) + popc64(L.w[2]) + popc64(L.w[3]);
+    L.half = h;
+    L.cnt = h + popc64(L.w[4]) + popc64(L.w[5]) + popc64(L.w[6]) + popc64(L.w[7]);
+    return L;
+}
+
+__global__ void count2_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                              uint64_t* __restrict__ super_cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t sum = 0;
+        for (int r = 0; r < (int)(kSuper2 / 32); r++) {
+            uint64_t j = i * kSuper2 + r * 32 + lane;
+            if (j < nblocks) sum += make_line2(text, n, j).cnt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) super_cnt[i] = sum;
+    }
+}
+
+__global__ void layout2_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               const uint64_t* __restrict__ super_base, uint4* __restrict__ lines,
+                               uint32_t* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        const uint64_t base = super_base[i];
+        const uint64_t s = base >> kShift2;  // paper: s_i = floor(rank(iS) / 2^11)
+        if (lane == 0) supers[i] = (uint32_t)s;
+        uint64_t running = base - (s << kShift2);  // rank(iS) mod 2^11, folded into every b_j
+        for (int r = 0; r < (int)(kSuper2 / 32); r++) {
+            const uint64_t j = i * kSuper2 + r * 32 + lane;
+            Line2 L;
+            if (j < nblocks) L = make_line2(text, n, j);
+            else L.cnt = 0, L.half = 0;
+            uint32_t incl = L.cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint64_t before = running + (incl - L.cnt);  // rank(jB) - 2^11 s_i
+            if (j < nblocks) {
+                const uint64_t b = before + L.half;  // rank(jB + 240) - 2^11 s_i  < 2^16
+                L.w[0] |= b;
+                uint4* dst = lines + 4 * j;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                        (uint32_t)(L.w[2 * k + 1] >> 32));
+            }
+            running += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- sigma = 4
+// Gather the low and high bits of 32 consecutive chars (one 64-bit window of
+// the 2-bit packed text) into two 32-bit values.
+__device__ __forceinline__ uint32_t even_bits(uint64_t x) {
+    x &= 0x5555555555555555ull;
+    x = (x | (x >> 1)) & 0x3333333333333333ull;
+    x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+    return (uint32_t)x;
+}
+
+struct Line4 {
+    uint64_t w[8];     // final words except the delta bits of w0, w1
+    uint32_t cnt[4];   // per-symbol count of the 224 chars
+    uint32_t half[4];  // per-symbol count of the first 96 chars
+};
+
+__device__ __forceinline__ void count_group(uint64_t L, uint64_t H, uint64_t valid, uint32_t c[4]) {
+    c[0] += popc64(~L & ~H & valid);
+    c[1] += popc64(L & ~H & valid);
+    c[2] += popc64(~L & H & valid);
+    c[3] += popc64(L & H & valid);
+}
+
+__device__ __forceinline__ Line4 make_line4(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    Line4 R;
+    const uint64_t nbits = 2 * n;
+    const uint64_t c0 = j * kB4;  // first char of the block
+    uint32_t cnt[4] = {0, 0, 0, 0};
+    // group (0,0): slots 32..63 = chars c0 .. c0+31 (slots 0..31 carry the deltas)
+    {
+        uint64_t x = bits64(t, nbits, 2 * c0);
+        uint64_t L = (uint64_t)even_bits(x) << 32, H = (uint64_t)even_bits(x >> 1) << 32;
+        count_group(L, H, 0xFFFFFFFF00000000ull, cnt);
+        R.w[0] = ~L;
+        R.w[1] = ~H;
+    }
+    // groups (0,1), (1,0), (1,1): slots 64(1+g') .. +63 = chars c0 + 32 + 64 g' .. +63
+#pragma unroll
+    for (int gg = 0; gg < 3; gg++) {
+        const uint64_t first = c0 + 32 + 64 * gg;
+        uint64_t x0 = bits64(t, nbits, 2 * first), x1 = bits64(t, nbits, 2 * first + 64);
+        uint64_t L = (uint64_t)even_bits(x0) | ((uint64_t)even_bits(x1) << 32);
+        uint64_t H = (uint64_t)even_bits(x0 >> 1) | ((uint64_t)even_bits(x1 >> 1) << 32);
+        if (gg == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) R.half[c] = cnt[c];
+            count_group(L, H, ~0ull, R.half);
+        }
+        count_group(L, H, ~0ull, cnt);
+        R.w[2 + 2 * gg] = ~L;
+        R.w[3 + 2 * gg] = ~H;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) R.cnt[c] = cnt[c];
+    return R;
+}
+
+__global__ void count4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                              uint64_t* __restrict__ super_cnt /* [4][nsuper] */) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t sum[4] = {0, 0, 0, 0};
+        for (int r = 0; r < (int)(kSuper4 / 32); r++) {
+            uint64_t j = i * kSuper4 + r * 32 + lane;
+            if (j < nblocks) {
+                Line4 L = make_line4(text, n, j);
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum[c] += L.cnt[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+            if (lane == 0) super_cnt[c * nsuper + i] = sum[c];
+        }
+    }
+}
+
+__global__ void layout4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               const uint64_t* __restrict__ super_base /* [4][nsuper] */, uint4* __restrict__ lines,
+                               uint4* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t running[4];
+        uint32_t s[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint64_t base = super_base[c * nsuper + i];
+            s[c] = (uint32_t)(base >> kShift4);  // paper: s_{i,c} = floor(rank(iS4, c) / 2^13)
+            running[c] = base - ((uint64_t)s[c] << kShift4);
+        }
+        if (lane == 0) supers[i] = make_uint4(s[0], s[1], s[2], s[3]);
+        for (int r = 0; r < (int)(kSuper4 / 32); r++) {
+            const uint64_t j = i * kSuper4 + r * 32 + lane;
+            Line4 L;
+            const bool live = j < nblocks;
+            if (live) L = make_line4(text, n, j);
+            uint64_t b[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t v = live ? L.cnt[c] : 0, incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                b[c] = running[c] + (incl - v) + (live ? L.half[c] : 0);  // rank(jB4 + 96, c) - 2^13 s_{i,c}
+                running[c] += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (live) {
+                L.w[0] = (L.w[0] & 0xFFFFFFFF00000000ull) | b[0] | (b[1] << 16);
+                L.w[1] = (L.w[1] & 0xFFFFFFFF00000000ull) | b[2] | (b[3] << 16);
+                uint4* dst = lines + 4 * j;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                        (uint32_t)(L.w[2 * k + 1] >> 32));
+            }
+        }
+    }
+}
+
+unsigned grid_for_warps(uint64_t nwarps) {
+    uint64_t blocks = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const uint64_t cap = (uint64_t)device_props().sms * 64;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
+    const uint64_t nsuper = idx->nsuper;
+    const int nsym = idx->sigma == 2 ? 1 : 4;
+    uint64_t* cnt = nullptr;
+    uint64_t* base = nullptr;
+    QR_CUDA_TRY(cudaMallocAsync((void**)&cnt, sizeof(uint64_t) * nsuper * nsym, s));
+    cudaError_t e = cudaMallocAsync((void**)&base, sizeof(uint64_t) * nsuper * nsym, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(cnt, s);
+        return cuda_fail(e, "cudaMallocAsync(scan)");
+    }
+    const unsigned grid = grid_for_warps(nsuper);
+    const unsigned threads = 32 * kWarpsPerBlock;
+    int rc = QR_OK;
+    if (idx->sigma == 2) {
+        count2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        rc = exclusive_scan_u64(cnt, base, nsuper, s);
+        if (rc == QR_OK)
+            layout2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                    (uint32_t*)idx->supers);
+    } else {
+        count4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        for (int c = 0; c < 4 && rc == QR_OK; c++)
+            rc = exclusive_scan_u64(cnt + c * nsuper, base + c * nsuper, nsuper, s);
+        if (rc == QR_OK)
+            layout4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                    (uint4*)idx->supers);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(base, s);
+    if (rc != QR_OK) return rc;
+    if (le != cudaSuccess) return cuda_fail(le, "rank layout kernels");
+    return QR_OK;
+}
+
+}  // namespace qr

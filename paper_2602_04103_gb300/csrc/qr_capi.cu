@@ -1,0 +1,296 @@
+// C-ABI entry points of the rank side (quadrank.h): argument checks, index
+// allocation, launches, the host-buffer pipeline and status handling.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "qr_common.cuh"
+
+namespace qr {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? QR_ENOMEM : QR_ECUDA;
+}
+
+const DeviceProps& device_props() {
+    static thread_local DeviceProps cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    DeviceProps& p = cache[dev & 63];
+    if (p.device != dev) {
+        p.device = dev;
+        cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&p.l2_bytes, cudaDevAttrL2CacheSize, dev);
+        if (p.sms <= 0) p.sms = 1;
+    }
+    return p;
+}
+
+static int tuning_ok(const qr_tuning_t& t) {
+    const int k = t.queries_per_thread;
+    if (k != 1 && k != 2 && k != 4 && k != 8) return 0;
+    if (t.block_threads < 64 || t.block_threads > 512 || (t.block_threads & 31)) return 0;
+    if (t.load_mode != 0 && t.load_mode != 1) return 0;
+    if (t.grid_blocks < 0) return 0;
+    return 1;
+}
+
+static void free_index(qr_index* idx) {
+    if (!idx) return;
+    if (idx->lines) cudaFree(idx->lines);
+    if (idx->supers) cudaFree(idx->supers);
+    if (idx->status) cudaFree(idx->status);
+    if (idx->stage) cudaFree(idx->stage);
+    for (auto& s : idx->pipe)
+        if (s) cudaStreamDestroy(s);
+    for (auto& e : idx->ev)
+        if (e) cudaEventDestroy(e);
+    delete idx;
+}
+
+}  // namespace qr
+
+using namespace qr;
+
+extern "C" {
+
+const char* qr_last_error(void) { return g_last_error.c_str(); }
+
+int qr_abi_version(void) { return 1; }
+
+int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device, int layout, void* stream,
+                qr_index** out) {
+    if (!out) return fail(QR_EINVAL, "qr_build: out is NULL");
+    *out = nullptr;
+    if (sigma != 2 && sigma != 4) return fail(QR_EINVAL, "qr_build: sigma must be 2 or 4");
+    if (layout != QR_LAYOUT_PAPER) return fail(QR_EINVAL, "qr_build: unknown layout");
+    if (sigma == 2 && n >= (1ull << 43)) return fail(QR_EINVAL, "qr_build: sigma 2 needs n < 2^43");
+    if (sigma == 4 && n >= (1ull << 45)) return fail(QR_EINVAL, "qr_build: sigma 4 needs n < 2^45");
+    if (!text && n > 0) return fail(QR_EINVAL, "qr_build: text is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    qr_index* idx = new qr_index();
+    cudaGetDevice(&idx->device);
+    idx->sigma = sigma;
+    idx->layout = layout;
+    idx->n = n;
+    const uint64_t B = sigma == 2 ? kB2 : kB4;
+    const uint64_t per = sigma == 2 ? kSuper2 : kSuper4;
+    idx->nblocks = n / B + 1;
+    idx->nsuper = (idx->nblocks + per - 1) / per;
+    cudaError_t e = cudaMalloc((void**)&idx->lines, 64 * idx->nblocks);
+    if (e == cudaSuccess) e = cudaMalloc(&idx->supers, (sigma == 2 ? 4 : 16) * idx->nsuper);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&idx->status, 64);
+    if (e == cudaSuccess) e = cudaMemsetAsync(idx->status, 0, 64, s);
+    if (e != cudaSuccess) {
+        free_index(idx);
+        return cuda_fail(e, "qr_build: allocation");
+    }
+    const uint64_t nwords = sigma == 2 ? (n + 63) / 64 : (n + 31) / 32;
+    const uint64_t* d_text = text;
+    uint64_t* tmp = nullptr;
+    if (!text_on_device && nwords > 0) {
+        e = cudaMallocAsync((void**)&tmp, nwords * 8, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, text, nwords * 8, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            if (tmp) cudaFreeAsync(tmp, s);
+            cudaStreamSynchronize(s);
+            free_index(idx);
+            return cuda_fail(e, "qr_build: text upload");
+        }
+        d_text = tmp;
+    }
+    int rc = build_rank_index(idx, d_text, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    e = cudaStreamSynchronize(s);
+    if (rc == QR_OK && e != cudaSuccess) rc = cuda_fail(e, "qr_build: synchronize");
+    if (rc != QR_OK) {
+        free_index(idx);
+        return rc;
+    }
+    *out = idx;
+    return QR_OK;
+}
+
+int qr_build(const uint64_t* text, uint64_t n, int sigma, int text_on_device, void* stream, qr_index** out) {
+    return qr_build_ex(text, n, sigma, text_on_device, QR_LAYOUT_PAPER, stream, out);
+}
+
+static int check_query(const qr_index* idx, const void* q, const void* out, uint64_t m, const char* who) {
+    if (!idx) return fail(QR_EINVAL, std::string(who) + ": index is NULL");
+    if (m > 0 && (!q || !out)) return fail(QR_EINVAL, std::string(who) + ": NULL buffer");
+    return QR_OK;
+}
+
+int qr_rank(const qr_index* idx, const uint64_t* q, uint64_t m, int c, uint64_t* out, void* stream) {
+    int rc = check_query(idx, q, out, m, "qr_rank");
+    if (rc) return rc;
+    if (c < 0 || c >= idx->sigma) return fail(QR_EINVAL, "qr_rank: symbol out of range");
+    return launch_rank(idx, q, nullptr, c, m, out, 0, (cudaStream_t)stream);
+}
+
+int qr_rank_c(const qr_index* idx, const uint64_t* q, const uint8_t* c, uint64_t m, uint64_t* out, void* stream) {
+    int rc = check_query(idx, q, out, m, "qr_rank_c");
+    if (rc) return rc;
+    if (m > 0 && !c) return fail(QR_EINVAL, "qr_rank_c: c is NULL");
+    return launch_rank(idx, q, c, 0, m, out, 0, (cudaStream_t)stream);
+}
+
+int qr_rank4(const qr_index* idx, const uint64_t* q, uint64_t m, uint64_t* out4, void* stream) {
+    int rc = check_query(idx, q, out4, m, "qr_rank4");
+    if (rc) return rc;
+    if (idx->sigma != 4) return fail(QR_EINVAL, "qr_rank4: needs a sigma 4 index");
+    if (((uintptr_t)out4 & 15) != 0) return fail(QR_EINVAL, "qr_rank4: out4 must be 16-byte aligned");
+    return launch_rank(idx, q, nullptr, 0, m, out4, 1, (cudaStream_t)stream);
+}
+
+// Host-buffer pipeline: chunks alternate between two internal streams; each
+// chunk is copied in, ranked and copied out on its stream, so the copy of one
+// chunk overlaps the kernel and the copy-out of its neighbours.
+static int host_pipeline(qr_index* idx, const uint64_t* qh, const uint8_t* ch, uint64_t m, int c, uint64_t* outh,
+                         int rank4, cudaStream_t caller) {
+    const uint64_t chunk = 1ull << 22;
+    const uint64_t out_per = rank4 ? 32 : 8;
+    const size_t slot_bytes = chunk * (8 + 1 + out_per);
+    const size_t need = 2 * slot_bytes;
+    if (idx->stage_bytes < need) {
+        if (idx->stage) {
+            cudaStreamSynchronize(caller);
+            for (auto& p : idx->pipe)
+                if (p) cudaStreamSynchronize(p);
+            cudaFree(idx->stage);
+            idx->stage = nullptr;
+            idx->stage_bytes = 0;
+        }
+        QR_CUDA_TRY(cudaMalloc(&idx->stage, need));
+        idx->stage_bytes = need;
+    }
+    for (auto& p : idx->pipe)
+        if (!p) QR_CUDA_TRY(cudaStreamCreateWithFlags(&p, cudaStreamNonBlocking));
+    for (auto& e : idx->ev)
+        if (!e) QR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    QR_CUDA_TRY(cudaEventRecord(idx->ev[2], caller));
+    for (auto& p : idx->pipe) QR_CUDA_TRY(cudaStreamWaitEvent(p, idx->ev[2], 0));
+    for (uint64_t off = 0, k = 0; off < m; off += chunk, k++) {
+        const uint64_t len = m - off < chunk ? m - off : chunk;
+        cudaStream_t st = idx->pipe[k & 1];
+        char* base = (char*)idx->stage + (k & 1) * slot_bytes;
+        uint64_t* dq = (uint64_t*)base;
+        uint64_t* dout = (uint64_t*)(base + chunk * 8);
+        uint8_t* dc = (uint8_t*)(base + chunk * (8 + out_per));
+        QR_CUDA_TRY(cudaMemcpyAsync(dq, qh + off, len * 8, cudaMemcpyHostToDevice, st));
+        if (ch) QR_CUDA_TRY(cudaMemcpyAsync(dc, ch + off, len, cudaMemcpyHostToDevice, st));
+        int rc = launch_rank(idx, dq, ch ? dc : nullptr, c, len, dout, rank4, st);
+        if (rc) return rc;
+        QR_CUDA_TRY(cudaMemcpyAsync(outh + off * (out_per / 8), dout, len * out_per, cudaMemcpyDeviceToHost, st));
+    }
+    for (int p = 0; p < 2; p++) {
+        QR_CUDA_TRY(cudaEventRecord(idx->ev[p], idx->pipe[p]));
+        QR_CUDA_TRY(cudaStreamWaitEvent(caller, idx->ev[p], 0));
+    }
+    QR_CUDA_TRY(cudaStreamSynchronize(caller));
+    return QR_OK;
+}
+
+int qr_rank_host(qr_index* idx, const uint64_t* q_host, const uint8_t* c_host, uint64_t m, int c,
+                 uint64_t* out_host, void* stream) {
+    int rc = check_query(idx, q_host, out_host, m, "qr_rank_host");
+    if (rc) return rc;
+    if (c >= 0 && c >= idx->sigma) return fail(QR_EINVAL, "qr_rank_host: symbol out of range");
+    if (c < 0 && m > 0 && !c_host) return fail(QR_EINVAL, "qr_rank_host: c_host is NULL");
+    if (m == 0) return QR_OK;
+    return host_pipeline(idx, q_host, c < 0 ? c_host : nullptr, m, c < 0 ? 0 : c, out_host, 0,
+                         (cudaStream_t)stream);
+}
+
+int qr_rank4_host(qr_index* idx, const uint64_t* q_host, uint64_t m, uint64_t* out4_host, void* stream) {
+    int rc = check_query(idx, q_host, out4_host, m, "qr_rank4_host");
+    if (rc) return rc;
+    if (idx->sigma != 4) return fail(QR_EINVAL, "qr_rank4_host: needs a sigma 4 index");
+    if (m == 0) return QR_OK;
+    return host_pipeline(idx, q_host, nullptr, m, 0, out4_host, 1, (cudaStream_t)stream);
+}
+
+int qr_info(const qr_index* idx, qr_info_t* info) {
+    if (!idx || !info) return fail(QR_EINVAL, "qr_info: NULL argument");
+    info->n = idx->n;
+    info->sigma = idx->sigma;
+    info->layout = idx->layout;
+    info->block_chars = idx->sigma == 2 ? kB2 : kB4;
+    info->super_blocks = idx->sigma == 2 ? kSuper2 : kSuper4;
+    info->nblocks = idx->nblocks;
+    info->nsuper = idx->nsuper;
+    info->bytes_blocks = 64 * idx->nblocks;
+    info->bytes_super = (idx->sigma == 2 ? 4 : 16) * idx->nsuper;
+    return QR_OK;
+}
+
+int qr_layout_ptrs(const qr_index* idx, const void** lines, const void** supers) {
+    if (!idx) return fail(QR_EINVAL, "qr_layout_ptrs: NULL index");
+    if (lines) *lines = idx->lines;
+    if (supers) *supers = idx->supers;
+    return QR_OK;
+}
+
+int qr_copy_layout(const qr_index* idx, void* lines_dst, void* supers_dst, void* stream) {
+    if (!idx) return fail(QR_EINVAL, "qr_copy_layout: NULL index");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (lines_dst) QR_CUDA_TRY(cudaMemcpyAsync(lines_dst, idx->lines, 64 * idx->nblocks, cudaMemcpyDefault, s));
+    if (supers_dst)
+        QR_CUDA_TRY(cudaMemcpyAsync(supers_dst, idx->supers, (idx->sigma == 2 ? 4 : 16) * idx->nsuper,
+                                    cudaMemcpyDefault, s));
+    QR_CUDA_TRY(cudaStreamSynchronize(s));
+    return QR_OK;
+}
+
+int qr_get_tuning(const qr_index* idx, qr_tuning_t* t) {
+    if (!idx || !t) return fail(QR_EINVAL, "qr_get_tuning: NULL argument");
+    *t = idx->tune;
+    return QR_OK;
+}
+
+int qr_set_tuning(qr_index* idx, const qr_tuning_t* t) {
+    if (!idx || !t) return fail(QR_EINVAL, "qr_set_tuning: NULL argument");
+    if (!tuning_ok(*t)) return fail(QR_EINVAL, "qr_set_tuning: invalid tuning");
+    idx->tune = *t;
+    return QR_OK;
+}
+
+int qr_status(qr_index* idx, void* stream) {
+    if (!idx) return fail(QR_EINVAL, "qr_status: NULL index");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t v = 0;
+    QR_CUDA_TRY(cudaMemcpyAsync(&v, idx->status, 4, cudaMemcpyDeviceToHost, s));
+    QR_CUDA_TRY(cudaMemsetAsync(idx->status, 0, 4, s));
+    QR_CUDA_TRY(cudaStreamSynchronize(s));
+    return (int)v;
+}
+
+int qr_free(qr_index* idx) {
+    if (!idx) return QR_OK;
+    cudaDeviceSynchronize();
+    free_index(idx);
+    return QR_OK;
+}
+
+int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out,
+                    int queries_per_thread, int block_threads, void* stream) {
+    if (bytes != 16 && bytes != 32 && bytes != 64 && bytes != 128) return fail(QR_EINVAL, "probe: bytes");
+    if (nrec == 0 || !buf || (m > 0 && !out)) return fail(QR_EINVAL, "probe: empty buffer");
+    if (((uintptr_t)buf & 15) != 0) return fail(QR_EINVAL, "probe: buf must be 16-byte aligned");
+    if (block_threads < 64 || block_threads > 1024 || (block_threads & 31)) return fail(QR_EINVAL, "probe: threads");
+    return launch_probe(buf, nrec, bytes, m, seed, out, queries_per_thread, block_threads, (cudaStream_t)stream);
+}
+
+}  // extern "C"

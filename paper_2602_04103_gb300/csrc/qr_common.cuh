@@ -1,0 +1,212 @@
+// Shared host/device helpers of the CUDA path: error reporting, layout
+// constants of BiRank16 / QuadRank16, exact division by the block sizes,
+// cache-hinted loads and stores, and the in-line query arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "quadrank.h"
+
+namespace qr {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define QR_CUDA_TRY(call)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::qr::cuda_fail(e_, #call);  \
+    } while (0)
+
+// ---------------------------------------------------------------- layout
+// BiRank16 (paper Sec. 3): a 64-byte line = 16-bit delta + B = 496 data bits,
+// S = 128 blocks per superblock, superblock offsets shifted right by 11,
+// deltas point to data offset 240 (line bit 256, the middle of the line).
+constexpr uint64_t kB2 = 496;
+constexpr uint64_t kSuper2 = 128;
+constexpr uint64_t kMid2 = 240;
+constexpr int kShift2 = 11;
+// QuadRank16 (paper Sec. 4): four 16-bit deltas + B4 = 224 chars, 256 blocks
+// per superblock, offsets shifted right by 13, deltas point to data index 96
+// (slot 128, the middle of the line); slot = data index + 32.
+constexpr uint64_t kB4 = 224;
+constexpr uint64_t kSuper4 = 256;
+constexpr uint64_t kMid4 = 96;
+constexpr int kShift4 = 13;
+
+// Status bits written by kernels (same values as the QR_E* status codes).
+constexpr uint32_t kStatusRange = QR_ERANGE;
+constexpr uint32_t kStatusBadSym = QR_EBADSYM;
+constexpr uint32_t kStatusTimeout = QR_ETIMEOUT;
+
+// ---------------------------------------------------------------- division
+// floor(q / 496) and floor(q / 224) for q < 2^63 without a 64-bit divide:
+// 496 = 16 * 31 and 224 = 32 * 7; x / d = mulhi(x, ceil(2^(64+s) / d)) >> s is
+// exact while x * (d * M - 2^(64+s)) < 2^(64+s) (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994).  Here
+// x < 2^59 and the error terms are 23 (d = 31, s = 4) and 6 (d = 7, s = 2).
+constexpr uint64_t kMagic31 = 0x8421084210842109ull;  // ceil(2^68 / 31)
+constexpr uint64_t kMagic7 = 0x924924924924924Aull;   // ceil(2^66 / 7)
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ uint64_t div496(uint64_t q) { return mulhi64(q >> 4, kMagic31) >> 4; }
+__host__ __device__ __forceinline__ uint64_t div224(uint64_t q) { return mulhi64(q >> 5, kMagic7) >> 2; }
+
+// ---------------------------------------------------------------- bit helpers
+__host__ __device__ __forceinline__ uint64_t low_mask(uint32_t nb) {  // nb in [0, 64]
+    return nb >= 64 ? ~0ull : ((1ull << nb) - 1ull);
+}
+__host__ __device__ __forceinline__ uint32_t clamp64(int32_t v) {
+    return (uint32_t)(v < 0 ? 0 : (v > 64 ? 64 : v));
+}
+__device__ __forceinline__ uint32_t popc64(uint64_t x) { return (uint32_t)__popcll(x); }
+
+// ---------------------------------------------------------------- memory
+// 16-byte loads of index lines: read-only path, no L1 allocation (a random
+// line is touched once per query).
+__device__ __forceinline__ uint4 ld_line16(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+// Streaming loads/stores of the query and result arrays (touched once).
+__device__ __forceinline__ uint64_t ld_stream_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint8_t ld_stream_u8(const uint8_t* p) {
+    uint16_t v;
+    asm volatile("ld.global.cs.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint8_t)v;
+}
+__device__ __forceinline__ void st_stream_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t lo64(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
+__device__ __forceinline__ uint64_t hi64(uint4 v) { return (uint64_t)v.z | ((uint64_t)v.w << 32); }
+
+// ---------------------------------------------------------------- BiRank16 query
+// A line is 8 words w0..w7; bits 0..15 of w0 hold b_j, line bit 16 + d holds
+// data bit jB + d (d < 496).  For p = q - jB:
+//   p >= 240: rank = 2^11 s + b + popcount(line bits [256, 16 + p))
+//   p <  240: rank = 2^11 s + b - popcount(line bits [16 + p, 256))
+// (paper Sec. 3, Eq. 1).  `x` holds the four words of the half the query
+// needs: w4..w7 when p >= 240, w0..w3 otherwise.
+__device__ __forceinline__ uint64_t birank_finish(uint64_t s, uint64_t w0, const uint64_t x[4], uint32_t p) {
+    const bool upper = p >= kMid2;
+    // number of counted bits measured from the start of the selected half
+    const int32_t t = upper ? (int32_t)(p - kMid2) : (int32_t)(16 + p);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        uint64_t m = low_mask(clamp64(t - 64 * k));
+        cnt += popc64(x[k] & (upper ? m : ~m));
+    }
+    const uint64_t mid = (s << kShift2) + (w0 & 0xFFFFull);
+    return upper ? mid + cnt : mid - cnt;
+}
+
+// ---------------------------------------------------------------- QuadRank16 query
+// Line words: for half h and group g, word 4h+2g = ~(low bits) and word
+// 4h+2g+1 = ~(high bits) of slots 128h+64g .. +63; the low 32 bits of words 0
+// and 1 hold b_{j,0} | b_{j,1} << 16 and b_{j,2} | b_{j,3} << 16.
+// slot = q - 224 j + 32; slot >= 128 adds the count of slots [128, slot),
+// otherwise the count of slots [slot, 128) is subtracted (paper Sec. 4 and the
+// rank1 listing of App. A).  x[0..3] = the 4 words of the needed half.
+__device__ __forceinline__ uint64_t quad_delta(uint64_t w0, uint64_t w1, int c) {
+    uint64_t w = (c & 2) ? w1 : w0;
+    return (w >> (16 * (c & 1))) & 0xFFFFull;
+}
+__device__ __forceinline__ void quad_masks(uint32_t slot, uint64_t m[2]) {
+    const bool upper = slot >= 128;
+    const int32_t t = upper ? (int32_t)(slot - 128) : (int32_t)slot;
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        uint64_t lm = low_mask(clamp64(t - 64 * g));
+        m[g] = upper ? lm : ~lm;
+    }
+}
+__device__ __forceinline__ uint64_t quad_finish1(uint64_t s_c, uint64_t delta, const uint64_t x[4], uint32_t slot,
+                                                 int c) {
+    uint64_t m[2];
+    quad_masks(slot, m);
+    const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
+    uint32_t cnt = popc64((x[0] ^ cl) & (x[1] ^ ch) & m[0]) + popc64((x[2] ^ cl) & (x[3] ^ ch) & m[1]);
+    const uint64_t mid = (s_c << kShift4) + delta;
+    return slot >= 128 ? mid + cnt : mid - cnt;
+}
+// All four counts of the masked slots: n3 = |L & H|, n1 = |L| - n3,
+// n2 = |H| - n3, n0 = |mask| - n1 - n2 - n3 (L, H = raw low/high bits).
+__device__ __forceinline__ void quad_finish4(const uint32_t s[4], uint64_t w0, uint64_t w1, const uint64_t x[4],
+                                             uint32_t slot, uint64_t r[4]) {
+    uint64_t m[2];
+    quad_masks(slot, m);
+    uint32_t nl = 0, nh = 0, n3 = 0;
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        uint64_t L = ~x[2 * g] & m[g], H = ~x[2 * g + 1] & m[g];
+        nl += popc64(L);
+        nh += popc64(H);
+        n3 += popc64(L & H);
+    }
+    const bool upper = slot >= 128;
+    const uint32_t nm = upper ? slot - 128 : 128 - slot;
+    uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        uint64_t mid = ((uint64_t)s[c] << kShift4) + quad_delta(w0, w1, c);
+        r[c] = upper ? mid + n[c] : mid - n[c];
+    }
+}
+
+// ---------------------------------------------------------------- host side
+struct DeviceProps {
+    int device = -1;
+    int sms = 0;
+    int l2_bytes = 0;
+};
+const DeviceProps& device_props();
+
+}  // namespace qr
+
+// Opaque handle of a rank index (see quadrank.h).
+struct qr_index {
+    int sigma = 2;
+    int layout = QR_LAYOUT_PAPER;
+    uint64_t n = 0;
+    uint64_t nblocks = 0, nsuper = 0;
+    uint4* lines = nullptr;      // nblocks x 64 B
+    void* supers = nullptr;      // sigma 2: uint32[nsuper]; sigma 4: uint4[nsuper]
+    uint32_t* status = nullptr;  // device status word
+    int device = 0;
+    qr_tuning_t tune{4, 256, 0, 0};
+    // host-buffer pipeline (lazy)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t pipe[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace qr {
+// Build the layout into an already sized index from a device text.
+int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
+// Launch the rank kernels (no argument checks beyond the mode).
+int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                int rank4, cudaStream_t s);
+int launch_probe(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out, int k,
+                 int threads, cudaStream_t s);
+}  // namespace qr

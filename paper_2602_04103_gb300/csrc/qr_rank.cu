@@ -1,0 +1,250 @@
+// Batched rank kernels over BiRank16 / QuadRank16 lines.
+//
+// One thread answers K independent queries: it first loads K query positions
+// (coalesced, streaming), then issues the line loads of all K queries (16-byte
+// vector loads, read-only path, no L1 allocation) and the superblock offsets,
+// and only then does the popcounts.  The K loads in flight per thread are the
+// GPU form of the paper's prefetch(q) (Sec. 3 "Prefetching"): the paper
+// prefetches the line of query i + 32 while answering query i; here every
+// resident thread keeps K lines in flight and the SM hides the latency across
+// its warps.  Load mode 1 fetches only the 32-byte sector(s) the query needs:
+// the half of the line holding its bits, plus the first 16 bytes for the
+// deltas.
+#include <cuda_runtime.h>
+
+#include "qr_common.cuh"
+
+namespace qr {
+namespace {
+
+enum Kind { kBiScalar = 0, kBiVec = 1, kQuadScalar = 2, kQuadVec = 3, kQuad4 = 4 };
+
+struct RankArgs {
+    const uint4* __restrict__ lines;
+    const void* __restrict__ supers;
+    uint64_t n;
+    const uint64_t* __restrict__ q;
+    const uint8_t* __restrict__ cvec;
+    int c;
+    uint64_t m;
+    uint64_t* __restrict__ out;
+    uint32_t* status;
+};
+
+template <int K, int LOAD, int KIND>
+__global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
+    constexpr bool kQuad = KIND >= kQuadScalar;
+    const uint64_t tile = (uint64_t)blockDim.x * K;
+    uint32_t bad_flags = 0;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < a.m; t0 += (uint64_t)gridDim.x * tile) {
+        uint64_t qv[K];
+        int cv[K];
+        bool live[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            live[k] = i < a.m;
+            qv[k] = live[k] ? ld_stream_u64(a.q + i) : 0;
+            if (KIND == kBiVec || KIND == kQuadVec) cv[k] = live[k] ? (int)ld_stream_u8(a.cvec + i) : 0;
+            else cv[k] = a.c;
+        }
+        // issue every load of the K queries before any arithmetic on them
+        uint4 v0[K], va[K], vb[K];
+        uint32_t s1[K];
+        uint4 s4[K];
+        uint32_t pos[K];  // p = q - jB (sigma 2) or slot = q - jB4 + 32 (sigma 4)
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t qq = qv[k] <= a.n ? qv[k] : 0;  // out-of-range queries read line 0
+            uint64_t j;
+            bool upper;
+            if (!kQuad) {
+                j = div496(qq);
+                pos[k] = (uint32_t)(qq - j * kB2);
+                upper = pos[k] >= kMid2;
+                s1[k] = __ldg((const uint32_t*)a.supers + (j >> 7));
+            } else {
+                j = div224(qq);
+                pos[k] = (uint32_t)(qq - j * kB4) + 32;
+                upper = pos[k] >= 128;
+                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
+                else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + (cv[k] & 3));
+            }
+            const uint4* L = a.lines + 4 * j;
+            v0[k] = ld_line16(L);
+            if (LOAD == 0) {
+                // whole line: all four 16-byte quarters (both 32-byte sectors)
+                const uint4 u1 = ld_line16(L + 1), u2 = ld_line16(L + 2), u3 = ld_line16(L + 3);
+                va[k] = upper ? u2 : u1;
+                vb[k] = upper ? u3 : u2;
+            } else {
+                // sectors: lower half = quarters 0, 1 (one sector); upper half =
+                // quarter 0 (deltas) + quarters 2, 3
+                va[k] = ld_line16(L + (upper ? 2 : 1));
+                vb[k] = upper ? ld_line16(L + 3) : make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            const bool range_bad = qv[k] > a.n;
+            const uint64_t w0 = lo64(v0[k]), w1 = hi64(v0[k]);
+            if (!kQuad) {
+                const bool upper = pos[k] >= kMid2;
+                uint64_t x[4];
+                if (upper) { x[0] = lo64(va[k]); x[1] = hi64(va[k]); x[2] = lo64(vb[k]); x[3] = hi64(vb[k]); }
+                else { x[0] = w0; x[1] = w1; x[2] = lo64(va[k]); x[3] = hi64(va[k]); }
+                const uint64_t r1 = birank_finish(s1[k], w0, x, pos[k]);
+                const int c = cv[k];
+                const bool sym_bad = (unsigned)c > 1u;
+                uint64_t r = c == 1 ? r1 : qv[k] - r1;
+                if (range_bad || sym_bad) r = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, r);
+                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            } else {
+                const bool upper = pos[k] >= 128;
+                uint64_t x[4];
+                if (upper) { x[0] = lo64(va[k]); x[1] = hi64(va[k]); x[2] = lo64(vb[k]); x[3] = hi64(vb[k]); }
+                else { x[0] = w0; x[1] = w1; x[2] = lo64(va[k]); x[3] = hi64(va[k]); }
+                if (KIND == kQuad4) {
+                    uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
+                    uint64_t r[4];
+                    quad_finish4(s, w0, w1, x, pos[k], r);
+                    if (range_bad) r[0] = r[1] = r[2] = r[3] = ~0ull;
+                    if (live[k]) {
+                        uint64_t* o = a.out + 4 * i;
+                        asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o), "l"(r[0]), "l"(r[1]) : "memory");
+                        asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o + 2), "l"(r[2]), "l"(r[3])
+                                     : "memory");
+                        bad_flags |= range_bad ? kStatusRange : 0u;
+                    }
+                } else {
+                    const int c = cv[k];
+                    const bool sym_bad = (unsigned)c > 3u;
+                    uint64_t r = quad_finish1(s1[k], quad_delta(w0, w1, c & 3), x, pos[k], c & 3);
+                    if (range_bad || sym_bad) r = ~0ull;
+                    if (live[k]) {
+                        st_stream_u64(a.out + i, r);
+                        bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                    }
+                }
+            }
+        }
+    }
+    if (bad_flags) atomicOr(a.status, bad_flags);
+}
+
+// ---------------------------------------------------------------- launch table
+using KernelFn = void (*)(RankArgs);
+
+template <int KIND>
+KernelFn pick(int k, int load) {
+    switch (k * 2 + load) {
+        case 2: return rank_kernel<1, 0, KIND>;
+        case 3: return rank_kernel<1, 1, KIND>;
+        case 4: return rank_kernel<2, 0, KIND>;
+        case 5: return rank_kernel<2, 1, KIND>;
+        case 8: return rank_kernel<4, 0, KIND>;
+        case 9: return rank_kernel<4, 1, KIND>;
+        case 16: return rank_kernel<8, 0, KIND>;
+        case 17: return rank_kernel<8, 1, KIND>;
+        default: return nullptr;
+    }
+}
+
+KernelFn pick_kind(int kind, int k, int load) {
+    switch (kind) {
+        case kBiScalar: return pick<kBiScalar>(k, load);
+        case kBiVec: return pick<kBiVec>(k, load);
+        case kQuadScalar: return pick<kQuadScalar>(k, load);
+        case kQuadVec: return pick<kQuadVec>(k, load);
+        case kQuad4: return pick<kQuad4>(k, load);
+        default: return nullptr;
+    }
+}
+
+unsigned resident_grid(KernelFn fn, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (unsigned)(per_sm * device_props().sms);
+}
+
+// ---------------------------------------------------------------- gather probe
+__device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <int K, int V>  // V = 16-byte vectors per record
+__global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ buf, uint64_t nrec, uint64_t m,
+                                                     uint64_t seed, uint64_t* __restrict__ out) {
+    const uint64_t tile = (uint64_t)blockDim.x * K;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < m; t0 += (uint64_t)gridDim.x * tile) {
+        uint4 v[K][V];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            const uint64_t r = mulhi64(probe_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull), nrec);
+#pragma unroll
+            for (int u = 0; u < V; u++) v[k][u] = ld_line16(buf + r * V + u);
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            uint64_t d = 0;
+#pragma unroll
+            for (int u = 0; u < V; u++) d ^= lo64(v[k][u]) ^ hi64(v[k][u]);
+            if (i < m) st_stream_u64(out + i, d);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                int rank4, cudaStream_t s) {
+    if (m == 0) return QR_OK;
+    int kind;
+    if (idx->sigma == 2) kind = cvec ? kBiVec : kBiScalar;
+    else kind = rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
+    const qr_tuning_t& t = idx->tune;
+    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode);
+    if (!fn) return fail(QR_EINVAL, "no rank kernel for this tuning");
+    RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status};
+    const uint64_t tiles = (m + (uint64_t)t.block_threads * t.queries_per_thread - 1) /
+                           ((uint64_t)t.block_threads * t.queries_per_thread);
+    uint64_t grid = t.grid_blocks > 0 ? (uint64_t)t.grid_blocks : resident_grid(fn, t.block_threads);
+    if (grid > tiles) grid = tiles;
+    fn<<<(unsigned)grid, t.block_threads, 0, s>>>(a);
+    QR_CUDA_TRY(cudaGetLastError());
+    return QR_OK;
+}
+
+int launch_probe(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out, int k,
+                 int threads, cudaStream_t s) {
+    if (m == 0) return QR_OK;
+    void (*fn)(const uint4*, uint64_t, uint64_t, uint64_t, uint64_t*) = nullptr;
+#define QR_PROBE_CASE(KK, VV) \
+    if (k == KK && bytes == 16 * VV) fn = probe_kernel<KK, VV>;
+    QR_PROBE_CASE(1, 1) QR_PROBE_CASE(1, 2) QR_PROBE_CASE(1, 4) QR_PROBE_CASE(1, 8)
+    QR_PROBE_CASE(2, 1) QR_PROBE_CASE(2, 2) QR_PROBE_CASE(2, 4) QR_PROBE_CASE(2, 8)
+    QR_PROBE_CASE(4, 1) QR_PROBE_CASE(4, 2) QR_PROBE_CASE(4, 4) QR_PROBE_CASE(4, 8)
+    QR_PROBE_CASE(8, 1) QR_PROBE_CASE(8, 2) QR_PROBE_CASE(8, 4)
+#undef QR_PROBE_CASE
+    if (!fn) return fail(QR_EINVAL, "qr_probe_gather: unsupported (bytes, queries_per_thread)");
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t tiles = (m + (uint64_t)threads * k - 1) / ((uint64_t)threads * k);
+    uint64_t grid = (uint64_t)per_sm * device_props().sms;
+    if (grid > tiles) grid = tiles;
+    fn<<<(unsigned)grid, threads, 0, s>>>((const uint4*)buf, nrec, m, seed, out);
+    QR_CUDA_TRY(cudaGetLastError());
+    return QR_OK;
+}
+
+}  // namespace qr

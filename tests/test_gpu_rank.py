@@ -1,0 +1,299 @@
+"""GPU parity of BiRank / QuadRank rank, rank with per-query symbols and
+rank_4 against the oracle: bit-exact (integer results).
+
+Covers tiny exhaustive texts, multi-superblock texts with every q, edge
+lengths around block and superblock boundaries, adversarial texts that reach
+the largest 16-bit deltas the paper's bounds allow (Sec. 3: b_j <= S + 2^11 - 1;
+Sec. 4: S4 + 2^13 - 1), out-of-range queries and symbols, every launch
+tuning, the host-buffer pipeline and the layout itself.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_04103_gb300 import synth
+from tests.gpu_util import build, dev_u64, dev_u8, host_u64, rank, rank4
+
+pytestmark = pytest.mark.gpu
+
+B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def check_bits(words, n, q=None, cs=(0, 1)):
+    idx = build(words, n, 2)
+    q = np.arange(n + 1, dtype=np.uint64) if q is None else q
+    for c in cs:
+        want, rc = oracle.rank(words, n, 2, q, c)
+        assert rc == 0
+        got = rank(idx, q, c)
+        assert np.array_equal(got, want), (n, c, np.flatnonzero(got != want)[:5])
+    return idx
+
+
+def check_dna(words, n, q=None):
+    idx = build(words, n, 4)
+    q = np.arange(n + 1, dtype=np.uint64) if q is None else q
+    w4, rc = oracle.rank4(words, n, q)
+    assert rc == 0
+    assert np.array_equal(rank4(idx, q), w4), n
+    for c in range(4):
+        assert np.array_equal(rank(idx, q, c), w4[:, c]), (n, c)
+    cv = synth.symbols(n + 17, q.size, 4)
+    assert np.array_equal(rank(idx, q, cv), w4[np.arange(q.size), cv])
+    return idx
+
+
+def test_tiny_exhaustive_bits():
+    for L in range(0, 11):
+        for bits in itertools.product([0, 1], repeat=L):
+            check_bits(synth.pack_bits(np.array(bits, dtype=np.uint8)), L)
+
+
+def test_tiny_exhaustive_dna():
+    for L in range(0, 6):
+        for codes in itertools.product(range(4), repeat=L):
+            check_dna(synth.pack2(np.array(codes, dtype=np.uint8)), L)
+
+
+@pytest.mark.parametrize("p", [0.5, 0.01, 0.99])
+def test_multi_superblock_bits_every_q(p):
+    n = 3 * S2 + 1234
+    words = synth.bits(synth.base_seed(1) + int(p * 100), n, p)
+    check_bits(words, n)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "gc_runs"])
+def test_multi_superblock_dna_every_q(kind):
+    n = 3 * S4 + 777
+    words = synth.dna_uniform(5, n) if kind == "uniform" else synth.dna_gc_runs(6, n, 0.4, 0.05, 10, 1000)
+    check_dna(words, n)
+
+
+@pytest.mark.parametrize("n", [0, 1, 63, 64, 239, 240, 241, 255, 256, 495, 496, 497, 991, 992, 993,
+                               S2 - 1, S2, S2 + 1, 2 * S2, 2 * S2 + 240])
+def test_edge_lengths_bits(n):
+    check_bits(synth.bits(n + 3, n, 0.5), n)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 95, 96, 97, 127, 128, 223, 224, 225, 447, 448,
+                               S4 - 1, S4, S4 + 1, 2 * S4 + 96])
+def test_edge_lengths_dna(n):
+    check_dna(synth.dna_uniform(n + 5, n), n)
+
+
+def read_layout(idx, sigma):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    info = capi.qr_info(idx)
+    lines = np.empty(info["bytes_blocks"] // 8, dtype=np.uint64)
+    sup = np.empty(info["bytes_super"] // 4, dtype=np.uint32)
+    capi.qr_copy_layout(idx, lines, sup)
+    return info, lines.reshape(-1, 8), sup
+
+
+def test_max_delta_bits():
+    # superblock 0 holds 2047 ones then zeros, so rank(S) mod 2^11 = 2047; superblock
+    # 1 is all ones: its last block's delta is 2047 + 127 * 496 + 240 = 65279
+    n = 2 * S2 + 3000
+    bits = np.zeros(n, dtype=np.uint8)
+    bits[:2047] = 1
+    bits[S2:2 * S2] = 1
+    words = synth.pack_bits(bits)
+    idx = check_bits(words, n)
+    info, lines, sup = read_layout(idx, 2)
+    deltas = (lines[:, 0] & np.uint64(0xFFFF)).astype(np.int64)
+    assert deltas.max() == 2047 + 127 * B2 + 240 == 65279
+    assert sup.tolist()[:3] == [0, 0, (2047 + S2) >> 11]
+
+
+def test_max_delta_dna():
+    n = 2 * S4 + 5000
+    codes = np.zeros(n, dtype=np.uint8)
+    codes[:8191] = 3
+    codes[S4:2 * S4] = 3
+    words = synth.pack2(codes)
+    idx = check_dna(words, n, q=np.concatenate([np.arange(0, n + 1, 7), [n]]).astype(np.uint64))
+    info, lines, sup = read_layout(idx, 4)
+    d3 = ((lines[:, 1] >> np.uint64(16)) & np.uint64(0xFFFF)).astype(np.int64)   # b_{j,T}
+    assert d3.max() == 8191 + 255 * B4 + 96 == 65407
+
+
+def test_layout_matches_definitions():
+    # b_j = rank(jB + 240) - 2^11 s_{j/128}, s_i = floor(rank(iS) / 2^11)   (Sec. 3)
+    n = 4 * S2 + 4321
+    words = synth.bits(99, n, 0.37)
+    idx = build(words, n, 2)
+    info, lines, sup = read_layout(idx, 2)
+    nb = n // B2 + 1
+    assert info["nblocks"] == nb and lines.shape[0] == nb
+    js = np.arange(nb, dtype=np.uint64)
+    mids = np.minimum(js * np.uint64(B2) + np.uint64(240), np.uint64(n))
+    r_mid, _ = oracle.rank(words, n, 2, mids, 1)
+    # past the end the text is padded with zeros, so rank(min(x, n)) is the padded rank
+    starts = np.arange(info["nsuper"], dtype=np.uint64) * np.uint64(S2)
+    r_sup, _ = oracle.rank(words, n, 2, np.minimum(starts, np.uint64(n)), 1)
+    assert np.array_equal(sup.astype(np.uint64), r_sup >> np.uint64(11))
+    want_b = r_mid - (sup.astype(np.uint64)[js >> np.uint64(7)] << np.uint64(11))
+    assert np.array_equal(lines[:, 0] & np.uint64(0xFFFF), want_b)
+    # the data bits follow the delta: line bit 16 + d = text bit jB + d
+    tb = np.unpackbits(words.view(np.uint8), bitorder="little")
+    lb = np.unpackbits(lines.view(np.uint8), bitorder="little").reshape(nb, 512)
+    for j in [0, 1, 127, 128, nb - 1]:
+        lo, hi = j * B2, min(j * B2 + B2, n)
+        assert np.array_equal(lb[j, 16:16 + hi - lo], tb[lo:hi])
+        assert lb[j, 16 + hi - lo:].sum() == 0
+
+
+def test_layout_matches_definitions_dna():
+    # b_{j,c} = rank(jB4 + 96, c) - 2^13 s_{j/256,c}; transposed, negated data (Sec. 4)
+    n = 2 * S4 + 999
+    words = synth.dna_uniform(123, n)
+    idx = build(words, n, 4)
+    info, lines, sup = read_layout(idx, 4)
+    sup = sup.reshape(-1, 4).astype(np.uint64)
+    nb = info["nblocks"]
+    js = np.arange(nb, dtype=np.uint64)
+    mids = np.minimum(js * np.uint64(B4) + np.uint64(96), np.uint64(n))
+    r4, _ = oracle.rank4(words, n, mids)
+    # padding chars are A (code 0): the padded rank of A at a middle past n grows by the excess
+    excess = (js * np.uint64(B4) + np.uint64(96)) - mids
+    r4[:, 0] += excess
+    starts = np.minimum(np.arange(info["nsuper"], dtype=np.uint64) * np.uint64(S4), np.uint64(n))
+    rs, _ = oracle.rank4(words, n, starts)
+    assert np.array_equal(sup, rs >> np.uint64(13))
+    w0, w1 = lines[:, 0], lines[:, 1]
+    got = np.stack([w0 & np.uint64(0xFFFF), (w0 >> np.uint64(16)) & np.uint64(0xFFFF),
+                    w1 & np.uint64(0xFFFF), (w1 >> np.uint64(16)) & np.uint64(0xFFFF)], axis=1)
+    assert np.array_equal(got, r4 - (sup[js >> np.uint64(8)] << np.uint64(13)))
+    # slot s of the line holds data char s - 32: raw low bit = ~word[4h+2g] bit
+    codes = synth.unpack2(words, n)
+    for j in [0, 1, 255, 256, nb - 1]:
+        for slot in range(32, 256):
+            d = j * B4 + slot - 32
+            h, g, b = slot // 128, (slot % 128) // 64, slot % 64
+            lo = (~int(lines[j, 4 * h + 2 * g]) >> b) & 1
+            hi = (~int(lines[j, 4 * h + 2 * g + 1]) >> b) & 1
+            want = int(codes[d]) if d < n else 0
+            assert lo | (hi << 1) == want, (j, slot)
+
+
+def test_sizes_and_paper_overheads():
+    from paper_2602_04103_gb300 import capi
+    for n in [1 << 20, 3 * S2 + 5]:
+        idx = build(synth.bits(1, n, 0.5), n, 2)
+        info = capi.qr_info(idx)
+        nb = n // B2 + 1
+        assert info["bytes_blocks"] == 64 * nb
+        assert info["bytes_super"] == 4 * ((nb + 127) // 128)
+    # overheads from the closed forms at large n: 3.28% (Sec. 3) and 14.40% (Sec. 4)
+    n2 = 1 << 34
+    nb = n2 // B2 + 1
+    over2 = (64 * nb + 4 * ((nb + 127) // 128)) * 8 / n2 - 1
+    assert abs(over2 * 100 - 3.28) < 0.005
+    n4 = 1 << 32
+    nb4 = n4 // B4 + 1
+    over4 = (64 * nb4 + 16 * ((nb4 + 255) // 256)) * 8 / (2 * n4) - 1
+    assert abs(over4 * 100 - 14.40) < 0.005
+
+
+def test_out_of_range_and_bad_symbols():
+    from paper_2602_04103_gb300 import capi
+    n = S2 + 10
+    words = synth.bits(3, n, 0.5)
+    idx = build(words, n, 2)
+    q = np.array([0, n, n + 1, 1 << 40, 5], dtype=np.uint64)
+    got = rank(idx, q, 1)
+    want, _ = oracle.rank(words, n, 2, np.array([0, n, 5], dtype=np.uint64), 1)
+    assert got[[0, 1, 4]].tolist() == want.tolist()
+    assert got[2] == np.uint64(2 ** 64 - 1) and got[3] == np.uint64(2 ** 64 - 1)
+    assert capi.qr_status(idx) == capi.QR_ERANGE
+    assert capi.qr_status(idx) == 0
+    got = rank(idx, np.array([1, 2, 3], dtype=np.uint64), np.array([1, 2, 0], dtype=np.uint8))
+    assert got[1] == np.uint64(2 ** 64 - 1)
+    assert capi.qr_status(idx) == capi.QR_EBADSYM
+    with pytest.raises(capi.QRError):
+        rank(idx, q, 2)
+    n4 = 1000
+    w4 = synth.dna_uniform(4, n4)
+    idx4 = build(w4, n4, 4)
+    r = rank4(idx4, np.array([n4 + 1, 3], dtype=np.uint64))
+    assert (r[0] == np.uint64(2 ** 64 - 1)).all()
+    assert capi.qr_status(idx4) == capi.QR_ERANGE
+    with pytest.raises(capi.QRError):
+        rank4(idx, np.array([1], dtype=np.uint64))   # sigma 2 index
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+@pytest.mark.parametrize("load", [0, 1])
+@pytest.mark.parametrize("threads", [64, 256, 512])
+def test_every_tuning(k, load, threads):
+    from paper_2602_04103_gb300 import capi
+    n, n4 = 3 * S2 + 77, 3 * S4 + 99
+    words, w4 = synth.bits(17, n, 0.5), synth.dna_uniform(18, n4)
+    q = synth.queries(19, n, 100_003)
+    q4 = synth.queries(20, n4, 100_003)
+    cv = synth.symbols(21, q4.size, 4)
+    idx, idx4 = build(words, n, 2), build(w4, n4, 4)
+    for i in (idx, idx4):
+        capi.qr_set_tuning(i, k, threads, load, 0)
+    assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
+    assert np.array_equal(rank(idx4, q4, cv), oracle.rank_c(w4, n4, 4, q4, cv)[0])
+    assert np.array_equal(rank4(idx4, q4), oracle.rank4(w4, n4, q4)[0])
+    capi.qr_set_tuning(idx, k, threads, load, 7)    # explicit small grid: grid-stride loop
+    assert np.array_equal(rank(idx, q, 0), oracle.rank(words, n, 2, q, 0)[0])
+
+
+def test_host_pipeline_matches_device():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 5 * S4 + 3
+    w4 = synth.dna_uniform(31, n)
+    idx = build(w4, n, 4)
+    m = (1 << 22) + 12345                       # two chunks, ragged
+    q = synth.queries(32, n, m)
+    cv = synth.symbols(33, m, 4)
+    qh = torch.from_numpy(q.view(np.int64)).pin_memory()
+    ch = torch.from_numpy(cv).pin_memory()
+    out = torch.empty(m, dtype=torch.int64).pin_memory()
+    capi.qr_rank_host(idx, qh, ch, out)
+    want1, _ = oracle.rank_c(w4, n, 4, q, cv)
+    assert np.array_equal(out.numpy().view(np.uint64), want1)
+    out4 = torch.empty((m, 4), dtype=torch.int64).pin_memory()
+    capi.qr_rank4_host(idx, qh, out4)
+    want4, _ = oracle.rank4(w4, n, q)
+    assert np.array_equal(out4.numpy().view(np.uint64), want4)
+    capi.qr_rank_host(idx, qh, 2, out)
+    assert np.array_equal(out.numpy().view(np.uint64), want4[:, 2])
+    # pageable host memory works too
+    outp = np.empty(m, dtype=np.uint64)
+    capi.qr_rank_host(idx, q, 1, outp)
+    assert np.array_equal(outp, want4[:, 1])
+
+
+def test_concurrent_streams_same_index():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 2 * S2 + 5
+    words = synth.bits(41, n, 0.5)
+    idx = build(words, n, 2)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    qs = [synth.queries(50 + i, n, 200_000) for i in range(4)]
+    outs = []
+    for s, q in zip(streams, qs):
+        with torch.cuda.stream(s):
+            dq = dev_u64(q)
+            o = torch.empty_like(dq)
+            capi.qr_rank(idx, dq, 1, o, stream=s)
+            outs.append((dq, o))
+    torch.cuda.synchronize()
+    for (dq, o), q in zip(outs, qs):
+        assert np.array_equal(host_u64(o), oracle.rank(words, n, 2, q, 1)[0])

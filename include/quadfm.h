@@ -1,0 +1,99 @@
+/*
+ * quadfm.h -- C ABI of the QuadFm count-only FM-index in libquadrank.so:
+ * index construction over a DNA text and batched exact-match counting by
+ * backward search over a QuadRank16 structure holding the BWT.
+ *
+ * Source: R. Groot Koerkamp, "QuadRank: Engineering a High Throughput Rank",
+ * arXiv 2602.04103, App. E ("QuadFm: A Batching FM-index").  Conventions
+ * (return codes, streams, ownership, status bits) are those of quadrank.h.
+ */
+#ifndef QUADFM_H
+#define QUADFM_H
+
+#include "quadrank.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qfm_index qfm_index;
+
+
+typedef struct {
+    uint64_t n;            /* text length (chars); the BWT has n + 1 rows     */
+    uint64_t dollar_row;   /* BWT row of the sentinel $                       */
+    uint64_t C[5];         /* C[c] = 1 + #chars < c; C[4] = n + 1             */
+    uint64_t bytes_rank;   /* bytes of the QuadRank16 structure over the BWT  */
+    uint64_t bytes_table;  /* bytes of the 8-mer table                        */
+    int32_t kmer;          /* prefix-table length (8)                          */
+    int32_t has_sa;        /* 1 if the suffix array was kept (QFM_KEEP_SA)     */
+} qfm_info_t;
+
+#define QFM_KEEP_SA 1      /* qfm_build flag: keep the suffix array for export */
+
+/*
+ * qfm_build -- build the count-only FM-index of a DNA text.
+ * Paper: App. E (QuadFm: one sentinel $ whose BWT position is stored, the
+ * BWT held in a QuadRank16 structure, an 8-character prefix lookup table that
+ * replaces the first 8 search steps).  The paper does not describe suffix
+ * array construction; this library sorts the suffixes of T$ by prefix
+ * doubling on the GPU.
+ *   codes  n bytes 0..3 (host if codes_on_device == 0, else device).
+ *   n      1 <= n < 2^32 - 1.
+ *   flags  0 or QFM_KEEP_SA.
+ *   stream the call synchronises it before returning.
+ * Errors: QR_EINVAL (n, null, a byte > 3), QR_ENOMEM, QR_ECUDA.
+ */
+int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, void* stream, qfm_index** out);
+
+/*
+ * qfm_count -- out[k] = number of occurrences of pattern k in T, for k < m,
+ * in one persistent kernel: every warp pulls pattern ids from a device work
+ * queue (an atomic counter), each lane runs one backward search (8-mer table,
+ * then LF steps lo = C[c] + rank(lo, c) - [c = 0 and lo > dollar_row], same for
+ * hi, while lo < hi), and a lane whose search ends is refilled at once.
+ * Paper: App. E (query_batch: a batch of active searches, finished ones
+ * swapped out, rank + LF for the rest), Sec. 4 rank1.
+ *   patterns  device bytes 0..3, pattern k = patterns[offsets[k] .. offsets[k+1]).
+ *   offsets   device array of m + 1 non-decreasing uint64.
+ *   out       device array of m uint64.
+ * The empty pattern counts n + 1 (every position 0..n).  A pattern holding a
+ * byte > 3 yields 0 and sets QR_EBADSYM in the status.  The call allocates a
+ * 16-byte work-queue counter from the stream-ordered pool of the stream.
+ * Errors: QR_EINVAL (null with m > 0), QR_ENOMEM, QR_ECUDA.
+ */
+int qfm_count(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
+              void* stream);
+
+/*
+ * qfm_count_stepwise -- the same counts with one kernel launch per search step
+ * (the plain form: a table-lookup launch, then launches that each advance
+ * every active search by one character).  Kept as the comparison baseline.
+ * It allocates per-pattern state (24 bytes x m) from the stream-ordered pool
+ * and synchronises the stream once to learn the longest pattern.
+ */
+int qfm_count_stepwise(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,
+                       uint64_t* out, void* stream);
+
+/* Index facts.  Errors: QR_EINVAL. */
+int qfm_info(const qfm_index* idx, qfm_info_t* info);
+
+/* Copy the index pieces to caller device buffers (any pointer may be NULL):
+ * sa (n + 1 uint32, requires QFM_KEEP_SA), bwt codes (n + 1 bytes, the $ row
+ * holds 0), table (4^8 x 2 uint64: [lo, hi) of every 8-mer, k-mer index
+ * sum code_i 4^(7-i)).  Synchronises stream. */
+int qfm_export(const qfm_index* idx, uint32_t* sa, uint8_t* bwt, uint64_t* table, void* stream);
+
+/* The rank index over the BWT (owned by the FM index). */
+const qr_index* qfm_rank_index(const qfm_index* idx);
+
+/* As qr_status, for the FM index. */
+int qfm_status(qfm_index* idx, void* stream);
+
+/* Release (waits for the device). NULL is a no-op. */
+int qfm_free(qfm_index* idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QUADFM_H */

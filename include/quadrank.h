@@ -68,8 +68,10 @@ typedef struct {
 typedef struct {
     int32_t queries_per_thread;  /* independent queries in flight per thread: 1,2,4,8 */
     int32_t block_threads;       /* 64..512, multiple of 32                            */
-    int32_t load_mode;           /* 0: whole 64-byte line; 1: only the 32-byte sectors  */
-                                 /*    the query needs                                  */
+    int32_t load_mode;           /* 0: whole 64-byte line, 16-byte loads;               */
+                                 /* 1: only the 32-byte sectors the query needs, 16-byte */
+                                 /*    loads; 2: whole line, 32-byte loads; 3: needed    */
+                                 /*    sectors, 32-byte loads                            */
     int32_t grid_blocks;         /* 0: SM count x resident blocks per SM                */
 } qr_tuning_t;
 
@@ -177,8 +179,9 @@ int qr_free(qr_index* idx);
 
 /*
  * qr_probe_gather -- measurement aid: out[k] = XOR of the `bytes`-byte record
- * at a random record index of buf for m draws, one 16-byte vector load at a
- * time, with the same threads-and-loads-in-flight scheme as the rank kernels.
+ * at a random record index of buf for m draws, read with load_bytes-byte (16
+ * or 32) vector loads, with the same threads-and-loads-in-flight scheme as the
+ * rank kernels.
  * It gives the random-access ceiling of this GPU's memory for records of 32,
  * 64 or 128 bytes, the GPU counterpart of the paper's measured random-access
  * limit of RAM (Sec. 5.1, "Lower bounds": 2.5 ns per cache line in total).
@@ -189,8 +192,8 @@ int qr_free(qr_index* idx);
  * Errors: QR_EINVAL (bytes not 16/32/64/128, nrec = 0, no kernel for
  * (bytes, queries_per_thread) -- 128-byte records allow at most 4 in flight).
  */
-int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out,
-                    int queries_per_thread, int block_threads, void* stream);
+int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed,
+                    uint64_t* out, int queries_per_thread, int block_threads, void* stream);
 
 #ifdef __cplusplus
 }

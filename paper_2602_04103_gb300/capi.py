@@ -66,7 +66,7 @@ _sig("qr_get_tuning", [vp, C.POINTER(qr_tuning_t)])
 _sig("qr_set_tuning", [vp, C.POINTER(qr_tuning_t)])
 _sig("qr_status", [vp, vp])
 _sig("qr_free", [vp])
-_sig("qr_probe_gather", [vp, u64, i32, u64, u64, vp, i32, i32, vp])
+_sig("qr_probe_gather", [vp, u64, i32, i32, u64, u64, vp, i32, i32, vp])
 
 
 def _check(rc: int, where: str) -> None:
@@ -183,6 +183,69 @@ def qr_status(idx: QRIndex, stream=None) -> int:
 
 
 def qr_probe_gather(buf, nrec: int, nbytes: int, m: int, seed: int, out, queries_per_thread=4,
-                    block_threads=256, stream=None) -> None:
-    _check(lib.qr_probe_gather(ptr(buf), nrec, nbytes, m, seed, ptr(out), queries_per_thread, block_threads,
-                               stream_ptr(stream)), "qr_probe_gather")
+                    block_threads=256, load_bytes=16, stream=None) -> None:
+    _check(lib.qr_probe_gather(ptr(buf), nrec, nbytes, load_bytes, m, seed, ptr(out), queries_per_thread,
+                               block_threads, stream_ptr(stream)), "qr_probe_gather")
+
+
+# ---------------------------------------------------------------- QuadFm (include/quadfm.h)
+class qfm_info_t(C.Structure):
+    _fields_ = [("n", u64), ("dollar_row", u64), ("C", u64 * 5), ("bytes_rank", u64), ("bytes_table", u64),
+                ("kmer", C.c_int32), ("has_sa", C.c_int32)]
+
+
+_sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
+_sig("qfm_count", [vp, vp, vp, u64, vp, vp])
+_sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
+_sig("qfm_info", [vp, C.POINTER(qfm_info_t)])
+_sig("qfm_export", [vp, vp, vp, vp, vp])
+_sig("qfm_rank_index", [vp], vp)
+_sig("qfm_status", [vp, vp])
+_sig("qfm_free", [vp])
+
+
+class QFMIndex(QRIndex):
+    """Owner of a qfm_index* (freed with qfm_free)."""
+
+    def free(self) -> None:
+        if self.handle:
+            lib.qfm_free(self.handle)
+            self.handle = None
+
+
+def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None) -> QFMIndex:
+    on_dev = int(hasattr(codes, "is_cuda") and codes.is_cuda)
+    n = numel(codes) if n is None else n
+    h = vp()
+    _check(lib.qfm_build(ptr(codes), n, on_dev, flags, stream_ptr(stream), C.byref(h)), "qfm_build")
+    return QFMIndex(h.value)
+
+
+def qfm_count(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:
+    m = numel(offsets) - 1
+    _check(lib.qfm_count(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)), "qfm_count")
+
+
+def qfm_count_stepwise(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:
+    m = numel(offsets) - 1
+    _check(lib.qfm_count_stepwise(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)),
+           "qfm_count_stepwise")
+
+
+def qfm_info(idx: QFMIndex) -> dict:
+    info = qfm_info_t()
+    _check(lib.qfm_info(idx, C.byref(info)), "qfm_info")
+    d = {k: getattr(info, k) for k, _ in qfm_info_t._fields_}
+    d["C"] = list(info.C)
+    return d
+
+
+def qfm_export(idx: QFMIndex, sa=None, bwt=None, table=None, stream=None) -> None:
+    _check(lib.qfm_export(idx, ptr(sa), ptr(bwt), ptr(table), stream_ptr(stream)), "qfm_export")
+
+
+def qfm_status(idx: QFMIndex, stream=None) -> int:
+    rc = lib.qfm_status(idx, stream_ptr(stream))
+    if rc in (QR_EINVAL, QR_ECUDA, QR_ENOMEM):
+        raise QRError(rc, "qfm_status")
+    return rc

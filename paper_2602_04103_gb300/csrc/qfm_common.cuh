@@ -1,0 +1,63 @@
+// QuadFm index handle and the rank step of the backward search, shared by the
+// builder and the count kernels.
+#pragma once
+
+#include "qr_common.cuh"
+
+constexpr int kQfmK = 8;                  // prefix-table length (paper App. E)
+constexpr uint64_t kQfmTable = 1ull << 16; // 4^8 entries
+
+// Opaque handle of a count-only FM-index (see quadfm.h).
+struct qfm_index {
+    uint64_t n = 0;            // text length; the BWT has n + 1 rows
+    uint64_t dollar_row = 0;   // BWT row of $ (stored as code 0 in the rank index)
+    uint64_t C[5] = {0, 0, 0, 0, 0};
+    qr_index* rank = nullptr;  // QuadRank16 over the BWT
+    uint64_t* table = nullptr; // [4^8][2] : [lo, hi) of every 8-mer
+    uint32_t* sa = nullptr;    // suffix array (only with QFM_KEEP_SA)
+    uint32_t* status = nullptr;
+    int device = 0;
+};
+
+namespace qr {
+
+// Everything a search step needs, passed by value to the kernels.
+struct FmView {
+    const uint4* __restrict__ lines;
+    const uint4* __restrict__ supers;  // 4 x uint32 per superblock
+    const uint64_t* __restrict__ table;
+    uint64_t nrows;                    // n + 1
+    uint64_t dollar;
+    uint64_t C[4];
+};
+
+// rank(q, c) over the BWT with the sentinel row counted as code 0.
+__device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, int c) {
+    const uint64_t j = div224(q);
+    const uint32_t slot = (uint32_t)(q - j * kB4) + 32;
+    const uint4* L = v.lines + 4 * j;
+    const uint32_t s = __ldg((const uint32_t*)v.supers + 4 * (j >> 8) + c);
+    const uint4 v0 = ld_line16(L);
+    const bool upper = slot >= 128;
+    const uint4 va = ld_line16(L + (upper ? 2 : 1));
+    uint64_t x[4];
+    if (upper) {
+        const uint4 vb = ld_line16(L + 3);
+        x[0] = lo64(va); x[1] = hi64(va); x[2] = lo64(vb); x[3] = hi64(vb);
+    } else {
+        x[0] = lo64(v0); x[1] = hi64(v0); x[2] = lo64(va); x[3] = hi64(va);
+    }
+    return quad_finish1(s, quad_delta(lo64(v0), hi64(v0), c), x, slot, c);
+}
+
+// LF step of one interval end: C[c] + rank(q, c), where the $ row (stored as
+// code 0) is removed from the count of c = 0 when it lies before q.
+__device__ __forceinline__ uint64_t fm_lf(const FmView& v, uint64_t q, int c) {
+    uint64_t r = fm_rank_stored(v, q, c);
+    if (c == 0 && q > v.dollar) r -= 1;
+    return v.C[c] + r;
+}
+
+int fm_view(const qfm_index* idx, FmView* v);
+
+}  // namespace qr

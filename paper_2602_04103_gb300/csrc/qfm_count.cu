@@ -1,0 +1,239 @@
+// Count-only backward search over the QuadFm index (paper App. E).
+//
+// qfm_count: one persistent launch.  Every warp takes pattern ids from a
+// device work queue (an atomic counter) in chunks of kChunk, keeps one search
+// per lane, and refills a lane as soon as its search ends, so the lanes of a
+// warp stay busy despite uneven pattern lengths and early mismatches.  This is
+// the GPU form of the paper's query_batch: a batch of active searches where
+// finished ones are swapped out and the rest take one rank + LF step per pass.
+//
+// qfm_count_stepwise: the plain form, one launch per search step over every
+// pattern (a table-lookup launch, then max-steps launches).
+#include "qfm_common.cuh"
+#include "quadfm.h"
+
+namespace qr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kChunk = 64;  // pattern ids taken from the queue at once per warp
+
+struct CountArgs {
+    FmView v;
+    const uint8_t* __restrict__ pat;
+    const uint64_t* __restrict__ off;
+    uint64_t m;
+    uint64_t* __restrict__ out;
+    unsigned long long* queue;
+    uint32_t* status;
+};
+
+// Start a search: the interval of the last 8 chars from the table (or the full
+// interval for shorter patterns).  Returns false for a malformed pattern.
+__device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restrict__ p, uint64_t len, uint64_t& lo,
+                                         uint64_t& hi, int64_t& i) {
+    if (len >= (uint64_t)kQfmK) {
+        uint32_t w = 0, badc = 0;
+#pragma unroll
+        for (int d = 0; d < kQfmK; d++) {
+            const uint32_t c = p[len - kQfmK + d];
+            badc |= c;
+            w = (w << 2) | (c & 3);
+        }
+        if (badc > 3) return false;
+        lo = __ldg(v.table + 2 * w);
+        hi = __ldg(v.table + 2 * w + 1);
+        i = (int64_t)len - kQfmK - 1;
+    } else {
+        lo = 0;
+        hi = v.nrows;
+        i = (int64_t)len - 1;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // warp-local pool of pattern ids [pool_next, pool_end)
+    uint64_t pool_next = 0, pool_end = 0;
+    bool drained = false;  // the queue has no ids left for this warp
+    bool active = false;
+    uint64_t id = 0, lo = 0, hi = 0, start = 0;
+    int64_t i = -1;
+    uint32_t bad = 0;
+    while (true) {
+        // ---- refill lanes whose search ended
+        const unsigned need = __ballot_sync(0xffffffffu, !active);
+        if (need && !drained) {
+            const uint32_t cnt = __popc(need);
+            const uint32_t r = __popc(need & lt_mask);
+            const uint64_t avail = pool_end - pool_next;
+            uint64_t base = 0;
+            if (avail < cnt) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(a.queue, (unsigned long long)kChunk);
+                base = __shfl_sync(0xffffffffu, (unsigned long long)b, 0);
+            }
+            if (!active) {
+                id = r < avail ? pool_next + r : base + (r - avail);
+                if (id < a.m) {
+                    start = a.off[id];
+                    const uint64_t end = a.off[id + 1];
+                    if (end < start || !fm_start(a.v, a.pat + start, end - start, lo, hi, i)) {
+                        a.out[id] = 0;  // malformed: offsets decrease or a byte > 3
+                        bad |= kStatusBadSym;
+                    } else {
+                        active = true;
+                    }
+                }
+            }
+            if (avail < cnt) {
+                pool_next = base + (cnt - avail);
+                pool_end = base + kChunk;
+                if (base >= a.m) drained = true;
+            } else {
+                pool_next += cnt;
+            }
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+            if (drained || pool_next >= a.m) break;
+            continue;
+        }
+        // ---- one LF step for every active lane
+        if (active) {
+            if (i >= 0 && lo < hi) {
+                const int c = a.pat[start + i];
+                if (c > 3) {
+                    a.out[id] = 0;
+                    bad |= kStatusBadSym;
+                    active = false;
+                } else {
+                    lo = fm_lf(a.v, lo, c);
+                    hi = fm_lf(a.v, hi, c);
+                    --i;
+                }
+            }
+            if (active && (i < 0 || lo >= hi)) {
+                a.out[id] = hi > lo ? hi - lo : 0;
+                active = false;
+            }
+        }
+    }
+    if (bad) atomicOr(a.status, bad);
+}
+
+// ---- stepwise baseline
+struct StepState {
+    uint64_t lo, hi;
+    int64_t i;  // next pattern index to consume; -2 = finished
+};
+
+__global__ void step_init(CountArgs a, StepState* __restrict__ st, unsigned long long* __restrict__ max_steps) {
+    uint64_t local_max = 0;
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = a.off[k], e = a.off[k + 1];
+        StepState x;
+        if (e < s || !fm_start(a.v, a.pat + s, e - s, x.lo, x.hi, x.i)) {
+            a.out[k] = 0;
+            atomicOr(a.status, kStatusBadSym);
+            x.i = -2;
+        } else {
+            local_max = max(local_max, (uint64_t)(x.i + 1));
+        }
+        st[k] = x;
+    }
+    atomicMax(max_steps, (unsigned long long)local_max);
+}
+
+__global__ void step_once(CountArgs a, StepState* __restrict__ st) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
+        StepState x = st[k];
+        if (x.i == -2) continue;
+        if (x.i >= 0 && x.lo < x.hi) {
+            const int c = a.pat[a.off[k] + x.i];
+            if (c > 3) {
+                a.out[k] = 0;
+                atomicOr(a.status, kStatusBadSym);
+                st[k].i = -2;
+                continue;
+            }
+            x.lo = fm_lf(a.v, x.lo, c);
+            x.hi = fm_lf(a.v, x.hi, c);
+            --x.i;
+        }
+        if (x.i < 0 || x.lo >= x.hi) {
+            a.out[k] = x.hi > x.lo ? x.hi - x.lo : 0;
+            x.i = -2;
+        }
+        st[k] = x;
+    }
+}
+
+unsigned persistent_grid() {
+    static thread_local int per_sm = 0;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, count_persistent, kThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    return (unsigned)(per_sm * device_props().sms);
+}
+
+}  // namespace
+
+int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
+                 unsigned long long* queue, cudaStream_t s) {
+    CountArgs a;
+    fm_view(idx, &a.v);
+    a.pat = pat;
+    a.off = off;
+    a.m = m;
+    a.out = out;
+    a.queue = queue;
+    a.status = idx->status;
+    uint64_t warps_needed = (m + kChunk - 1) / kChunk;
+    uint64_t grid = persistent_grid();
+    const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+    if (grid > blocks_needed) grid = blocks_needed;
+    if (grid == 0) grid = 1;
+    count_persistent<<<(unsigned)grid, kThreads, 0, s>>>(a);
+    QR_CUDA_TRY(cudaGetLastError());
+    return QR_OK;
+}
+
+int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
+                          cudaStream_t s) {
+    CountArgs a;
+    fm_view(idx, &a.v);
+    a.pat = pat;
+    a.off = off;
+    a.m = m;
+    a.out = out;
+    a.queue = nullptr;
+    a.status = idx->status;
+    StepState* st = nullptr;
+    unsigned long long* mx = nullptr;
+    QR_CUDA_TRY(cudaMallocAsync((void**)&st, m * sizeof(StepState), s));
+    cudaError_t e = cudaMallocAsync((void**)&mx, 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 8, s);
+    uint64_t blocks = (m + kThreads - 1) / kThreads;
+    const uint64_t cap = (uint64_t)device_props().sms * 16;
+    if (blocks > cap) blocks = cap;
+    unsigned long long steps = 0;
+    if (e == cudaSuccess) {
+        step_init<<<(unsigned)blocks, kThreads, 0, s>>>(a, st, mx);
+        e = cudaMemcpyAsync(&steps, mx, 8, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (unsigned long long t = 0; e == cudaSuccess && t < steps + 1; t++) {
+        step_once<<<(unsigned)blocks, kThreads, 0, s>>>(a, st);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(st, s);
+    cudaFreeAsync(mx, s);
+    if (e != cudaSuccess) return cuda_fail(e, "qfm_count_stepwise");
+    return QR_OK;
+}
+
+}  // namespace qr

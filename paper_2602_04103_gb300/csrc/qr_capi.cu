@@ -42,7 +42,7 @@ static int tuning_ok(const qr_tuning_t& t) {
     const int k = t.queries_per_thread;
     if (k != 1 && k != 2 && k != 4 && k != 8) return 0;
     if (t.block_threads < 64 || t.block_threads > 512 || (t.block_threads & 31)) return 0;
-    if (t.load_mode != 0 && t.load_mode != 1) return 0;
+    if (t.load_mode < 0 || t.load_mode > 3) return 0;
     if (t.grid_blocks < 0) return 0;
     return 1;
 }
@@ -284,13 +284,15 @@ int qr_free(qr_index* idx) {
     return QR_OK;
 }
 
-int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out,
-                    int queries_per_thread, int block_threads, void* stream) {
+int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed,
+                    uint64_t* out, int queries_per_thread, int block_threads, void* stream) {
     if (bytes != 16 && bytes != 32 && bytes != 64 && bytes != 128) return fail(QR_EINVAL, "probe: bytes");
+    if (load_bytes != 16 && load_bytes != 32) return fail(QR_EINVAL, "probe: load_bytes");
     if (nrec == 0 || !buf || (m > 0 && !out)) return fail(QR_EINVAL, "probe: empty buffer");
     if (((uintptr_t)buf & 15) != 0) return fail(QR_EINVAL, "probe: buf must be 16-byte aligned");
     if (block_threads < 64 || block_threads > 1024 || (block_threads & 31)) return fail(QR_EINVAL, "probe: threads");
-    return launch_probe(buf, nrec, bytes, m, seed, out, queries_per_thread, block_threads, (cudaStream_t)stream);
+    return launch_probe(buf, nrec, bytes, load_bytes, m, seed, out, queries_per_thread, block_threads,
+                        (cudaStream_t)stream);
 }
 
 }  // extern "C"

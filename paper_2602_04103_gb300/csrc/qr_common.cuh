@@ -96,6 +96,17 @@ __device__ __forceinline__ uint8_t ld_stream_u8(const uint8_t* p) {
 __device__ __forceinline__ void st_stream_u64(uint64_t* p, uint64_t v) {
     asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// 32-byte loads (sm_100+ 256-bit vector load): one instruction per sector.
+struct u64x4 {
+    uint64_t a, b, c, d;
+};
+__device__ __forceinline__ u64x4 ld_line32(const uint4* p) {
+    u64x4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.b64 {%0,%1,%2,%3}, [%4];"
+                 : "=l"(v.a), "=l"(v.b), "=l"(v.c), "=l"(v.d)
+                 : "l"(p));
+    return v;
+}
 __device__ __forceinline__ uint64_t lo64(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
 __device__ __forceinline__ uint64_t hi64(uint4 v) { return (uint64_t)v.z | ((uint64_t)v.w << 32); }
 
@@ -207,6 +218,6 @@ int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
 // Launch the rank kernels (no argument checks beyond the mode).
 int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                 int rank4, cudaStream_t s);
-int launch_probe(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out, int k,
-                 int threads, cudaStream_t s);
+int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
+                 int k, int threads, cudaStream_t s);
 }  // namespace qr

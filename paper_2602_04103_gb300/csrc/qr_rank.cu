@@ -71,17 +71,39 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
                 else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + (cv[k] & 3));
             }
             const uint4* L = a.lines + 4 * j;
-            v0[k] = ld_line16(L);
             if (LOAD == 0) {
-                // whole line: all four 16-byte quarters (both 32-byte sectors)
+                // whole line: four 16-byte loads (both 32-byte sectors)
+                v0[k] = ld_line16(L);
                 const uint4 u1 = ld_line16(L + 1), u2 = ld_line16(L + 2), u3 = ld_line16(L + 3);
                 va[k] = upper ? u2 : u1;
                 vb[k] = upper ? u3 : u2;
-            } else {
-                // sectors: lower half = quarters 0, 1 (one sector); upper half =
-                // quarter 0 (deltas) + quarters 2, 3
+            } else if (LOAD == 1) {
+                // needed sectors, 16-byte loads: lower half = quarters 0, 1 (one
+                // sector); upper half = quarter 0 (deltas) + quarters 2, 3
+                v0[k] = ld_line16(L);
                 va[k] = ld_line16(L + (upper ? 2 : 1));
                 vb[k] = upper ? ld_line16(L + 3) : make_uint4(0, 0, 0, 0);
+            } else if (LOAD == 2) {
+                // whole line: two 32-byte loads
+                const u64x4 s0 = ld_line32(L), s1 = ld_line32(L + 2);
+                v0[k] = make_uint4((uint32_t)s0.a, (uint32_t)(s0.a >> 32), (uint32_t)s0.b, (uint32_t)(s0.b >> 32));
+                const uint64_t e0 = upper ? s1.a : s0.c, e1 = upper ? s1.b : s0.d;
+                va[k] = make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                vb[k] = make_uint4((uint32_t)s1.c, (uint32_t)(s1.c >> 32), (uint32_t)s1.d, (uint32_t)(s1.d >> 32));
+            } else {
+                // needed sectors, 32-byte loads: lower half = sector 0; upper half
+                // = sector 1 + the first 16 bytes (deltas)
+                if (upper) {
+                    v0[k] = ld_line16(L);
+                    const u64x4 s1 = ld_line32(L + 2);
+                    va[k] = make_uint4((uint32_t)s1.a, (uint32_t)(s1.a >> 32), (uint32_t)s1.b, (uint32_t)(s1.b >> 32));
+                    vb[k] = make_uint4((uint32_t)s1.c, (uint32_t)(s1.c >> 32), (uint32_t)s1.d, (uint32_t)(s1.d >> 32));
+                } else {
+                    const u64x4 s0 = ld_line32(L);
+                    v0[k] = make_uint4((uint32_t)s0.a, (uint32_t)(s0.a >> 32), (uint32_t)s0.b, (uint32_t)(s0.b >> 32));
+                    va[k] = make_uint4((uint32_t)s0.c, (uint32_t)(s0.c >> 32), (uint32_t)s0.d, (uint32_t)(s0.d >> 32));
+                    vb[k] = make_uint4(0, 0, 0, 0);
+                }
             }
         }
 #pragma unroll
@@ -139,17 +161,24 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
 // ---------------------------------------------------------------- launch table
 using KernelFn = void (*)(RankArgs);
 
+template <int K, int KIND>
+KernelFn pick_load(int load) {
+    switch (load) {
+        case 0: return rank_kernel<K, 0, KIND>;
+        case 1: return rank_kernel<K, 1, KIND>;
+        case 2: return rank_kernel<K, 2, KIND>;
+        case 3: return rank_kernel<K, 3, KIND>;
+        default: return nullptr;
+    }
+}
+
 template <int KIND>
 KernelFn pick(int k, int load) {
-    switch (k * 2 + load) {
-        case 2: return rank_kernel<1, 0, KIND>;
-        case 3: return rank_kernel<1, 1, KIND>;
-        case 4: return rank_kernel<2, 0, KIND>;
-        case 5: return rank_kernel<2, 1, KIND>;
-        case 8: return rank_kernel<4, 0, KIND>;
-        case 9: return rank_kernel<4, 1, KIND>;
-        case 16: return rank_kernel<8, 0, KIND>;
-        case 17: return rank_kernel<8, 1, KIND>;
+    switch (k) {
+        case 1: return pick_load<1, KIND>(load);
+        case 2: return pick_load<2, KIND>(load);
+        case 4: return pick_load<4, KIND>(load);
+        case 8: return pick_load<8, KIND>(load);
         default: return nullptr;
     }
 }
@@ -179,25 +208,34 @@ __device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-template <int K, int V>  // V = 16-byte vectors per record
+template <int K, int V, int W>  // V = 16-byte quarters per record, W = bytes per load (16 or 32)
 __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ buf, uint64_t nrec, uint64_t m,
                                                      uint64_t seed, uint64_t* __restrict__ out) {
     const uint64_t tile = (uint64_t)blockDim.x * K;
+    constexpr int kLoads = W == 32 && V >= 2 ? V / 2 : V;
     for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < m; t0 += (uint64_t)gridDim.x * tile) {
-        uint4 v[K][V];
+        uint64_t v[K][kLoads];
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
             const uint64_t r = mulhi64(probe_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull), nrec);
 #pragma unroll
-            for (int u = 0; u < V; u++) v[k][u] = ld_line16(buf + r * V + u);
+            for (int u = 0; u < kLoads; u++) {
+                if (W == 32 && V >= 2) {
+                    const u64x4 x = ld_line32(buf + r * V + 2 * u);
+                    v[k][u] = x.a ^ x.b ^ x.c ^ x.d;
+                } else {
+                    const uint4 x = ld_line16(buf + r * V + u);
+                    v[k][u] = lo64(x) ^ hi64(x);
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
             uint64_t d = 0;
 #pragma unroll
-            for (int u = 0; u < V; u++) d ^= lo64(v[k][u]) ^ hi64(v[k][u]);
+            for (int u = 0; u < kLoads; u++) d ^= v[k][u];
             if (i < m) st_stream_u64(out + i, d);
         }
     }
@@ -224,12 +262,13 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     return QR_OK;
 }
 
-int launch_probe(const void* buf, uint64_t nrec, int bytes, uint64_t m, uint64_t seed, uint64_t* out, int k,
-                 int threads, cudaStream_t s) {
+int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
+                 int k, int threads, cudaStream_t s) {
     if (m == 0) return QR_OK;
     void (*fn)(const uint4*, uint64_t, uint64_t, uint64_t, uint64_t*) = nullptr;
-#define QR_PROBE_CASE(KK, VV) \
-    if (k == KK && bytes == 16 * VV) fn = probe_kernel<KK, VV>;
+#define QR_PROBE_CASE(KK, VV)                                                            \
+    if (k == KK && bytes == 16 * VV && load_bytes == 16) fn = probe_kernel<KK, VV, 16>; \
+    if (k == KK && bytes == 16 * VV && load_bytes == 32 && VV >= 2) fn = probe_kernel<KK, VV, 32>;
     QR_PROBE_CASE(1, 1) QR_PROBE_CASE(1, 2) QR_PROBE_CASE(1, 4) QR_PROBE_CASE(1, 8)
     QR_PROBE_CASE(2, 1) QR_PROBE_CASE(2, 2) QR_PROBE_CASE(2, 4) QR_PROBE_CASE(2, 8)
     QR_PROBE_CASE(4, 1) QR_PROBE_CASE(4, 2) QR_PROBE_CASE(4, 4) QR_PROBE_CASE(4, 8)

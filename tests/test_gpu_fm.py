@@ -1,0 +1,149 @@
+"""GPU parity of the QuadFm index and counts against the oracle (bit-exact).
+
+The suffix array of T$ is unique, so the GPU's prefix-doubling SA is compared
+row by row with the oracle's comparison sort; the BWT, the $ row, C and the
+8-mer table follow from their definitions (QuadRank paper, App. E); counts
+from the persistent kernel and the per-step baseline are compared with the
+oracle's SA-interval counts and brute-force counts.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_04103_gb300 import synth
+from tests.gpu_util import dev_u64, dev_u8, host_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def build_fm(codes, keep_sa=True):
+    from paper_2602_04103_gb300 import capi
+    return capi.qfm_build(dev_u8(codes), codes.size, capi.QFM_KEEP_SA if keep_sa else 0)
+
+
+def export(idx, n):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    sa = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    bwt = torch.empty(n + 1, dtype=torch.uint8, device="cuda")
+    table = torch.empty(2 * 4 ** 8, dtype=torch.int64, device="cuda")
+    capi.qfm_export(idx, sa, bwt, table)
+    return (sa.cpu().numpy().view(np.uint32).astype(np.uint64), bwt.cpu().numpy(),
+            table.cpu().numpy().view(np.uint64).reshape(-1, 2))
+
+
+def counts(idx, pats, off, stepwise=False):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    m = off.size - 1
+    out = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    dp = dev_u8(pats if pats.size else np.zeros(1, np.uint8))
+    (capi.qfm_count_stepwise if stepwise else capi.qfm_count)(idx, dp, dev_u64(off), out)
+    return host_u64(out)[:m]
+
+
+def check_index(codes):
+    from paper_2602_04103_gb300 import capi
+    n = codes.size
+    idx = build_fm(codes)
+    sa, bwt, table = export(idx, n)
+    want_sa = oracle.suffix_array(codes)
+    assert np.array_equal(sa, want_sa), np.flatnonzero(sa != want_sa)[:5]
+    want_bwt, row = oracle.bwt(codes, want_sa)
+    info = capi.qfm_info(idx)
+    assert info["dollar_row"] == row
+    want_bwt = want_bwt.copy()
+    want_bwt[row] = 0          # the $ row is stored as code 0
+    assert np.array_equal(bwt, want_bwt)
+    assert info["C"] == [1 + int((codes < c).sum()) for c in range(5)]
+    # table: SA interval of every 8-mer
+    for w in range(0, 4 ** 8, 1 if n < 2000 else 97):
+        p = np.array([(w >> (2 * (7 - d))) & 3 for d in range(8)], dtype=np.uint8)
+        assert tuple(table[w]) == oracle.sa_interval(codes, want_sa, p), w
+    return idx, want_sa
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 8, 9, 31, 100, 1000])
+def test_index_small_random(n):
+    rng = np.random.default_rng(n)
+    check_index(rng.integers(0, 4, n).astype(np.uint8))
+
+
+@pytest.mark.parametrize("codes", ["A" * 50, "AC" * 40, "ACGT" * 30, "A" * 30 + "C" + "A" * 30])
+def test_index_repetitive(codes):
+    check_index(np.array(["ACGT".index(ch) for ch in codes], dtype=np.uint8))
+
+
+def test_index_planted_repeats():
+    t = synth.fm_text(11, 200_000, repeat_cover=0.2, len_min=300, len_max=5000, sub_rate=0.02)
+    check_index(t)
+
+
+def test_counts_tiny_exhaustive():
+    # every text of length <= 5 over {A,C}, every pattern of length <= 4 over ACGT
+    pats = [np.array(p, dtype=np.uint8) for L in range(0, 5) for p in itertools.product(range(4), repeat=L)]
+    off = np.concatenate([[0], np.cumsum([p.size for p in pats])]).astype(np.uint64)
+    flat = np.concatenate(pats).astype(np.uint8)
+    for L in range(1, 6):
+        for t in itertools.product([0, 1], repeat=L):
+            t = np.array(t, dtype=np.uint8)
+            idx = build_fm(t, keep_sa=False)
+            want = oracle.count_brute_batch(t, flat, off)
+            assert np.array_equal(counts(idx, flat, off), want), t
+            idx.free()
+
+
+@pytest.mark.parametrize("stepwise", [False, True])
+def test_counts_mid_size(stepwise):
+    n = 1 << 20
+    t = synth.fm_text(21, n)
+    idx = build_fm(t)
+    sa = oracle.suffix_array(t)
+    pats, off = synth.patterns(22, t, 100_000, 1, 150, sub_rate=0.01)
+    want = oracle.count_sa(t, sa, pats, off)
+    got = counts(idx, pats, off, stepwise=stepwise)
+    assert np.array_equal(got, want), np.flatnonzero(got != want)[:5]
+    sample = np.arange(0, 100_000, 997)
+    sub_off = np.concatenate([[0], np.cumsum(np.diff(off.astype(np.int64))[sample])]).astype(np.uint64)
+    sub = np.concatenate([pats[off[k]:off[k + 1]] for k in sample])
+    assert np.array_equal(got[sample], oracle.count_brute_batch(t, sub, sub_off))
+
+
+def test_counts_edge_patterns():
+    from paper_2602_04103_gb300 import capi
+    n = 5000
+    t = synth.fm_text(31, n, repeat_cover=0.3, len_min=100, len_max=400)
+    idx = build_fm(t)
+    sa = oracle.suffix_array(t)
+    pl = [np.zeros(0, np.uint8), t[:1], t[:8], t[:9], t[-8:], t[-9:], t.copy(), np.concatenate([t, [0]]),
+          t[100:107], t[100:108], t[100:109], np.full(20, 3, np.uint8)]
+    off = np.concatenate([[0], np.cumsum([p.size for p in pl])]).astype(np.uint64)
+    flat = np.concatenate(pl).astype(np.uint8)
+    want = oracle.count_sa(t, sa, flat, off)
+    assert want[0] == n + 1 and want[6] == 1 and want[7] == 0
+    for stepwise in (False, True):
+        assert np.array_equal(counts(idx, flat, off, stepwise), want)
+    assert capi.qfm_status(idx) == 0
+    # a byte > 3 gives 0 and the bad-symbol status bit
+    bad = flat.copy()
+    bad[off[3]] = 7
+    got = counts(idx, bad, off)
+    assert got[3] == 0 and np.array_equal(np.delete(got, 3), np.delete(want, 3))
+    assert capi.qfm_status(idx) == capi.QR_EBADSYM
+    # empty batch
+    assert counts(idx, np.zeros(0, np.uint8), np.zeros(1, np.uint64)).size == 0
+
+
+def test_build_rejects_bad_text():
+    from paper_2602_04103_gb300 import capi
+    with pytest.raises(capi.QRError):
+        build_fm(np.array([0, 1, 4, 2], dtype=np.uint8))

@@ -81,8 +81,7 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
 static int check_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                        const char* who) {
     if (!idx) return fail(QR_EINVAL, std::string(who) + ": index is NULL");
-    if (m > 0 && (!off || !out)) return fail(QR_EINVAL, std::string(who) + ": NULL buffer");
-    (void)pat;
+    if (m > 0 && (!pat || !off || !out)) return fail(QR_EINVAL, std::string(who) + ": NULL buffer");
     return QR_OK;
 }
 

@@ -75,6 +75,30 @@ int qfm_count(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, 
 int qfm_count_stepwise(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,
                        uint64_t* out, void* stream);
 
+/*
+ * qfm_count_noalloc -- qfm_count that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they count -- code that runs inside a memory pool or
+ * allocator owned by another framework, under a hard device-memory budget,
+ * or on a latency path where an allocation call is not allowed.
+ * Same arguments, results and status bits as qfm_count; the caller still
+ * passes every input and output buffer.  The kernel's only scratch, its
+ * work-queue counter (16 bytes, for any m), lives in a static 256-byte
+ * device array of the library instead of the stream-ordered pool; every GPU
+ * that loads the library holds that array until the process exits.  A call
+ * whose scratch need exceeded the array would be rejected with QR_EINVAL
+ * (the need is fixed, so valid calls are never rejected).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array
+ * and reset its counter at the start: calls whose executions overlap on the
+ * GPU (different streams, no ordering between them) race on it and must not
+ * be issued; calls ordered on one stream are fine.
+ * Errors: QR_EINVAL (null arguments with m > 0), QR_ECUDA.
+ */
+int qfm_count_noalloc(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,
+                      uint64_t* out, void* stream);
+
 /* Index facts.  Errors: QR_EINVAL. */
 int qfm_info(const qfm_index* idx, qfm_info_t* info);
 

@@ -197,6 +197,7 @@ class qfm_info_t(C.Structure):
 _sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
 _sig("qfm_count", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
+_sig("qfm_count_noalloc", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_info", [vp, C.POINTER(qfm_info_t)])
 _sig("qfm_export", [vp, vp, vp, vp, vp])
 _sig("qfm_rank_index", [vp], vp)
@@ -230,6 +231,13 @@ def qfm_count_stepwise(idx: QFMIndex, patterns, offsets, out, stream=None) -> No
     m = numel(offsets) - 1
     _check(lib.qfm_count_stepwise(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)),
            "qfm_count_stepwise")
+
+
+def qfm_count_noalloc(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:
+    """qfm_count without any device allocation (static scratch; see quadfm.h)."""
+    m = numel(offsets) - 1
+    _check(lib.qfm_count_noalloc(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)),
+           "qfm_count_noalloc")
 
 
 def qfm_info(idx: QFMIndex) -> dict:

@@ -9,6 +9,8 @@
 //
 // qfm_count_stepwise: the plain form, one launch per search step over every
 // pattern (a table-lookup launch, then max-steps launches).
+#include <mutex>
+
 #include "qfm_common.cuh"
 #include "quadfm.h"
 
@@ -237,3 +239,65 @@ int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* of
 }
 
 }  // namespace qr
+
+// ---------------------------------------------------------------------------
+// qfm_count_noalloc: qfm_count for callers that cannot allocate device memory.
+//
+// The persistent kernel's only scratch is its work-queue counter.  qfm_count
+// takes it from the stream-ordered pool; this variant keeps it in the static
+// device array below instead, so a call makes no cudaMalloc, cudaMallocAsync,
+// cudaFree or other allocating call.  The array is part of the library image:
+// every GPU that loads the library holds its 256 bytes until the process
+// exits.  In host code the name g_noalloc_scratch is only a host-side stand-in
+// for the device array, so its device address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[32];  // 256 bytes
+
+namespace qr {
+namespace {
+
+constexpr size_t kNoallocScratchBytes = sizeof(g_noalloc_scratch);
+constexpr size_t kNoallocQueueBytes = 16;  // one work-queue counter (+ padding)
+constexpr int kNoallocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+unsigned long long* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the static scratch on the current device (looked up on
+// the first call per device, with that device current).
+int noalloc_scratch(unsigned long long** out) {
+    int dev = 0;
+    QR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(QR_EINVAL, "qfm_count_noalloc: device ordinal >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "qfm_count_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = (unsigned long long*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return QR_OK;
+}
+
+}  // namespace
+}  // namespace qr
+
+extern "C" int qfm_count_noalloc(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,
+                                 uint64_t* out, void* stream) {
+    using namespace qr;
+    if (!idx) return fail(QR_EINVAL, "qfm_count_noalloc: index is NULL");
+    if (m > 0 && (!patterns || !offsets || !out)) return fail(QR_EINVAL, "qfm_count_noalloc: NULL buffer");
+    if (m == 0) return QR_OK;
+    // the scratch a call needs: one work-queue counter, whatever m is
+    if (kNoallocQueueBytes > kNoallocScratchBytes)
+        return fail(QR_EINVAL, "qfm_count_noalloc: scratch need exceeds the 256-byte static array");
+    unsigned long long* queue = nullptr;
+    int rc = noalloc_scratch(&queue);
+    if (rc != QR_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's counter: start this call's queue at 0
+    QR_CUDA_TRY(cudaMemsetAsync(queue, 0, kNoallocQueueBytes, s));
+    return launch_count(idx, patterns, offsets, m, out, queue, s);
+}

@@ -48,6 +48,11 @@ extern "C" {
 #define QR_EBADSYM 8   /* status bit: some pattern byte was > 3                   */
 
 #define QR_LAYOUT_PAPER 0   /* BiRank16 / QuadRank16 exactly as in the paper      */
+#define QR_LAYOUT_SECTOR 1  /* one self-contained 32-byte sector per query:       */
+                            /* sigma 2 = the paper's BiRank16x2 (two 16-bit deltas */
+                            /* at 1/4 and 3/4 of a 480-bit block, 6.72%), each     */
+                            /* delta at the head of its 32-byte half; sigma 4 =    */
+                            /* four deltas + 96 transposed chars per sector (33%)  */
 
 typedef struct qr_index qr_index;
 
@@ -56,7 +61,8 @@ typedef struct {
     uint64_t n;             /* text length (bits or chars)                           */
     int32_t sigma;          /* 2 or 4                                                */
     int32_t layout;         /* QR_LAYOUT_*                                           */
-    uint64_t block_chars;   /* B = 496 (sigma 2) or B4 = 224 (sigma 4)               */
+    uint64_t block_chars;   /* chars per 64-byte line: 496 / 224 (paper layout),      */
+                            /* 480 / 192 (sector layout) for sigma 2 / 4             */
     uint64_t super_blocks;  /* blocks per superblock: 128 (sigma 2) or 256 (sigma 4) */
     uint64_t nblocks;       /* floor(n / B) + 1 cache lines of 64 bytes              */
     uint64_t nsuper;        /* ceil(nblocks / super_blocks) superblock entries        */
@@ -102,7 +108,12 @@ int qr_abi_version(void);
  */
 int qr_build(const uint64_t* text, uint64_t n, int sigma, int text_on_device, void* stream, qr_index** out);
 
-/* qr_build with an explicit layout (QR_LAYOUT_*). */
+/* qr_build with an explicit layout (QR_LAYOUT_*).  QR_LAYOUT_SECTOR follows the
+ * paper's BiRank16x2 variant (Sec. 3.1: two 16-bit deltas, to 1/4 and 3/4 of
+ * the block, so only a quarter of the line is popcounted); the sigma 4 form
+ * applies the same idea to QuadRank (Sec. 4.1 variants: larger inline values
+ * so that fewer characters are counted).  Every query reads one 32-byte
+ * sector of its line. */
 int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device, int layout, void* stream,
                 qr_index** out);
 
@@ -167,6 +178,34 @@ int qr_copy_layout(const qr_index* idx, void* lines_dst, void* supers_dst, void*
 /* Read the launch tuning / set it (values are validated; QR_EINVAL if not). */
 int qr_get_tuning(const qr_index* idx, qr_tuning_t* t);
 int qr_set_tuning(qr_index* idx, const qr_tuning_t* t);
+
+/*
+ * qr_autotune -- time the rank kernel of this index for every supported
+ * tuning (queries in flight per thread 1/2/4/8, block of 128/256/512 threads,
+ * every load mode of the layout) on the caller's queries, keep the fastest in
+ * the handle and return it in *best (may be NULL).  Timing: CUDA events on
+ * `stream`, best of 3 launches per candidate after one warm-up.
+ *   q        device queries (m of them, m >= 1); they should look like the
+ *            production batch (same size class and distribution).
+ *   mode     0: qr_rank with symbol c; 1: qr_rank_c with c_vec; 2: qr_rank4.
+ *   out      device scratch output: m uint64 (4 m for mode 2).
+ * Synchronises stream.  Errors: QR_EINVAL, QR_ECUDA.  This library's own
+ * addition: the paper tunes by hand per CPU (Sec. 3.1 and 4.1 variants).
+ */
+int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out,
+                void* stream, qr_tuning_t* best);
+
+/*
+ * qr_build_tuned -- build the index in every layout whose space overhead is at
+ * most max_overhead (fraction of the text size, e.g. 0.10), autotune each on
+ * the given queries as qr_autotune does, and return the fastest; the others
+ * are freed.  *layout_out (may be NULL) receives the chosen QR_LAYOUT_*.
+ * Overheads: sigma 2 paper 3.28%, sector 6.72%; sigma 4 paper 14.40%, sector
+ * 33.46%.  Errors: QR_EINVAL (no layout within max_overhead), as qr_build.
+ */
+int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_device, double max_overhead,
+                   const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out, void* stream,
+                   qr_index** idx_out, int* layout_out);
 
 /* Synchronise stream, return the OR of the status bits (QR_ERANGE, QR_EBADSYM,
  * QR_ETIMEOUT; each >= 4) set by queries since the last call, and clear them;

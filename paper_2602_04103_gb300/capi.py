@@ -19,7 +19,7 @@ lib = C.CDLL(str(_SO))
 
 QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA = 0, 1, 2, 3
 QR_ERANGE, QR_EBADSYM, QR_ETIMEOUT = 4, 8, 16
-QR_LAYOUT_PAPER = 0
+QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR = 0, 1
 QFM_KEEP_SA = 1
 
 u64, i32, vp = C.c_uint64, C.c_int, C.c_void_p
@@ -64,6 +64,9 @@ _sig("qr_layout_ptrs", [vp, C.POINTER(vp), C.POINTER(vp)])
 _sig("qr_copy_layout", [vp, vp, vp, vp])
 _sig("qr_get_tuning", [vp, C.POINTER(qr_tuning_t)])
 _sig("qr_set_tuning", [vp, C.POINTER(qr_tuning_t)])
+_sig("qr_autotune", [vp, vp, u64, i32, i32, vp, vp, vp, C.POINTER(qr_tuning_t)])
+_sig("qr_build_tuned", [vp, u64, i32, i32, C.c_double, vp, u64, i32, i32, vp, vp, vp, C.POINTER(vp),
+                        C.POINTER(C.c_int)])
 _sig("qr_status", [vp, vp])
 _sig("qr_free", [vp])
 _sig("qr_probe_gather", [vp, u64, i32, i32, u64, u64, vp, i32, i32, vp])
@@ -173,6 +176,34 @@ def qr_get_tuning(idx: QRIndex) -> dict:
 def qr_set_tuning(idx: QRIndex, queries_per_thread=4, block_threads=256, load_mode=0, grid_blocks=0) -> None:
     t = qr_tuning_t(queries_per_thread, block_threads, load_mode, grid_blocks)
     _check(lib.qr_set_tuning(idx, C.byref(t)), "qr_set_tuning")
+
+
+def _mode_args(c, rank4):
+    if rank4:
+        return 2, 0, None
+    if isinstance(c, (int,)):
+        return 0, c, None
+    return 1, 0, ptr(c)
+
+
+def qr_autotune(idx: QRIndex, q, out, c=1, rank4=False, stream=None) -> dict:
+    """Pick the fastest tuning on these queries (out: device scratch of m, or 4m for rank4)."""
+    mode, ci, cv = _mode_args(c, rank4)
+    t = qr_tuning_t()
+    _check(lib.qr_autotune(idx, ptr(q), numel(q), mode, ci, cv, ptr(out), stream_ptr(stream), C.byref(t)),
+           "qr_autotune")
+    return {k: getattr(t, k) for k, _ in qr_tuning_t._fields_}
+
+
+def qr_build_tuned(text, n: int, sigma: int, q, out, c=1, rank4=False, max_overhead=1.0,
+                   stream=None) -> tuple[QRIndex, int]:
+    """Build every layout within max_overhead, autotune each, return (fastest index, its layout)."""
+    mode, ci, cv = _mode_args(c, rank4)
+    on_dev = int(hasattr(text, "is_cuda") and text.is_cuda)
+    h, lay = vp(), C.c_int()
+    _check(lib.qr_build_tuned(ptr(text), n, sigma, on_dev, max_overhead, ptr(q), numel(q), mode, ci, cv, ptr(out),
+                              stream_ptr(stream), C.byref(h), C.byref(lay)), "qr_build_tuned")
+    return QRIndex(h.value), lay.value
 
 
 def qr_status(idx: QRIndex, stream=None) -> int:

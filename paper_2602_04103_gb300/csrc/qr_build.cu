@@ -232,6 +232,198 @@ __global__ void layout4_kernel(const uint64_t* __restrict__ text, uint64_t n, ui
     }
 }
 
+// ---------------------------------------------------------------- sector layout
+// sigma 2 (BiRank16x2): half h of line j holds data bits [480j + 240h, +240)
+// at half bits 16..255 and its delta in bits 0..15.
+struct Half2 {
+    uint64_t w[4];
+    uint32_t cnt, quarter;  // ones in the 240 bits / in their first 120 bits
+};
+
+__device__ __forceinline__ Half2 make_half2(const uint64_t* __restrict__ t, uint64_t n, uint64_t base) {
+    Half2 H;
+    H.w[0] = bits64(t, n, base) << 16;
+    H.w[1] = bits64(t, n, base + 48);
+    H.w[2] = bits64(t, n, base + 112);
+    H.w[3] = bits64(t, n, base + 176);
+    H.quarter = popc64(H.w[0]) + popc64(H.w[1]) + popc64(H.w[2] & 0xFFull);
+    H.cnt = popc64(H.w[0]) + popc64(H.w[1]) + popc64(H.w[2]) + popc64(H.w[3]);
+    return H;
+}
+
+__global__ void count2s_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               uint64_t* __restrict__ super_cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t sum = 0;
+        for (int r = 0; r < (int)(kSuper2 / 32); r++) {
+            const uint64_t j = i * kSuper2 + r * 32 + lane;
+            if (j < nblocks) sum += make_half2(text, n, j * kB2s).cnt + make_half2(text, n, j * kB2s + kHalf2s).cnt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) super_cnt[i] = sum;
+    }
+}
+
+__global__ void layout2s_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                                const uint64_t* __restrict__ super_base, uint4* __restrict__ lines,
+                                uint32_t* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        const uint64_t base = super_base[i];
+        const uint64_t s = base >> kShift2;
+        if (lane == 0) supers[i] = (uint32_t)s;
+        uint64_t running = base - (s << kShift2);
+        for (int r = 0; r < (int)(kSuper2 / 32); r++) {
+            const uint64_t j = i * kSuper2 + r * 32 + lane;
+            const bool live = j < nblocks;
+            Half2 h0, h1;
+            if (live) {
+                h0 = make_half2(text, n, j * kB2s);
+                h1 = make_half2(text, n, j * kB2s + kHalf2s);
+            }
+            const uint32_t v = live ? h0.cnt + h1.cnt : 0;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (live) {
+                const uint64_t before = running + (incl - v);  // rank(jB) - 2^11 s_i
+                h0.w[0] |= before + h0.quarter;                // rank(jB + 120) - 2^11 s_i
+                h1.w[0] |= before + h0.cnt + h1.quarter;       // rank(jB + 360) - 2^11 s_i
+                uint4* dst = lines + 4 * j;
+                dst[0] = make_uint4((uint32_t)h0.w[0], (uint32_t)(h0.w[0] >> 32), (uint32_t)h0.w[1],
+                                    (uint32_t)(h0.w[1] >> 32));
+                dst[1] = make_uint4((uint32_t)h0.w[2], (uint32_t)(h0.w[2] >> 32), (uint32_t)h0.w[3],
+                                    (uint32_t)(h0.w[3] >> 32));
+                dst[2] = make_uint4((uint32_t)h1.w[0], (uint32_t)(h1.w[0] >> 32), (uint32_t)h1.w[1],
+                                    (uint32_t)(h1.w[1] >> 32));
+                dst[3] = make_uint4((uint32_t)h1.w[2], (uint32_t)(h1.w[2] >> 32), (uint32_t)h1.w[3],
+                                    (uint32_t)(h1.w[3] >> 32));
+            }
+            running += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+// sigma 4 sector layout: half h of line j holds chars [192j + 96h, +96).
+struct Half4 {
+    uint64_t w[4];     // w[0] (deltas) left 0 here
+    uint32_t cnt[4];   // per-symbol count of the 96 chars
+    uint32_t mid[4];   // per-symbol count of the first 48 chars
+};
+
+__device__ __forceinline__ Half4 make_half4(const uint64_t* __restrict__ t, uint64_t n, uint64_t c0) {
+    Half4 H;
+    const uint64_t nbits = 2 * n;
+    const uint64_t x0 = bits64(t, nbits, 2 * c0), x1 = bits64(t, nbits, 2 * c0 + 64), x2 = bits64(t, nbits, 2 * c0 + 128);
+    const uint64_t LA = (uint64_t)even_bits(x0) | ((uint64_t)even_bits(x1) << 32);
+    const uint64_t HA = (uint64_t)even_bits(x0 >> 1) | ((uint64_t)even_bits(x1 >> 1) << 32);
+    const uint64_t LB = even_bits(x2), HB = even_bits(x2 >> 1);
+    H.w[0] = 0;
+    H.w[1] = ~LA;
+    H.w[2] = ~HA;
+    H.w[3] = (~LB & 0xFFFFFFFFull) | ((~HB & 0xFFFFFFFFull) << 32);
+    uint32_t c[4] = {0, 0, 0, 0};
+    count_group(LA, HA, 0x0000FFFFFFFFFFFFull, c);  // chars 0..47
+#pragma unroll
+    for (int k = 0; k < 4; k++) H.mid[k] = c[k];
+    count_group(LA, HA, 0xFFFF000000000000ull, c);  // chars 48..63
+    count_group(LB, HB, 0x00000000FFFFFFFFull, c);  // chars 64..95
+#pragma unroll
+    for (int k = 0; k < 4; k++) H.cnt[k] = c[k];
+    return H;
+}
+
+__global__ void count4s_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               uint64_t* __restrict__ super_cnt /* [4][nsuper] */) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t sum[4] = {0, 0, 0, 0};
+        for (int r = 0; r < (int)(kSuper4 / 32); r++) {
+            const uint64_t j = i * kSuper4 + r * 32 + lane;
+            if (j < nblocks) {
+                const Half4 a = make_half4(text, n, j * kB4s), b = make_half4(text, n, j * kB4s + kHalf4s);
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum[c] += a.cnt[c] + b.cnt[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+            if (lane == 0) super_cnt[c * nsuper + i] = sum[c];
+        }
+    }
+}
+
+__global__ void layout4s_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                                const uint64_t* __restrict__ super_base, uint4* __restrict__ lines,
+                                uint4* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t running[4];
+        uint32_t s[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint64_t base = super_base[c * nsuper + i];
+            s[c] = (uint32_t)(base >> kShift4);
+            running[c] = base - ((uint64_t)s[c] << kShift4);
+        }
+        if (lane == 0) supers[i] = make_uint4(s[0], s[1], s[2], s[3]);
+        for (int r = 0; r < (int)(kSuper4 / 32); r++) {
+            const uint64_t j = i * kSuper4 + r * 32 + lane;
+            const bool live = j < nblocks;
+            Half4 h0, h1;
+            if (live) {
+                h0 = make_half4(text, n, j * kB4s);
+                h1 = make_half4(text, n, j * kB4s + kHalf4s);
+            }
+            uint64_t d0 = 0, d1 = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const uint32_t v = live ? h0.cnt[c] + h1.cnt[c] : 0;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (live) {
+                    const uint64_t before = running[c] + (incl - v);          // rank(jB, c) - 2^13 s_{i,c}
+                    d0 |= (before + h0.mid[c]) << (16 * c);                   // rank(jB + 48, c) - ...
+                    d1 |= (before + h0.cnt[c] + h1.mid[c]) << (16 * c);       // rank(jB + 144, c) - ...
+                }
+                running[c] += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (live) {
+                h0.w[0] = d0;
+                h1.w[0] = d1;
+                uint4* dst = lines + 4 * j;
+                dst[0] = make_uint4((uint32_t)h0.w[0], (uint32_t)(h0.w[0] >> 32), (uint32_t)h0.w[1],
+                                    (uint32_t)(h0.w[1] >> 32));
+                dst[1] = make_uint4((uint32_t)h0.w[2], (uint32_t)(h0.w[2] >> 32), (uint32_t)h0.w[3],
+                                    (uint32_t)(h0.w[3] >> 32));
+                dst[2] = make_uint4((uint32_t)h1.w[0], (uint32_t)(h1.w[0] >> 32), (uint32_t)h1.w[1],
+                                    (uint32_t)(h1.w[1] >> 32));
+                dst[3] = make_uint4((uint32_t)h1.w[2], (uint32_t)(h1.w[2] >> 32), (uint32_t)h1.w[3],
+                                    (uint32_t)(h1.w[3] >> 32));
+            }
+        }
+    }
+}
+
 unsigned grid_for_warps(uint64_t nwarps) {
     uint64_t blocks = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const uint64_t cap = (uint64_t)device_props().sms * 64;
@@ -256,17 +448,26 @@ int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
     const unsigned grid = grid_for_warps(nsuper);
     const unsigned threads = 32 * kWarpsPerBlock;
     int rc = QR_OK;
+    const bool sector = idx->layout == QR_LAYOUT_SECTOR;
     if (idx->sigma == 2) {
-        count2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        if (sector) count2s_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        else count2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
         rc = exclusive_scan_u64(cnt, base, nsuper, s);
-        if (rc == QR_OK)
+        if (rc == QR_OK && sector)
+            layout2s_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                     (uint32_t*)idx->supers);
+        else if (rc == QR_OK)
             layout2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
                                                     (uint32_t*)idx->supers);
     } else {
-        count4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        if (sector) count4s_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+        else count4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
         for (int c = 0; c < 4 && rc == QR_OK; c++)
             rc = exclusive_scan_u64(cnt + c * nsuper, base + c * nsuper, nsuper, s);
-        if (rc == QR_OK)
+        if (rc == QR_OK && sector)
+            layout4s_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                     (uint4*)idx->supers);
+        else if (rc == QR_OK)
             layout4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
                                                     (uint4*)idx->supers);
     }

@@ -75,7 +75,7 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     if (!out) return fail(QR_EINVAL, "qr_build: out is NULL");
     *out = nullptr;
     if (sigma != 2 && sigma != 4) return fail(QR_EINVAL, "qr_build: sigma must be 2 or 4");
-    if (layout != QR_LAYOUT_PAPER) return fail(QR_EINVAL, "qr_build: unknown layout");
+    if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR) return fail(QR_EINVAL, "qr_build: unknown layout");
     if (sigma == 2 && n >= (1ull << 43)) return fail(QR_EINVAL, "qr_build: sigma 2 needs n < 2^43");
     if (sigma == 4 && n >= (1ull << 45)) return fail(QR_EINVAL, "qr_build: sigma 4 needs n < 2^45");
     if (!text && n > 0) return fail(QR_EINVAL, "qr_build: text is NULL");
@@ -85,7 +85,8 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     idx->sigma = sigma;
     idx->layout = layout;
     idx->n = n;
-    const uint64_t B = sigma == 2 ? kB2 : kB4;
+    const bool sector = layout == QR_LAYOUT_SECTOR;
+    const uint64_t B = sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
     const uint64_t per = sigma == 2 ? kSuper2 : kSuper4;
     idx->nblocks = n / B + 1;
     idx->nsuper = (idx->nblocks + per - 1) / per;
@@ -227,7 +228,8 @@ int qr_info(const qr_index* idx, qr_info_t* info) {
     info->n = idx->n;
     info->sigma = idx->sigma;
     info->layout = idx->layout;
-    info->block_chars = idx->sigma == 2 ? kB2 : kB4;
+    const bool sector = idx->layout == QR_LAYOUT_SECTOR;
+    info->block_chars = idx->sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
     info->super_blocks = idx->sigma == 2 ? kSuper2 : kSuper4;
     info->nblocks = idx->nblocks;
     info->nsuper = idx->nsuper;
@@ -264,6 +266,126 @@ int qr_set_tuning(qr_index* idx, const qr_tuning_t* t) {
     if (!idx || !t) return fail(QR_EINVAL, "qr_set_tuning: NULL argument");
     if (!tuning_ok(*t)) return fail(QR_EINVAL, "qr_set_tuning: invalid tuning");
     idx->tune = *t;
+    return QR_OK;
+}
+
+static int run_mode(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* cv, uint64_t* out,
+                    cudaStream_t s) {
+    if (mode == 0) return launch_rank(idx, q, nullptr, c, m, out, 0, s);
+    if (mode == 1) return launch_rank(idx, q, cv, 0, m, out, 0, s);
+    return launch_rank(idx, q, nullptr, 0, m, out, 1, s);
+}
+
+int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out,
+                void* stream, qr_tuning_t* best) {
+    if (!idx || !q || !out || m == 0) return fail(QR_EINVAL, "qr_autotune: NULL argument or m = 0");
+    if (mode < 0 || mode > 2) return fail(QR_EINVAL, "qr_autotune: mode must be 0, 1 or 2");
+    if (mode == 0 && (c < 0 || c >= idx->sigma)) return fail(QR_EINVAL, "qr_autotune: symbol out of range");
+    if (mode == 1 && !c_vec) return fail(QR_EINVAL, "qr_autotune: c_vec is NULL");
+    if (mode == 2 && idx->sigma != 4) return fail(QR_EINVAL, "qr_autotune: rank4 needs sigma 4");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    QR_CUDA_TRY(cudaEventCreate(&e0));
+    QR_CUDA_TRY(cudaEventCreate(&e1));
+    const qr_tuning_t saved = idx->tune;
+    qr_tuning_t win = saved;
+    float win_ms = 1e30f;
+    const int ks[] = {1, 2, 4, 8}, ths[] = {128, 256, 512};
+    const int nload = idx->layout == QR_LAYOUT_SECTOR ? 1 : 4;
+    int rc = QR_OK;
+    for (int li = 0; li < nload && rc == QR_OK; li++)
+        for (int k : ks)
+            for (int th : ths) {
+                idx->tune = qr_tuning_t{k, th, li, 0};
+                rc = run_mode(idx, q, m, mode, c, c_vec, out, s);  // warm-up
+                float bestk = 1e30f;
+                for (int r = 0; r < 3 && rc == QR_OK; r++) {
+                    cudaEventRecord(e0, s);
+                    rc = run_mode(idx, q, m, mode, c, c_vec, out, s);
+                    cudaEventRecord(e1, s);
+                    cudaError_t e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) rc = cuda_fail(e, "qr_autotune: timing");
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < bestk) bestk = ms;
+                }
+                if (rc != QR_OK) break;
+                if (bestk < win_ms) {
+                    win_ms = bestk;
+                    win = idx->tune;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    idx->tune = rc == QR_OK ? win : saved;
+    if (best) *best = idx->tune;
+    return rc;
+}
+
+static double layout_overhead(int sigma, int layout, uint64_t n) {
+    const bool sector = layout == QR_LAYOUT_SECTOR;
+    const uint64_t B = sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
+    const uint64_t per = sigma == 2 ? kSuper2 : kSuper4;
+    const uint64_t nb = n / B + 1, ns = (nb + per - 1) / per;
+    const double bytes = 64.0 * nb + (sigma == 2 ? 4.0 : 16.0) * ns;
+    const double text = sigma == 2 ? n / 8.0 : n / 4.0;
+    return n ? bytes / text - 1.0 : 0.0;
+}
+
+int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_device, double max_overhead,
+                   const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out, void* stream,
+                   qr_index** idx_out, int* layout_out) {
+    if (!idx_out) return fail(QR_EINVAL, "qr_build_tuned: idx_out is NULL");
+    *idx_out = nullptr;
+    qr_index* best = nullptr;
+    int best_layout = -1;
+    float best_ms = 1e30f;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR}) {
+        if (sigma == 2 || sigma == 4) {
+            if (layout_overhead(sigma, layout, n < 4096 ? 1u << 30 : n) > max_overhead) continue;
+        }
+        qr_index* idx = nullptr;
+        int rc = qr_build_ex(text, n, sigma, text_on_device, layout, stream, &idx);
+        if (rc != QR_OK) {
+            if (best) qr_free(best);
+            return rc;
+        }
+        qr_tuning_t t;
+        rc = qr_autotune(idx, q, m, mode, c, c_vec, out, stream, &t);
+        if (rc != QR_OK) {
+            qr_free(idx);
+            if (best) qr_free(best);
+            return rc;
+        }
+        // time the tuned kernel once more for the comparison across layouts
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float ms = 1e30f;
+        for (int r = 0; r < 3; r++) {
+            cudaEventRecord(e0, s);
+            rc = run_mode(idx, q, m, mode, c, c_vec, out, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float x = 0;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (x < ms) ms = x;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (ms < best_ms) {
+            if (best) qr_free(best);
+            best = idx;
+            best_ms = ms;
+            best_layout = layout;
+        } else {
+            qr_free(idx);
+        }
+    }
+    if (!best) return fail(QR_EINVAL, "qr_build_tuned: no layout within max_overhead");
+    *idx_out = best;
+    if (layout_out) *layout_out = best_layout;
     return QR_OK;
 }
 

@@ -39,6 +39,20 @@ constexpr uint64_t kSuper4 = 256;
 constexpr uint64_t kMid4 = 96;
 constexpr int kShift4 = 13;
 
+// Sector layout (QR_LAYOUT_SECTOR): each 32-byte half of a line is
+// self-contained.  sigma 2 (the paper's BiRank16x2, Sec. 3.1): a half holds a
+// 16-bit delta + 240 data bits, a block (line) B = 480 bits, the delta points
+// to data offset 120 of its half (1/4 and 3/4 of the block).  sigma 4: a half
+// holds four 16-bit deltas + 96 chars (transposed: ~low bits of chars 0..63,
+// ~high bits of chars 0..63, then ~low | ~high << 32 of chars 64..95), a line
+// holds 192 chars, the deltas point to char 48 of the half.
+constexpr uint64_t kB2s = 480;
+constexpr uint64_t kHalf2s = 240;
+constexpr uint64_t kMid2s = 120;
+constexpr uint64_t kB4s = 192;
+constexpr uint64_t kHalf4s = 96;
+constexpr uint64_t kMid4s = 48;
+
 // Status bits written by kernels (same values as the QR_E* status codes).
 constexpr uint32_t kStatusRange = QR_ERANGE;
 constexpr uint32_t kStatusBadSym = QR_EBADSYM;
@@ -62,6 +76,11 @@ __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 }
 __host__ __device__ __forceinline__ uint64_t div496(uint64_t q) { return mulhi64(q >> 4, kMagic31) >> 4; }
 __host__ __device__ __forceinline__ uint64_t div224(uint64_t q) { return mulhi64(q >> 5, kMagic7) >> 2; }
+// 480 = 32 * 15 and 192 = 64 * 3, same method (error terms 7 and 1).
+constexpr uint64_t kMagic15 = 0x8888888888888889ull;  // ceil(2^67 / 15)
+constexpr uint64_t kMagic3 = 0xAAAAAAAAAAAAAAABull;   // ceil(2^65 / 3)
+__host__ __device__ __forceinline__ uint64_t div480(uint64_t q) { return mulhi64(q >> 5, kMagic15) >> 3; }
+__host__ __device__ __forceinline__ uint64_t div192(uint64_t q) { return mulhi64(q >> 6, kMagic3) >> 1; }
 
 // ---------------------------------------------------------------- bit helpers
 __host__ __device__ __forceinline__ uint64_t low_mask(uint32_t nb) {  // nb in [0, 64]
@@ -181,6 +200,56 @@ __device__ __forceinline__ void quad_finish4(const uint32_t s[4], uint64_t w0, u
     for (int c = 0; c < 4; c++) {
         uint64_t mid = ((uint64_t)s[c] << kShift4) + quad_delta(w0, w1, c);
         r[c] = upper ? mid + n[c] : mid - n[c];
+    }
+}
+
+// ---------------------------------------------------------------- sector layout queries
+// Mask of bits [a, b) inside 64-bit word k of a bit string (0 <= a <= b).
+__device__ __forceinline__ uint64_t range_mask(int32_t a, int32_t b, int k) {
+    return low_mask(clamp64(b - 64 * k)) & ~low_mask(clamp64(a - 64 * k));
+}
+// BiRank16x2 half-line: W = the 4 words of the query's 32-byte half, r = data
+// offset inside the half (0..239).  Data offset d sits at half bit 16 + d; the
+// delta counts the ones before data offset 120 of the half.
+__device__ __forceinline__ uint64_t birank_sector_finish(uint64_t s, const u64x4& W, uint32_t r) {
+    const bool upper = r >= kMid2s;
+    const int32_t a = upper ? (int32_t)(16 + kMid2s) : (int32_t)(16 + r);
+    const int32_t b = upper ? (int32_t)(16 + r) : (int32_t)(16 + kMid2s);
+    const uint32_t cnt = popc64(W.a & range_mask(a, b, 0)) + popc64(W.b & range_mask(a, b, 1)) +
+                         popc64(W.c & range_mask(a, b, 2)) + popc64(W.d & range_mask(a, b, 3));
+    const uint64_t mid = (s << kShift2) + (W.a & 0xFFFFull);
+    return upper ? mid + cnt : mid - cnt;
+}
+// QuadRank sector: chars [a, b) of the half, as masks of group A (chars 0..63,
+// words b/c) and group B (chars 64..95, low/high 32-bit halves of word d).
+__device__ __forceinline__ void quad_sector_range(uint32_t r, int32_t& a, int32_t& b) {
+    const bool upper = r >= kMid4s;
+    a = upper ? (int32_t)kMid4s : (int32_t)r;
+    b = upper ? (int32_t)r : (int32_t)kMid4s;
+}
+__device__ __forceinline__ uint64_t quad_sector_finish1(uint64_t s_c, const u64x4& W, uint32_t r, int c) {
+    int32_t a, b;
+    quad_sector_range(r, a, b);
+    const uint64_t mA = range_mask(a, b, 0), mB = range_mask(a, b, 1) & 0xFFFFFFFFull;
+    const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
+    const uint32_t cnt = popc64((W.b ^ cl) & (W.c ^ ch) & mA) + popc64((W.d ^ cl) & ((W.d >> 32) ^ ch) & mB);
+    const uint64_t mid = (s_c << kShift4) + ((W.a >> (16 * c)) & 0xFFFFull);
+    return r >= kMid4s ? mid + cnt : mid - cnt;
+}
+__device__ __forceinline__ void quad_sector_finish4(const uint32_t s[4], const u64x4& W, uint32_t r, uint64_t out[4]) {
+    int32_t a, b;
+    quad_sector_range(r, a, b);
+    const uint64_t mA = range_mask(a, b, 0), mB = range_mask(a, b, 1) & 0xFFFFFFFFull;
+    const uint64_t LA = ~W.b & mA, HA = ~W.c & mA, LB = ~W.d & mB, HB = (~W.d >> 32) & mB;
+    const uint32_t n3 = popc64(LA & HA) + popc64(LB & HB);
+    const uint32_t nl = popc64(LA) + popc64(LB), nh = popc64(HA) + popc64(HB);
+    const uint32_t nm = (uint32_t)(b - a);
+    const uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+    const bool upper = r >= kMid4s;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const uint64_t mid = ((uint64_t)s[c] << kShift4) + ((W.a >> (16 * c)) & 0xFFFFull);
+        out[c] = upper ? mid + n[c] : mid - n[c];
     }
 }
 

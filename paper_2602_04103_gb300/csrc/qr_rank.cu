@@ -158,6 +158,91 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
     if (bad_flags) atomicOr(a.status, bad_flags);
 }
 
+// Sector layout (QR_LAYOUT_SECTOR): one 32-byte load per query -- the half of
+// the line that holds both the query's bits and the delta to their middle.
+template <int K, int KIND>
+__global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
+    constexpr bool kQuad = KIND >= kQuadScalar;
+    const uint64_t tile = (uint64_t)blockDim.x * K;
+    uint32_t bad_flags = 0;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < a.m; t0 += (uint64_t)gridDim.x * tile) {
+        uint64_t qv[K];
+        int cv[K];
+        bool live[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            live[k] = i < a.m;
+            qv[k] = live[k] ? ld_stream_u64(a.q + i) : 0;
+            if (KIND == kBiVec || KIND == kQuadVec) cv[k] = live[k] ? (int)ld_stream_u8(a.cvec + i) : 0;
+            else cv[k] = a.c;
+        }
+        u64x4 W[K];
+        uint32_t s1[K];
+        uint4 s4[K];
+        uint32_t r[K];  // offset inside the half: data bit (sigma 2) or char (sigma 4)
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t qq = qv[k] <= a.n ? qv[k] : 0;
+            uint64_t j;
+            uint32_t h;
+            if (!kQuad) {
+                j = div480(qq);
+                const uint32_t p = (uint32_t)(qq - j * kB2s);
+                h = p >= kHalf2s;
+                r[k] = p - h * (uint32_t)kHalf2s;
+                s1[k] = __ldg((const uint32_t*)a.supers + (j >> 7));
+            } else {
+                j = div192(qq);
+                const uint32_t d = (uint32_t)(qq - j * kB4s);
+                h = d >= kHalf4s;
+                r[k] = d - h * (uint32_t)kHalf4s;
+                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
+                else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + (cv[k] & 3));
+            }
+            W[k] = ld_line32(a.lines + 4 * j + 2 * h);
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            const bool range_bad = qv[k] > a.n;
+            if (!kQuad) {
+                const uint64_t r1 = birank_sector_finish(s1[k], W[k], r[k]);
+                const int c = cv[k];
+                const bool sym_bad = (unsigned)c > 1u;
+                uint64_t res = c == 1 ? r1 : qv[k] - r1;
+                if (range_bad || sym_bad) res = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, res);
+                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            } else if (KIND == kQuad4) {
+                const uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
+                uint64_t res[4];
+                quad_sector_finish4(s, W[k], r[k], res);
+                if (range_bad) res[0] = res[1] = res[2] = res[3] = ~0ull;
+                if (live[k]) {
+                    uint64_t* o = a.out + 4 * i;
+                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o), "l"(res[0]), "l"(res[1]) : "memory");
+                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o + 2), "l"(res[2]), "l"(res[3])
+                                 : "memory");
+                    bad_flags |= range_bad ? kStatusRange : 0u;
+                }
+            } else {
+                const int c = cv[k];
+                const bool sym_bad = (unsigned)c > 3u;
+                uint64_t res = quad_sector_finish1(s1[k], W[k], r[k], c & 3);
+                if (range_bad || sym_bad) res = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, res);
+                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            }
+        }
+    }
+    if (bad_flags) atomicOr(a.status, bad_flags);
+}
+
 // ---------------------------------------------------------------- launch table
 using KernelFn = void (*)(RankArgs);
 
@@ -183,7 +268,28 @@ KernelFn pick(int k, int load) {
     }
 }
 
-KernelFn pick_kind(int kind, int k, int load) {
+template <int KIND>
+KernelFn pick_sector(int k) {
+    switch (k) {
+        case 1: return rank_sector_kernel<1, KIND>;
+        case 2: return rank_sector_kernel<2, KIND>;
+        case 4: return rank_sector_kernel<4, KIND>;
+        case 8: return rank_sector_kernel<8, KIND>;
+        default: return nullptr;
+    }
+}
+
+KernelFn pick_kind(int kind, int k, int load, bool sector) {
+    if (sector) {
+        switch (kind) {
+            case kBiScalar: return pick_sector<kBiScalar>(k);
+            case kBiVec: return pick_sector<kBiVec>(k);
+            case kQuadScalar: return pick_sector<kQuadScalar>(k);
+            case kQuadVec: return pick_sector<kQuadVec>(k);
+            case kQuad4: return pick_sector<kQuad4>(k);
+            default: return nullptr;
+        }
+    }
     switch (kind) {
         case kBiScalar: return pick<kBiScalar>(k, load);
         case kBiVec: return pick<kBiVec>(k, load);
@@ -250,7 +356,7 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     if (idx->sigma == 2) kind = cvec ? kBiVec : kBiScalar;
     else kind = rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
     const qr_tuning_t& t = idx->tune;
-    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode);
+    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR);
     if (!fn) return fail(QR_EINVAL, "no rank kernel for this tuning");
     RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status};
     const uint64_t tiles = (m + (uint64_t)t.block_threads * t.queries_per_thread - 1) /

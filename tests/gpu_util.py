@@ -17,9 +17,9 @@ def host_u64(t) -> np.ndarray:
     return t.cpu().numpy().view(np.uint64)
 
 
-def build(text_words: np.ndarray, n: int, sigma: int):
+def build(text_words: np.ndarray, n: int, sigma: int, layout: int = 0):
     from paper_2602_04103_gb300 import capi
-    return capi.qr_build(dev_u64(text_words), n, sigma)
+    return capi.qr_build(dev_u64(text_words), n, sigma, layout=layout)
 
 
 def rank(idx, q: np.ndarray, c):

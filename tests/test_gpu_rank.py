@@ -19,6 +19,8 @@ from tests.gpu_util import build, dev_u64, dev_u8, host_u64, rank, rank4
 pytestmark = pytest.mark.gpu
 
 B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
+B2S, S2S, B4S, S4S = 480, 480 * 128, 192, 192 * 256
+LAYOUTS = [0, 1]   # QR_LAYOUT_PAPER (BiRank16 / QuadRank16), QR_LAYOUT_SECTOR
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,8 +30,8 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def check_bits(words, n, q=None, cs=(0, 1)):
-    idx = build(words, n, 2)
+def check_bits(words, n, q=None, cs=(0, 1), layout=0):
+    idx = build(words, n, 2, layout)
     q = np.arange(n + 1, dtype=np.uint64) if q is None else q
     for c in cs:
         want, rc = oracle.rank(words, n, 2, q, c)
@@ -39,8 +41,8 @@ def check_bits(words, n, q=None, cs=(0, 1)):
     return idx
 
 
-def check_dna(words, n, q=None):
-    idx = build(words, n, 4)
+def check_dna(words, n, q=None, layout=0):
+    idx = build(words, n, 4, layout)
     q = np.arange(n + 1, dtype=np.uint64) if q is None else q
     w4, rc = oracle.rank4(words, n, q)
     assert rc == 0
@@ -52,42 +54,49 @@ def check_dna(words, n, q=None):
     return idx
 
 
-def test_tiny_exhaustive_bits():
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_tiny_exhaustive_bits(layout):
     for L in range(0, 11):
         for bits in itertools.product([0, 1], repeat=L):
-            check_bits(synth.pack_bits(np.array(bits, dtype=np.uint8)), L)
+            check_bits(synth.pack_bits(np.array(bits, dtype=np.uint8)), L, layout=layout)
 
 
-def test_tiny_exhaustive_dna():
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_tiny_exhaustive_dna(layout):
     for L in range(0, 6):
         for codes in itertools.product(range(4), repeat=L):
-            check_dna(synth.pack2(np.array(codes, dtype=np.uint8)), L)
+            check_dna(synth.pack2(np.array(codes, dtype=np.uint8)), L, layout=layout)
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("p", [0.5, 0.01, 0.99])
-def test_multi_superblock_bits_every_q(p):
+def test_multi_superblock_bits_every_q(p, layout):
     n = 3 * S2 + 1234
     words = synth.bits(synth.base_seed(1) + int(p * 100), n, p)
-    check_bits(words, n)
+    check_bits(words, n, layout=layout)
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", ["uniform", "gc_runs"])
-def test_multi_superblock_dna_every_q(kind):
+def test_multi_superblock_dna_every_q(kind, layout):
     n = 3 * S4 + 777
     words = synth.dna_uniform(5, n) if kind == "uniform" else synth.dna_gc_runs(6, n, 0.4, 0.05, 10, 1000)
-    check_dna(words, n)
+    check_dna(words, n, layout=layout)
 
 
-@pytest.mark.parametrize("n", [0, 1, 63, 64, 239, 240, 241, 255, 256, 495, 496, 497, 991, 992, 993,
-                               S2 - 1, S2, S2 + 1, 2 * S2, 2 * S2 + 240])
+@pytest.mark.parametrize("n", [0, 1, 63, 64, 119, 120, 121, 239, 240, 241, 255, 256, 359, 360, 361, 479, 480,
+                               481, 495, 496, 497, 991, 992, 993, S2S - 1, S2S, S2S + 1, S2 - 1, S2, S2 + 1,
+                               2 * S2, 2 * S2 + 240])
 def test_edge_lengths_bits(n):
-    check_bits(synth.bits(n + 3, n, 0.5), n)
+    for layout in LAYOUTS:
+        check_bits(synth.bits(n + 3, n, 0.5), n, layout=layout)
 
 
-@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 95, 96, 97, 127, 128, 223, 224, 225, 447, 448,
-                               S4 - 1, S4, S4 + 1, 2 * S4 + 96])
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 47, 48, 49, 95, 96, 97, 127, 128, 143, 144, 145, 191, 192, 193,
+                               223, 224, 225, 447, 448, S4S - 1, S4S, S4S + 1, S4 - 1, S4, S4 + 1, 2 * S4 + 96])
 def test_edge_lengths_dna(n):
-    check_dna(synth.dna_uniform(n + 5, n), n)
+    for layout in LAYOUTS:
+        check_dna(synth.dna_uniform(n + 5, n), n, layout=layout)
 
 
 def read_layout(idx, sigma):
@@ -233,16 +242,16 @@ def test_out_of_range_and_bad_symbols():
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
-@pytest.mark.parametrize("load", [0, 1])
+@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 1)])
 @pytest.mark.parametrize("threads", [64, 256, 512])
-def test_every_tuning(k, load, threads):
+def test_every_tuning(k, load, layout, threads):
     from paper_2602_04103_gb300 import capi
     n, n4 = 3 * S2 + 77, 3 * S4 + 99
     words, w4 = synth.bits(17, n, 0.5), synth.dna_uniform(18, n4)
     q = synth.queries(19, n, 100_003)
     q4 = synth.queries(20, n4, 100_003)
     cv = synth.symbols(21, q4.size, 4)
-    idx, idx4 = build(words, n, 2), build(w4, n4, 4)
+    idx, idx4 = build(words, n, 2, layout), build(w4, n4, 4, layout)
     for i in (idx, idx4):
         capi.qr_set_tuning(i, k, threads, load, 0)
     assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
@@ -252,12 +261,13 @@ def test_every_tuning(k, load, threads):
     assert np.array_equal(rank(idx, q, 0), oracle.rank(words, n, 2, q, 0)[0])
 
 
-def test_host_pipeline_matches_device():
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_host_pipeline_matches_device(layout):
     import torch
     from paper_2602_04103_gb300 import capi
     n = 5 * S4 + 3
     w4 = synth.dna_uniform(31, n)
-    idx = build(w4, n, 4)
+    idx = build(w4, n, 4, layout)
     m = (1 << 22) + 12345                       # two chunks, ragged
     q = synth.queries(32, n, m)
     cv = synth.symbols(33, m, 4)
@@ -297,3 +307,96 @@ def test_concurrent_streams_same_index():
     torch.cuda.synchronize()
     for (dq, o), q in zip(outs, qs):
         assert np.array_equal(host_u64(o), oracle.rank(words, n, 2, q, 1)[0])
+
+
+def test_sector_layout_matches_definitions():
+    # BiRank16x2 (Sec. 3.1): deltas to 1/4 and 3/4 of a 480-bit block,
+    # b_{j,h} = rank(480 j + 240 h + 120) - 2^11 s_{j/128}; half h holds data
+    # bits [480 j + 240 h, +240) after its 16-bit delta
+    from paper_2602_04103_gb300 import capi
+    n = 4 * S2S + 4321
+    words = synth.bits(77, n, 0.41)
+    idx = build(words, n, 2, 1)
+    info, lines, sup = read_layout(idx, 2)
+    nb = n // B2S + 1
+    assert info["nblocks"] == nb and info["block_chars"] == 480
+    starts = np.minimum(np.arange(info["nsuper"], dtype=np.uint64) * np.uint64(S2S), np.uint64(n))
+    r_sup, _ = oracle.rank(words, n, 2, starts, 1)
+    assert np.array_equal(sup.astype(np.uint64), r_sup >> np.uint64(11))
+    js = np.arange(nb, dtype=np.uint64)
+    tb = np.unpackbits(words.view(np.uint8), bitorder="little")
+    lb = np.unpackbits(lines.view(np.uint8), bitorder="little").reshape(nb, 2, 256)
+    for h in range(2):
+        mids = np.minimum(js * np.uint64(B2S) + np.uint64(240 * h + 120), np.uint64(n))
+        r_mid, _ = oracle.rank(words, n, 2, mids, 1)
+        want = r_mid - (sup.astype(np.uint64)[js >> np.uint64(7)] << np.uint64(11))
+        assert np.array_equal(lines[:, 4 * h] & np.uint64(0xFFFF), want)
+        for j in [0, 1, 127, 128, nb - 1]:
+            lo, hi = j * B2S + 240 * h, min(j * B2S + 240 * h + 240, n)
+            if hi > lo:
+                assert np.array_equal(lb[j, h, 16:16 + hi - lo], tb[lo:hi])
+
+
+def test_sector_max_deltas():
+    # sigma 2: 2047 + 127 * 480 + 240 + 120 = 63367; sigma 4: 8191 + 255 * 192 + 96 + 48 = 57295
+    n = 2 * S2S + 3000
+    bits = np.zeros(n, dtype=np.uint8)
+    bits[:2047] = 1
+    bits[S2S:2 * S2S] = 1
+    idx = check_bits(synth.pack_bits(bits), n, layout=1)
+    _, lines, _ = read_layout(idx, 2)
+    d = np.maximum(lines[:, 0] & np.uint64(0xFFFF), lines[:, 4] & np.uint64(0xFFFF)).astype(np.int64)
+    assert d.max() == 63367
+    n4 = 2 * S4S + 5000
+    codes = np.zeros(n4, dtype=np.uint8)
+    codes[:8191] = 3
+    codes[S4S:2 * S4S] = 3
+    idx4 = check_dna(synth.pack2(codes), n4, q=np.concatenate([np.arange(0, n4 + 1, 7), [n4]]).astype(np.uint64),
+                     layout=1)
+    _, lines4, _ = read_layout(idx4, 4)
+    dT = np.maximum(lines4[:, 0] >> np.uint64(48), lines4[:, 4] >> np.uint64(48)).astype(np.int64)
+    assert dT.max() == 57295
+
+
+def test_sector_sizes_and_overheads():
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S2S + 5
+    info = capi.qr_info(build(synth.bits(1, n, 0.5), n, 2, 1))
+    nb = n // 480 + 1
+    assert info["bytes_blocks"] == 64 * nb and info["bytes_super"] == 4 * ((nb + 127) // 128)
+    # BiRank16x2's overhead as printed in Sec. 3.1: 6.72%
+    n2 = 1 << 34
+    nb = n2 // 480 + 1
+    over = (64 * nb + 4 * ((nb + 127) // 128)) * 8 / n2 - 1
+    assert abs(over * 100 - 6.72) < 0.005
+
+
+def test_autotune_and_build_tuned():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 6 * S2 + 5
+    words = synth.bits(61, n, 0.5)
+    q = synth.queries(62, n, 300_000)
+    dq = dev_u64(q)
+    scratch = torch.empty_like(dq)
+    idx = build(words, n, 2, 0)
+    t = capi.qr_autotune(idx, dq, scratch, c=1)
+    assert t["queries_per_thread"] in (1, 2, 4, 8) and t["load_mode"] in (0, 1, 2, 3)
+    assert capi.qr_get_tuning(idx) == t
+    assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
+    # a 5% space budget admits only BiRank16 (3.28%); 7% admits BiRank16x2 (6.72%) too
+    idx5, lay5 = capi.qr_build_tuned(dev_u64(words), n, 2, dq, scratch, c=1, max_overhead=0.05)
+    assert lay5 == 0
+    idx7, lay7 = capi.qr_build_tuned(dev_u64(words), n, 2, dq, scratch, c=0, max_overhead=0.07)
+    assert lay7 in (0, 1)
+    for i in (idx5, idx7):
+        assert np.array_equal(rank(i, q, 0), oracle.rank(words, n, 2, q, 0)[0])
+    with pytest.raises(capi.QRError):
+        capi.qr_build_tuned(dev_u64(words), n, 2, dq, scratch, max_overhead=0.01)
+    n4 = 3 * S4 + 1
+    w4 = synth.dna_uniform(63, n4)
+    q4 = synth.queries(64, n4, 100_000)
+    dq4 = dev_u64(q4)
+    s4 = torch.empty((q4.size, 4), dtype=torch.int64, device="cuda")
+    idx4, lay4 = capi.qr_build_tuned(dev_u64(w4), n4, 4, dq4, s4, rank4=True, max_overhead=0.40)
+    assert np.array_equal(rank4(idx4, q4), oracle.rank4(w4, n4, q4)[0])

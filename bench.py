@@ -1,22 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the rank / QuadFm hot path on GB300.
 
-Headline workload: BiRank (sigma 2) over n = 2^34 i.i.d. bits (p = 0.5),
-2^28 uint64 queries uniform in [0, n], rank(q) into uint64 outputs; a step is
-one qr_rank call over the whole batch.  The JSON line also carries the other
-rows of the hot path measured in the same run (``extra``): sorted queries,
-density 0.01, an L2-resident 2^26-bit text, QuadRank rank with random symbols
-and rank_4 over 2^32 DNA chars, and QuadFm counts.
+Headline (the workload the metric is quoted on): BiRank (sigma 2) over
+n = 2^34 i.i.d. bits (p = 0.5), 2^28 uint64 queries uniform in [0, n],
+rank(q) into uint64 outputs.  A step is one qr_rank call over the whole
+batch, on an index built by the tuned build (every layout within the space
+budget, autotuned, fastest kept).  The line also carries, measured in the
+same run: the GPU's random 32-byte request ceiling (gather probe), the
+end-to-end rate through the host-buffer API, and under ``extra`` the other
+rows of the hot path (sorted queries, density 0.01, an L2-resident text,
+QuadRank rank / rank_4 over 2^32 chars, QuadFm counts: persistent vs
+per-step launches).
 
-``--impl reference`` times the CPU oracle (the only comparison program this
-project has) on a bounded sample of the same workload.
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload (this project has no other comparison program).
 
-Multi-GPU: one process per GPU; each rank holds its own index and answers its
+Multi-GPU: one process per GPU, each holding its own index and answering its
 own 2^28 queries (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -31,49 +36,42 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "rank Gqueries/s and % of HBM random-access roofline; QuadFm patterns/s"
-B2 = 496
 FALLBACK_HBM_GBS = 6800.0
+CHUNK_HOST = 1 << 22  # queries per chunk of the host-buffer pipeline (qr_rank_host)
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-# ---------------------------------------------------------------- environment
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
-        d = json.loads(p.read_text())
-        return float(d["hbm_gbs"]), "measured"
+        return float(json.loads(p.read_text())["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines: list[str] = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
             time.sleep(0.3)
         except FileNotFoundError:
             self.proc = None
@@ -112,19 +110,17 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- helpers
-def to_dev_u64(a):
+def dev_u64(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
 
 
 def time_launches(fn, steps, stream):
-    """Run fn() `steps` times; CUDA events on `stream` around each launch.
-    Returns (total ms, list of per-launch ms)."""
+    """fn() `steps` times with CUDA events on `stream` around each call.
+    Returns (total ms, per-call ms)."""
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for a, b in evs:
         a.record(stream)
@@ -133,6 +129,12 @@ def time_launches(fn, steps, stream):
     t1.record(stream)
     t1.synchronize()
     return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in evs]
+
+
+def best_ms(fn, stream, reps=3):
+    fn()
+    _, per = time_launches(fn, reps, stream)
+    return float(np.median(per))
 
 
 def barrier_sync(ws):
@@ -144,20 +146,20 @@ def barrier_sync(ws):
     torch.cuda.synchronize()
 
 
-def max_over_ranks(x: float, ws: int) -> float:
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """Largest x over the ranks (the slowest rank's timed region)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per unit of a kernel from a committed ncu summary, if the
-    kernel's sources have not changed since the capture."""
-    import hashlib
+    """DRAM bytes per query of a kernel from the committed ncu summary, if the
+    kernel's sources are unchanged since the capture (else None)."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
@@ -167,25 +169,48 @@ def traffic_record(kernel: str):
     h = hashlib.sha256()
     for f in d["sources"]:
         h.update((ROOT / f).read_bytes())
-    if h.hexdigest() != d["sha256"]:
-        return None
-    return d
+    return d if h.hexdigest() == d["sha256"] else None
 
 
-# ---------------------------------------------------------------- workloads
-def birank_workload(n, m, seed_id, p=0.5, sorted_q=False):
-    from paper_2602_04103_gb300 import synth
-    base = synth.base_seed(seed_id)
-    text = synth.bits(synth.substream(base, 1), n, p)
-    q = synth.queries(synth.substream(base, 2), n, m)
-    if sorted_q:
-        q.sort()
-    return text, q
+def bytes_per_query(sigma: int, layout: int, load_mode: int, rank4: bool = False, per_query_c: bool = False):
+    """Algorithmic bytes of one query: the index bytes it must read (the
+    32-byte half-line of the sector layout, the 64-byte line of the paper
+    layout) + the 8-byte query + the result (8, or 32 for rank_4) + 1 byte
+    of symbol when symbols are per query."""
+    index = 32 if layout == 1 else 64
+    return index + 8 + (32 if rank4 else 8) + (1 if per_query_c else 0)
+
+
+def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
+    """Random 32-byte DRAM requests of one uniform query (superblock entries
+    are L2-resident): the sector layout reads one sector; the paper layout
+    reads one sector below the block middle and two above it (both with
+    whole-line load modes 0 and 2)."""
+    if layout == 1:
+        return 1.0
+    if load_mode in (0, 2):
+        return 2.0
+    lower = 240 / 496 if sigma == 2 else 96 / 224
+    return lower + 2 * (1 - lower)
+
+
+# ---------------------------------------------------------------- our arm
+def probe_ceiling(stream):
+    """Random 32-byte loads over a 4 GiB buffer: the GPU's random request rate."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    nbytes, m = 4 << 30, 1 << 26
+    buf = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    out = torch.empty(m, dtype=torch.int64, device="cuda")
+    ms = best_ms(lambda: capi.qr_probe_gather(buf, nbytes // 32, 32, m, 99, out, 4, 256, load_bytes=32), stream)
+    del buf, out
+    torch.cuda.empty_cache()
+    return m / (ms * 1e-3) / 1e9
 
 
 def run_ours(args):
     import torch
-    from paper_2602_04103_gb300 import capi
+    from paper_2602_04103_gb300 import capi, workloads
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -193,19 +218,21 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    n = 1 << args.log_n
-    m = 1 << args.log_m
-    t_gen = time.time()
-    # every rank answers its own batch (seed offset by rank): weak scaling
-    text, q = birank_workload(n, m, 2 + 100 * rank)
-    log(f"[bench] generated n=2^{args.log_n} bits, m=2^{args.log_m} queries in {time.time() - t_gen:.1f}s")
-    d_text = to_dev_u64(text)
-    idx = capi.qr_build(d_text, n, 2)
+    n, m = 1 << args.log_n, 1 << args.log_m
+    t0 = time.time()
+    text, q = workloads.birank_inputs(args.log_n, args.log_m, rank=rank)
+    log(f"[bench] inputs n=2^{args.log_n} bits, m=2^{args.log_m} queries: {time.time() - t0:.1f}s")
+    ceiling = probe_ceiling(stream)
+    log(f"[bench] random 32-byte request ceiling: {ceiling:.2f} G/s")
+    dq = dev_u64(q)
+    d_text = dev_u64(text)
+    t0 = time.time()
+    idx, layout, tuning = workloads.build_tuned(d_text, n, 2, dq, c=1)
+    t_tune = time.time() - t0
     del d_text
-    if args.tune:
-        capi.qr_set_tuning(idx, *args.tune)
-    tuning = capi.qr_get_tuning(idx)
-    dq = to_dev_u64(q)
+    torch.cuda.empty_cache()
+    info = capi.qr_info(idx)
+    log(f"[bench] tuned build: layout {layout}, {tuning} ({t_tune:.1f}s)")
     out = torch.empty_like(dq)
 
     def step():
@@ -218,22 +245,26 @@ def run_ours(args):
         total_ms, per = time_launches(step, args.steps, stream)
         barrier_sync(ws)
     total_ms = max_over_ranks(total_ms, ws)
-    status = capi.qr_status(idx)
-    assert status == 0, f"device status {status}"
+    assert capi.qr_status(idx) == 0
     value = ws * m * args.steps / (total_ms * 1e-3) / 1e9
     avg_ms = float(np.mean(per))
-    bytes_per_q = 64 + 8 + 8
-    achieved = bytes_per_q * m / (avg_ms * 1e-3) / 1e9
+    bpq = bytes_per_query(2, layout, tuning["load_mode"])
+    rpq = requests_per_query(2, layout, tuning["load_mode"])
+    achieved = bpq * m / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    tr = traffic_record("birank_rank")
+    kname = "birank_rank_sector" if layout == 1 else "birank_rank_paper"
+    tr = traffic_record(kname)
+    gq_launch = m / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": (round(tr["bytes_per_query"] * m) if tr else None),
-                "peak_kind": f"of {peak_kind}",
-                "algorithmic_bytes_per_query": bytes_per_q,
-                "kernel": "rank_kernel<K,LOAD,kBiScalar>"}
+                "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
+                "peak_kind": f"of {peak_kind} (copy bandwidth)",
+                "kernel": "rank_sector_kernel<K,kBiScalar>" if layout == 1 else "rank_kernel<K,LOAD,kBiScalar>",
+                "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
+                "random_requests_per_query": round(rpq, 3),
+                "random_request_ceiling_G_per_s": round(ceiling, 2),
+                "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4)}
 
-    # end to end through the public API with host buffers
+    # end to end through the public host-buffer API (H2D + kernels + D2H)
     qh = torch.from_numpy(q.view(np.int64)).pin_memory()
     oh = torch.empty(m, dtype=torch.int64).pin_memory()
 
@@ -242,37 +273,42 @@ def run_ours(args):
 
     e2e_step()
     barrier_sync(ws)
-    e_ms, _ = time_launches(e2e_step, max(1, min(args.steps, 3)), stream)
-    e_ms = max_over_ranks(e_ms, ws)
     e_steps = max(1, min(args.steps, 3))
+    e_ms, _ = time_launches(e2e_step, e_steps, stream)
+    e_ms = max_over_ranks(e_ms, ws)
     e2e_val = ws * m * e_steps / (e_ms * 1e-3) / 1e9
-    chunks = (m + (1 << 22) - 1) >> 22
-    # spot check of the e2e output against the device output
     torch.cuda.synchronize()
-    assert np.array_equal(oh[:1 << 16].numpy(), out[:1 << 16].cpu().numpy())
+    assert np.array_equal(oh[: 1 << 16].numpy(), out[: 1 << 16].cpu().numpy())
 
     extra = {}
     if not args.no_extra and rank == 0:
-        idx.free()
-        del dq, out, qh, oh
-        torch.cuda.empty_cache()
-        extra = run_extras(args)
+        extra = run_extras(args, idx, layout, tuning, dq, out, stream, peak)
+    idx.free()
+    del dq, out, qh, oh
+    torch.cuda.empty_cache()
+    if not args.no_extra and rank == 0:
+        extra.update(run_extras_other(args, stream, peak))
 
-    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gqueries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
-                               f"uniform uint64 queries per GPU", "n_bits": n, "queries_per_gpu": m,
-                   "layout": "BiRank16 (3.28% overhead)", "tuning": tuning,
-                   "l2": "inputs larger than L2 (2 GiB queries, 2.2 GB index)", "parallelism": f"replica x{ws}"},
+                               f"uniform uint64 queries per GPU",
+                   "n_bits": n, "queries_per_gpu": m,
+                   "layout": ("BiRank16x2 sector layout (6.72% overhead)" if layout == 1
+                              else "BiRank16 (3.28% overhead)"),
+                   "index_bytes": info["bytes_blocks"] + info["bytes_super"], "tuning": tuning,
+                   "tuned_build_s": round(t_tune, 2),
+                   "l2": "inputs larger than L2 (2 GiB queries, 2.3 GB index; L2 129 MB)",
+                   "parallelism": f"independent replica per GPU x{ws}"},
         "roofline": roofline,
         "e2e": {"value": round(e2e_val, 3), "unit": "Gqueries/s", "h2d_bytes_per_step": 8 * m,
-                "d2h_bytes_per_step": 8 * m, "api": "qr_rank_host (pinned host buffers, chunked pipeline)"},
+                "d2h_bytes_per_step": 8 * m,
+                "api": "qr_rank_host: pinned host q/out, chunks of 2^22 on two streams"},
         "gpu_launches": args.steps,
-        "gpu_launches_e2e_per_step": chunks,
-        "clocks": clocks,
+        "gpu_launches_e2e_per_step": (m + CHUNK_HOST - 1) // CHUNK_HOST,
+        "clocks": clk.summary(),
     }
     if extra:
         line["extra"] = extra
@@ -286,97 +322,138 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_extras(args):
-    """Other rows of the hot path, each timed with CUDA events (L2 flushed by
-    inputs larger than L2 unless stated)."""
+def run_extras(args, idx, layout, tuning, dq, out, stream, peak):
+    """Rows that reuse the headline index: the same queries sorted."""
     import torch
     from paper_2602_04103_gb300 import capi
-    out = {}
-    stream = torch.cuda.current_stream()
-    peak, _ = peaks()
+    m = dq.numel()
+    res = {}
+    qs = torch.sort(dq).values
+    ms = best_ms(lambda: capi.qr_rank(idx, qs, 1, out), stream)
+    info = capi.qr_info(idx)
+    gq = m / (ms * 1e-3) / 1e9
+    bpq = 16 + (info["bytes_blocks"] + info["bytes_super"]) / m   # every line once + q + out
+    res["birank_sorted_queries"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3),
+                                    "algorithmic_bytes_per_query": round(bpq, 2),
+                                    "roofline_frac": round(gq * bpq / peak, 4), "layout": layout}
+    log(f"[bench] sorted: {gq:.2f} Gq/s")
+    return res
+
+
+def run_extras_other(args, stream, peak):
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    res = {}
     m = 1 << args.log_m
-
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        _, per = time_launches(fn, reps, stream)
-        return float(np.mean(per))
-
-    # BiRank: sorted queries, density 0.01, L2-resident text
-    for name, log_n, p, srt in [("birank_sorted", args.log_n, 0.5, True), ("birank_p001", args.log_n, 0.01, False),
-                                ("birank_l2_resident_2^26", 26, 0.5, False)]:
-        n = 1 << log_n
-        text, q = birank_workload(n, m, 12, p=p, sorted_q=srt)
-        idx = capi.qr_build(to_dev_u64(text), n, 2)
+    # BiRank p = 0.01 (full size) and an L2-resident 2^26-bit text
+    for name, log_n, p in [("birank_p0.01", args.log_n, 0.01), ("birank_l2_resident_2^26", 26, 0.5)]:
+        text, q = workloads.birank_inputs(log_n, args.log_m, p=p, workload=12)
+        dq = dev_u64(q)
+        idx, layout, tuning = workloads.build_tuned(dev_u64(text), 1 << log_n, 2, dq, c=1)
         del text
-        dq = to_dev_u64(q)
         o = torch.empty_like(dq)
-        ms = timed(lambda: capi.qr_rank(idx, dq, 1, o))
-        info = capi.qr_info(idx)
+        ms = best_ms(lambda: capi.qr_rank(idx, dq, 1, o), stream)
         gq = m / (ms * 1e-3) / 1e9
-        bpq = 16 + (64 if not srt and log_n > 27 else (info["bytes_blocks"] + info["bytes_super"]) / m)
-        out[name] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "algorithmic_bytes_per_query": round(bpq, 2),
-                     "roofline_frac": round(gq * bpq / peak, 4)}
+        bpq = bytes_per_query(2, layout, tuning["load_mode"]) if log_n > 27 else 16
+        res[name] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout, "tuning": tuning,
+                     "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4)}
+        log(f"[bench] {name}: {gq:.2f} Gq/s")
         idx.free()
         del dq, o
         torch.cuda.empty_cache()
-        log(f"[bench] {name}: {gq:.2f} Gq/s")
-
-    # QuadRank over 2^32 uniform DNA chars: rank(q, c) with random c, and rank_4
-    from paper_2602_04103_gb300 import synth
+    # QuadRank over 2^32 uniform DNA: rank(q, c) with random c, and rank_4
     n4 = 1 << args.log_n4
-    base = synth.base_seed(3)
-    t4 = synth.dna_uniform(synth.substream(base, 1), n4)
-    q4 = synth.queries(synth.substream(base, 2), n4, m)
-    c4 = synth.symbols(synth.substream(base, 3), m, 4)
-    idx4 = capi.qr_build(to_dev_u64(t4), n4, 4)
+    t4, q4, c4 = workloads.quadrank_inputs(args.log_n4, args.log_m, "uniform")
+    dq, dc = dev_u64(q4), torch.from_numpy(c4).cuda()
+    idx4, layout4, tuning4 = workloads.build_tuned(dev_u64(t4), n4, 4, dq, c=dc)
     del t4
-    dq = to_dev_u64(q4)
-    dc = torch.from_numpy(c4).cuda()
     o = torch.empty_like(dq)
-    ms = timed(lambda: capi.qr_rank_c(idx4, dq, dc, o))
+    ms = best_ms(lambda: capi.qr_rank_c(idx4, dq, dc, o), stream)
     gq = m / (ms * 1e-3) / 1e9
-    out["quadrank_rank_random_c"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "algorithmic_bytes_per_query": 81,
-                                     "roofline_frac": round(gq * 81 / peak, 4)}
+    bpq = bytes_per_query(4, layout4, tuning4["load_mode"], per_query_c=True)
+    res["quadrank_rank_random_c"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": tuning4,
+                                     "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4)}
     del o
     o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
-    ms = timed(lambda: capi.qr_rank4(idx4, dq, o4))
+    t4r = capi.qr_autotune(idx4, dq[: 1 << 24], o4, rank4=True)
+    ms = best_ms(lambda: capi.qr_rank4(idx4, dq, o4), stream)
     gq = m / (ms * 1e-3) / 1e9
-    out["quadrank_rank4"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "algorithmic_bytes_per_query": 104,
-                             "roofline_frac": round(gq * 104 / peak, 4)}
+    bpq = bytes_per_query(4, layout4, t4r["load_mode"], rank4=True)
+    res["quadrank_rank4"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": t4r,
+                             "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4)}
+    log(f"[bench] quadrank: {res['quadrank_rank_random_c']['Gq_s']} / {res['quadrank_rank4']['Gq_s']} Gq/s")
     idx4.free()
     del dq, dc, o4
     torch.cuda.empty_cache()
-    log(f"[bench] quadrank: {out['quadrank_rank_random_c']['Gq_s']} / {out['quadrank_rank4']['Gq_s']} Gq/s")
-    return out
+    res.update(run_fm(args, stream))
+    return res
+
+
+def run_fm(args, stream):
+    """QuadFm count over the 2^26-char text, 10^7 patterns of length 16..150:
+    one persistent launch vs one launch per search step."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    text, pats, off = workloads.fm_inputs(args.fm_log_n, args.fm_m)
+    m = off.size - 1
+    dt = torch.from_numpy(text).cuda()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    fidx = capi.qfm_build(dt, text.size)
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    info = capi.qfm_info(fidx)
+    dp = torch.from_numpy(pats).cuda()
+    doff = torch.from_numpy(off.view(np.int64)).cuda()
+    o = torch.empty(m, dtype=torch.int64, device="cuda")
+    ms_p = best_ms(lambda: capi.qfm_count(fidx, dp, doff, o), stream)
+    ref = o.clone()
+    ms_s = best_ms(lambda: capi.qfm_count_stepwise(fidx, dp, doff, o), stream)
+    assert torch.equal(ref, o)
+    assert capi.qfm_status(fidx) == 0
+    res = {"qfm_count_persistent": {"patterns_per_s": round(m / (ms_p * 1e-3)), "ms": round(ms_p, 3)},
+           "qfm_count_stepwise": {"patterns_per_s": round(m / (ms_s * 1e-3)), "ms": round(ms_s, 3)},
+           "qfm_speedup_persistent_vs_stepwise": round(ms_s / ms_p, 2),
+           "qfm_build_s": round(t_build, 3), "qfm_index_bytes": info["bytes_rank"] + info["bytes_table"]}
+    work = ROOT / "tests" / "golden" / "fm_work_config4.json"
+    if work.exists() and args.fm_log_n == 26 and args.fm_m == 10_000_000:
+        w = json.loads(work.read_text())
+        steps = w["mean_lf_steps"] * m
+        res["qfm_count_persistent"]["lf_steps_per_s"] = round(steps / (ms_p * 1e-3))
+        res["qfm_count_persistent"]["rank_queries_per_s"] = round(2 * steps / (ms_p * 1e-3))
+        res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_config4.json)"
+    log(f"[bench] qfm: persistent {m / ms_p / 1e3:.1f} M/s, stepwise {m / ms_s / 1e3:.1f} M/s")
+    fidx.free()
+    return res
 
 
 def cpu_baseline(args, n, text, q):
-    """The oracle as it stands, on a bounded sample of the workload: the
-    sweep answers a sample of the same queries over the full text."""
+    """The oracle as it stands on a bounded sample: the first 2^k queries,
+    answered by one sort + linear sweep over the full text."""
     import oracle
     sample = q[: 1 << args.cpu_log_sample].copy()
     t0 = time.perf_counter()
-    _, rc = oracle.rank(text, n, 2, sample, 1)
+    oracle.rank(text, n, 2, sample, 1)
     dt = time.perf_counter() - t0
     return {"value": round(sample.size / dt / 1e9, 6), "unit": "Gqueries/s", "cores": 1, "kind": "oracle",
             "sample": f"first 2^{args.cpu_log_sample} of the queries over the full 2^{args.log_n}-bit text "
                       f"(sort + one linear sweep), {dt:.1f}s"}
 
 
+# ---------------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle as the reference arm: each step answers a bounded sample
     of the workload's queries over the full text."""
     import oracle
+    from paper_2602_04103_gb300 import workloads
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     n = 1 << args.log_n
-    m = 1 << args.log_m
-    text, q = birank_workload(n, m, 2)
+    text, q = workloads.birank_inputs(args.log_n, args.log_m)
     sample = q[: 1 << args.cpu_log_sample].copy()
     for _ in range(args.warmup):
-        oracle.rank(text, n, 2, sample[: 1 << 16], 1)
+        oracle.rank(text, n, 2, sample[: 1 << 12], 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.rank(text, n, 2, sample, 1)
@@ -386,9 +463,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
-                                   f"uniform uint64 queries per GPU", "n_bits": n, "queries_per_gpu": m},
+                                   f"uniform uint64 queries per GPU", "n_bits": n, "queries_per_gpu": 1 << args.log_m},
             "cpu_baseline": {"value": round(value, 6), "unit": "Gqueries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"2^{args.cpu_log_sample} of the queries per step over the full text"},
+                             "sample": f"2^{args.cpu_log_sample} of the queries per step (sort + one sweep over "
+                                       f"the full text)"},
             "e2e": {"value": round(value, 6), "unit": "Gqueries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -402,18 +480,19 @@ def main():
     ap.add_argument("--log-n", type=int, default=34)
     ap.add_argument("--log-m", type=int, default=28)
     ap.add_argument("--log-n4", type=int, default=32)
+    ap.add_argument("--fm-log-n", type=int, default=26)
+    ap.add_argument("--fm-m", type=int, default=10_000_000)
     ap.add_argument("--cpu-log-sample", type=int, default=22)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--tune", type=int, nargs=4, metavar=("K", "THREADS", "LOAD", "GRID"))
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
-        log("[bench] warmup raised to 3")
-        args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
-        run_ours(args)
+        return
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3")
+        args.warmup = 3
+    run_ours(args)
 
 
 if __name__ == "__main__":

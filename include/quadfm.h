@@ -117,6 +117,76 @@ int qfm_status(qfm_index* idx, void* stream);
 /* Release (waits for the device). NULL is a no-op. */
 int qfm_free(qfm_index* idx);
 
+/* ---------------------------------------------------------------------- */
+/* Continuous-batching server over one index                               */
+/* ---------------------------------------------------------------------- */
+/*
+ * The paper processes reads in batches inside each thread (App. E); this
+ * server is the host runtime that turns a stream of independent count
+ * requests into such batches on the GPU.  A worker thread owns `slots` batch
+ * slots (device buffers carved from budget_bytes, pinned staging, a stream).
+ * Whenever a slot is free and requests wait, it packs waiting requests in
+ * arrival order while they fit (max_batch_patterns, max_batch_bytes,
+ * max_requests_per_batch), runs qfm_count on the slot's stream and copies the
+ * counts back, so requests that arrive while earlier batches run are admitted
+ * into the next free slot and their work overlaps on the device.  Completion
+ * is polled from the host (no device-side waits).  With slots = 1 and
+ * max_requests_per_batch = 1 the server is the plain per-request path.
+ */
+typedef struct qfm_server qfm_server;
+
+typedef struct {
+    uint64_t budget_bytes;          /* device memory for all slots                     */
+    int32_t slots;                  /* batches in flight (1..64)                        */
+    int32_t max_requests_per_batch; /* >= 1                                             */
+    uint64_t max_batch_patterns;    /* patterns per batch (a request may not exceed it) */
+    uint64_t max_batch_bytes;       /* pattern bytes per batch (same)                   */
+    int32_t poll_us;                /* worker's completion-poll interval                */
+    int32_t fail_after_batches;     /* test hook: > 0 makes batch k+1 fail on the host  */
+} qfm_server_opts_t;
+
+typedef struct {
+    uint64_t submitted, completed, pending, in_flight, batches;
+    double mean_requests_per_batch;
+    int32_t error;                  /* first error of the server (QR_OK if none)        */
+} qfm_server_stats_t;
+
+/* Fill *opts with defaults: 1 GiB budget, 4 slots, 2^20 patterns and 64 MiB
+ * of pattern bytes per batch, no limit on requests per batch, 20 us poll. */
+int qfm_server_default_opts(qfm_server_opts_t* opts);
+
+/* Start a server (allocates the slots; the index must outlive it).
+ * Errors: QR_EINVAL (options, slots x capacity above the budget), QR_ENOMEM. */
+int qfm_server_create(qfm_index* idx, const qfm_server_opts_t* opts, qfm_server** out);
+
+/* Queue one request of m >= 1 patterns (host memory, pattern k =
+ * patterns[offsets[k] .. offsets[k+1])); counts go to out[0..m) (host).  The
+ * buffers must stay untouched until the request completes.  Returns at once.
+ * Errors: QR_EINVAL (NULL, decreasing offsets, larger than a slot). */
+int qfm_server_submit(qfm_server* sv, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
+                      uint64_t* request_id);
+
+/* Take up to cap completed requests: ids, latency (submit to completion, us)
+ * and status (QR_OK or the error that failed the request); *n_done = count. */
+int qfm_server_poll(qfm_server* sv, uint64_t* ids, double* latency_us, int* status, uint64_t cap, uint64_t* n_done);
+
+/* Wait until every submitted request has completed (QR_ETIMEOUT after
+ * timeout_s seconds); returns the server's error if a batch failed. */
+int qfm_server_drain(qfm_server* sv, double timeout_s);
+
+int qfm_server_stats(qfm_server* sv, qfm_server_stats_t* stats);
+
+/* Stop after the queued requests complete, free the slots. NULL is a no-op. */
+int qfm_server_destroy(qfm_server* sv);
+
+/* Replay a request trace from a native thread: request r (patterns
+ * req_first[r] .. req_first[r+1] of the pattern set `offsets`) is submitted
+ * arrival_s[r] seconds after the start; the call waits for all, writes counts
+ * to out (indexed like the pattern set), per-request latency_us[r] and the
+ * makespan.  The server must have no other submitters or unpolled requests. */
+int qfm_server_replay(qfm_server* sv, const uint8_t* patterns, const uint64_t* offsets, const uint64_t* req_first,
+                      uint64_t nreq, const double* arrival_s, uint64_t* out, double* latency_us, double* makespan_s);
+
 #ifdef __cplusplus
 }
 #endif

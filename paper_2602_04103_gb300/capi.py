@@ -288,3 +288,83 @@ def qfm_status(idx: QFMIndex, stream=None) -> int:
     if rc in (QR_EINVAL, QR_ECUDA, QR_ENOMEM):
         raise QRError(rc, "qfm_status")
     return rc
+
+
+# ---------------------------------------------------------------- serving
+class qfm_server_opts_t(C.Structure):
+    _fields_ = [("budget_bytes", u64), ("slots", C.c_int32), ("max_requests_per_batch", C.c_int32),
+                ("max_batch_patterns", u64), ("max_batch_bytes", u64), ("poll_us", C.c_int32),
+                ("fail_after_batches", C.c_int32)]
+
+
+class qfm_server_stats_t(C.Structure):
+    _fields_ = [("submitted", u64), ("completed", u64), ("pending", u64), ("in_flight", u64), ("batches", u64),
+                ("mean_requests_per_batch", C.c_double), ("error", C.c_int32)]
+
+
+_sig("qfm_server_default_opts", [C.POINTER(qfm_server_opts_t)])
+_sig("qfm_server_create", [vp, C.POINTER(qfm_server_opts_t), C.POINTER(vp)])
+_sig("qfm_server_submit", [vp, vp, vp, u64, vp, C.POINTER(u64)])
+_sig("qfm_server_poll", [vp, vp, vp, vp, u64, C.POINTER(u64)])
+_sig("qfm_server_drain", [vp, C.c_double])
+_sig("qfm_server_stats", [vp, C.POINTER(qfm_server_stats_t)])
+_sig("qfm_server_destroy", [vp])
+_sig("qfm_server_replay", [vp, vp, vp, vp, u64, vp, vp, vp, C.POINTER(C.c_double)])
+
+
+class QFMServer:
+    """Owner of a qfm_server* (stopped and freed with qfm_server_destroy)."""
+
+    def __init__(self, idx: QFMIndex, **opts):
+        o = qfm_server_opts_t()
+        _check(lib.qfm_server_default_opts(C.byref(o)), "qfm_server_default_opts")
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = vp()
+        _check(lib.qfm_server_create(idx, C.byref(o), C.byref(h)), "qfm_server_create")
+        self.handle, self.idx = h.value, idx
+
+    @property
+    def _as_parameter_(self):
+        return vp(self.handle)
+
+    def submit(self, patterns, offsets, out) -> int:
+        rid = u64()
+        _check(lib.qfm_server_submit(self, ptr(patterns), ptr(offsets), numel(offsets) - 1, ptr(out), C.byref(rid)),
+               "qfm_server_submit")
+        return rid.value
+
+    def poll(self, cap: int = 4096):
+        import numpy as np
+        ids = np.empty(cap, np.uint64)
+        lat = np.empty(cap, np.float64)
+        st = np.empty(cap, np.int32)
+        n = u64()
+        _check(lib.qfm_server_poll(self, ptr(ids), ptr(lat), ptr(st), cap, C.byref(n)), "qfm_server_poll")
+        k = n.value
+        return ids[:k], lat[:k], st[:k]
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(lib.qfm_server_drain(self, timeout_s), "qfm_server_drain")
+
+    def stats(self) -> dict:
+        st = qfm_server_stats_t()
+        _check(lib.qfm_server_stats(self, C.byref(st)), "qfm_server_stats")
+        return {k: getattr(st, k) for k, _ in qfm_server_stats_t._fields_}
+
+    def replay(self, patterns, offsets, req_first, arrival_s, out, latency_us) -> float:
+        mk = C.c_double()
+        _check(lib.qfm_server_replay(self, ptr(patterns), ptr(offsets), ptr(req_first), numel(req_first) - 1,
+                                     ptr(arrival_s), ptr(out), ptr(latency_us), C.byref(mk)), "qfm_server_replay")
+        return mk.value
+
+    def close(self) -> None:
+        if self.handle:
+            lib.qfm_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,81 @@
+"""Synthetic workloads of the benchmark (and of the full-size parity tests),
+with the tuned build the benchmark times.
+
+Every input comes from the counter-based generators in ``synth`` with base
+seed ``0x5EED0000 + workload id``:
+
+1. BiRank sigma 2, n = 2^24 i.i.d. bits p = 0.5, 10^6 uniform queries in [0, n].
+2. BiRank sigma 2, n = 2^34 bits, p = 0.5 or 0.01, 2^28 uniform queries (also
+   sorted ascending); 2^26-bit texts for the L2-resident comparison.
+3. QuadRank sigma 4, n = 2^32 chars, i.i.d. uniform ACGT or 40% GC with 5%
+   homopolymer runs (length 10..1000), 2^28 uniform queries, random symbols.
+4. QuadFm, 2^26-char text, 20% covered by planted repeats (300..5000 long, 2%
+   substitutions), 10^7 patterns of length 16..150, even ones sampled from
+   the text with 1% substitutions, odd ones random.
+5. QuadFm serving, same generator at 2^28 chars, requests of 1..4096
+   patterns of length 16..250.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import synth
+
+# space budget of the tuned build: admits BiRank16x2 (6.72%) and the sigma 4
+# sector layout (33.46%), both variants the paper evaluates (Sec. 3.1, 4.1)
+MAX_OVERHEAD = {2: 0.07, 4: 0.34}
+TUNE_SAMPLE_LOG = 24
+
+
+def birank_inputs(log_n: int, log_m: int, p: float = 0.5, workload: int = 2, rank: int = 0):
+    """(packed text, queries) for BiRank; `rank` offsets the seed per GPU."""
+    base = synth.base_seed(workload + 100 * rank)
+    n, m = 1 << log_n, 1 << log_m
+    text = synth.bits(synth.substream(base, 1), n, p)
+    q = synth.queries(synth.substream(base, 2), n, m)
+    return text, q
+
+
+def quadrank_inputs(log_n: int, log_m: int, kind: str = "uniform", rank: int = 0):
+    """(packed DNA text, queries, per-query symbols) for QuadRank."""
+    base = synth.base_seed(3 + 100 * rank)
+    n, m = 1 << log_n, 1 << log_m
+    if kind == "uniform":
+        text = synth.dna_uniform(synth.substream(base, 1), n)
+    else:
+        text = synth.dna_gc_runs(synth.substream(base, 1), n, gc=0.4, run_cover=0.05, run_min=10, run_max=1000)
+    q = synth.queries(synth.substream(base, 2), n, m)
+    c = synth.symbols(synth.substream(base, 3), m, 4)
+    return text, q, c
+
+
+def fm_inputs(log_n: int = 26, m: int = 10_000_000, len_min: int = 16, len_max: int = 150, workload: int = 4):
+    """(text codes, pattern bytes, offsets) of the QuadFm count workload."""
+    base = synth.base_seed(workload)
+    text = synth.fm_text(synth.substream(base, 1), 1 << log_n)
+    pats, off = synth.patterns(synth.substream(base, 5), text, m, len_min, len_max, 0.01)
+    return text, pats, off
+
+
+def build_tuned(text_dev, n: int, sigma: int, q_dev, c=1, rank4: bool = False):
+    """The benchmark's build: every layout within MAX_OVERHEAD[sigma], each
+    autotuned on the first 2^24 queries, the fastest kept.
+    Returns (index, layout, tuning)."""
+    import torch
+
+    from . import capi
+    qs = q_dev[: 1 << TUNE_SAMPLE_LOG]
+    if rank4:
+        scratch = torch.empty((qs.numel(), 4), dtype=torch.int64, device=qs.device)
+    else:
+        scratch = torch.empty_like(qs)
+    cs = c if isinstance(c, int) else c[: qs.numel()]
+    idx, layout = capi.qr_build_tuned(text_dev, n, sigma, qs, scratch, c=cs, rank4=rank4,
+                                      max_overhead=MAX_OVERHEAD[sigma])
+    return idx, layout, capi.qr_get_tuning(idx)
+
+
+def sample_indices(m: int, k: int, seed: int) -> np.ndarray:
+    """k sorted distinct positions of [0, m): both ends plus a uniform draw."""
+    q = synth.queries(seed, m - 1, k)
+    return np.unique(np.concatenate([[0, m - 1], q.astype(np.int64)]))

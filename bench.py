@@ -37,7 +37,7 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "rank Gqueries/s and % of HBM random-access roofline; QuadFm patterns/s"
 FALLBACK_HBM_GBS = 6800.0
-CHUNK_HOST = 1 << 22  # queries per chunk of the host-buffer pipeline (qr_rank_host)
+CHUNK_HOST = 1 << 23  # queries per chunk of the host-buffer pipeline (qr_rank_host)
 
 
 def log(*a):
@@ -222,12 +222,18 @@ def run_ours(args):
     t0 = time.time()
     text, q = workloads.birank_inputs(args.log_n, args.log_m, rank=rank)
     log(f"[bench] inputs n=2^{args.log_n} bits, m=2^{args.log_m} queries: {time.time() - t0:.1f}s")
-    ceiling = probe_ceiling(stream)
+    ceiling = probe_ceiling(stream) if args.layout is None else float("nan")
     log(f"[bench] random 32-byte request ceiling: {ceiling:.2f} G/s")
     dq = dev_u64(q)
     d_text = dev_u64(text)
     t0 = time.time()
-    idx, layout, tuning = workloads.build_tuned(d_text, n, 2, dq, c=1)
+    if args.layout is None:
+        idx, layout, tuning = workloads.build_tuned(d_text, n, 2, dq, c=1)
+    else:   # fixed layout and tuning (profiling runs): no autotuning launches
+        layout = args.layout
+        idx = capi.qr_build(d_text, n, 2, layout=layout)
+        capi.qr_set_tuning(idx, args.tuning[0], args.tuning[1], args.tuning[2], 0)
+        tuning = capi.qr_get_tuning(idx)
     t_tune = time.time() - t0
     del d_text
     torch.cuda.empty_cache()
@@ -261,8 +267,8 @@ def run_ours(args):
                 "kernel": "rank_sector_kernel<K,kBiScalar>" if layout == 1 else "rank_kernel<K,LOAD,kBiScalar>",
                 "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
                 "random_requests_per_query": round(rpq, 3),
-                "random_request_ceiling_G_per_s": round(ceiling, 2),
-                "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4)}
+                "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
+                "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4) if ceiling == ceiling else None}
 
     # end to end through the public host-buffer API (H2D + kernels + D2H)
     qh = torch.from_numpy(q.view(np.int64)).pin_memory()
@@ -305,7 +311,7 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": {"value": round(e2e_val, 3), "unit": "Gqueries/s", "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 8 * m,
-                "api": "qr_rank_host: pinned host q/out, chunks of 2^22 on two streams"},
+                "api": "qr_rank_host: pinned host q/out, chunks of 2^23 on four streams"},
         "gpu_launches": args.steps,
         "gpu_launches_e2e_per_step": (m + CHUNK_HOST - 1) // CHUNK_HOST,
         "clocks": clk.summary(),
@@ -361,7 +367,17 @@ def run_extras_other(args, stream, peak):
         idx.free()
         del dq, o
         torch.cuda.empty_cache()
-    # QuadRank over 2^32 uniform DNA: rank(q, c) with random c, and rank_4
+    res.update(run_quadrank(args, stream, peak))
+    res.update(run_fm(args, stream))
+    return res
+
+
+def run_quadrank(args, stream, peak):
+    """QuadRank over 2^32 uniform DNA: rank(q, c) with random c, and rank_4."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    res = {}
+    m = 1 << args.log_m
     n4 = 1 << args.log_n4
     t4, q4, c4 = workloads.quadrank_inputs(args.log_n4, args.log_m, "uniform")
     dq, dc = dev_u64(q4), torch.from_numpy(c4).cuda()
@@ -385,7 +401,6 @@ def run_extras_other(args, stream, peak):
     idx4.free()
     del dq, dc, o4
     torch.cuda.empty_cache()
-    res.update(run_fm(args, stream))
     return res
 
 
@@ -485,7 +500,19 @@ def main():
     ap.add_argument("--cpu-log-sample", type=int, default=22)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--layout", type=int, choices=[0, 1], default=None,
+                    help="fixed layout for the headline (skips the tuned build and the probe)")
+    ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
+    ap.add_argument("--only", choices=["fm", "quadrank"], default=None,
+                    help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.current_stream()
+        res = run_fm(args, stream) if args.only == "fm" else run_quadrank(args, stream, peaks()[0])
+        print(json.dumps(res), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

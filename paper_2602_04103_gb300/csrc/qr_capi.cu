@@ -156,15 +156,17 @@ int qr_rank4(const qr_index* idx, const uint64_t* q, uint64_t m, uint64_t* out4,
     return launch_rank(idx, q, nullptr, 0, m, out4, 1, (cudaStream_t)stream);
 }
 
-// Host-buffer pipeline: chunks alternate between two internal streams; each
-// chunk is copied in, ranked and copied out on its stream, so the copy of one
-// chunk overlaps the kernel and the copy-out of its neighbours.
+// Host-buffer pipeline: chunks go round-robin to kPipe internal streams;
+// each chunk is copied in, ranked and copied out on its stream, so the copies
+// of some chunks overlap the kernels and copy-outs of others (the copy
+// engines of both directions and the SMs work at once).
 static int host_pipeline(qr_index* idx, const uint64_t* qh, const uint8_t* ch, uint64_t m, int c, uint64_t* outh,
                          int rank4, cudaStream_t caller) {
-    const uint64_t chunk = 1ull << 22;
+    constexpr int P = qr_index::kPipe;
+    const uint64_t chunk = 1ull << 23;
     const uint64_t out_per = rank4 ? 32 : 8;
     const size_t slot_bytes = chunk * (8 + 1 + out_per);
-    const size_t need = 2 * slot_bytes;
+    const size_t need = P * slot_bytes;
     if (idx->stage_bytes < need) {
         if (idx->stage) {
             cudaStreamSynchronize(caller);
@@ -181,12 +183,12 @@ static int host_pipeline(qr_index* idx, const uint64_t* qh, const uint8_t* ch, u
         if (!p) QR_CUDA_TRY(cudaStreamCreateWithFlags(&p, cudaStreamNonBlocking));
     for (auto& e : idx->ev)
         if (!e) QR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    QR_CUDA_TRY(cudaEventRecord(idx->ev[2], caller));
-    for (auto& p : idx->pipe) QR_CUDA_TRY(cudaStreamWaitEvent(p, idx->ev[2], 0));
+    QR_CUDA_TRY(cudaEventRecord(idx->ev[P], caller));
+    for (auto& p : idx->pipe) QR_CUDA_TRY(cudaStreamWaitEvent(p, idx->ev[P], 0));
     for (uint64_t off = 0, k = 0; off < m; off += chunk, k++) {
         const uint64_t len = m - off < chunk ? m - off : chunk;
-        cudaStream_t st = idx->pipe[k & 1];
-        char* base = (char*)idx->stage + (k & 1) * slot_bytes;
+        cudaStream_t st = idx->pipe[k % P];
+        char* base = (char*)idx->stage + (k % P) * slot_bytes;
         uint64_t* dq = (uint64_t*)base;
         uint64_t* dout = (uint64_t*)(base + chunk * 8);
         uint8_t* dc = (uint8_t*)(base + chunk * (8 + out_per));
@@ -196,7 +198,7 @@ static int host_pipeline(qr_index* idx, const uint64_t* qh, const uint8_t* ch, u
         if (rc) return rc;
         QR_CUDA_TRY(cudaMemcpyAsync(outh + off * (out_per / 8), dout, len * out_per, cudaMemcpyDeviceToHost, st));
     }
-    for (int p = 0; p < 2; p++) {
+    for (int p = 0; p < P; p++) {
         QR_CUDA_TRY(cudaEventRecord(idx->ev[p], idx->pipe[p]));
         QR_CUDA_TRY(cudaStreamWaitEvent(caller, idx->ev[p], 0));
     }

@@ -274,11 +274,12 @@ struct qr_index {
     uint32_t* status = nullptr;  // device status word
     int device = 0;
     qr_tuning_t tune{4, 256, 0, 0};
-    // host-buffer pipeline (lazy)
+    // host-buffer pipeline (lazy): kPipe streams, one staging slot each
+    static constexpr int kPipe = 4;
     void* stage = nullptr;
     size_t stage_bytes = 0;
-    cudaStream_t pipe[2] = {nullptr, nullptr};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t pipe[kPipe] = {};
+    cudaEvent_t ev[kPipe + 1] = {};
 };
 
 namespace qr {

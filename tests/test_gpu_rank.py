@@ -268,7 +268,7 @@ def test_host_pipeline_matches_device(layout):
     n = 5 * S4 + 3
     w4 = synth.dna_uniform(31, n)
     idx = build(w4, n, 4, layout)
-    m = (1 << 22) + 12345                       # two chunks, ragged
+    m = (1 << 23) * 4 + 12345                   # more chunks than streams, ragged
     q = synth.queries(32, n, m)
     cv = synth.symbols(33, m, 4)
     qh = torch.from_numpy(q.view(np.int64)).pin_memory()

@@ -54,7 +54,9 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
  * hi, while lo < hi), and a lane whose search ends is refilled at once.
  * Paper: App. E (query_batch: a batch of active searches, finished ones
  * swapped out, rank + LF for the rest), Sec. 4 rank1.
- *   patterns  device bytes 0..3, pattern k = patterns[offsets[k] .. offsets[k+1]).
+ *   patterns  device bytes 0..3, pattern k = patterns[offsets[k] .. offsets[k+1]);
+ *             the whole range [patterns, patterns + offsets[m]) must be readable
+ *             (the kernel reads it in aligned 16-byte chunks inside that range).
  *   offsets   device array of m + 1 non-decreasing uint64.
  *   out       device array of m uint64.
  * The empty pattern counts n + 1 (every position 0..n).  A pattern holding a

@@ -54,9 +54,35 @@ __device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restr
     return true;
 }
 
+// A lane reads its pattern backwards through a 16-byte register window: one
+// aligned vector load per 16 characters instead of one byte load per step.
+// The window is only loaded when the whole aligned chunk lies inside the
+// pattern buffer [pat, pat + total); otherwise the byte is loaded alone.
+struct PatWindow {
+    uint4 w;
+    uint64_t lo = ~0ull;  // byte offset (from pat) of the window start; ~0 = empty
+};
+
+__device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uint64_t total, uint64_t p, PatWindow& win) {
+    if (p - win.lo >= 16) {  // also true for an empty window
+        const uint64_t a = p - (((uintptr_t)(pat + p)) & 15);  // aligned chunk start, as an offset
+        if (a <= p && a + 16 <= total && (((uintptr_t)(pat + a)) & 15) == 0) {
+            win.w = __ldg((const uint4*)(pat + a));
+            win.lo = a;
+        } else {
+            return pat[p];
+        }
+    }
+    const uint32_t k = (uint32_t)(p - win.lo);
+    const uint32_t word = k < 8 ? (k < 4 ? win.w.x : win.w.y) : (k < 12 ? win.w.z : win.w.w);
+    return (int)((word >> (8 * (k & 3))) & 0xFF);
+}
+
 __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t total = a.m ? a.off[a.m] : 0;  // bytes of the pattern buffer
+    PatWindow win;
     // warp-local pool of pattern ids [pool_next, pool_end)
     uint64_t pool_next = 0, pool_end = 0;
     bool drained = false;  // the queue has no ids left for this warp
@@ -105,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
         // ---- one LF step for every active lane
         if (active) {
             if (i >= 0 && lo < hi) {
-                const int c = a.pat[start + i];
+                const int c = pattern_char(a.pat, total, start + (uint64_t)i, win);
                 if (c > 3) {
                     a.out[id] = 0;
                     bad |= kStatusBadSym;

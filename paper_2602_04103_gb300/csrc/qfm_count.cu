@@ -60,15 +60,17 @@ __device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restr
 // pattern buffer [pat, pat + total); otherwise the byte is loaded alone.
 struct PatWindow {
     uint4 w;
-    uint64_t lo = ~0ull;  // byte offset (from pat) of the window start; ~0 = empty
+    uint64_t lo = 0;      // byte offset (from pat) of the window start
+    bool valid = false;
 };
 
 __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uint64_t total, uint64_t p, PatWindow& win) {
-    if (p - win.lo >= 16) {  // also true for an empty window
+    if (!win.valid || p < win.lo || p - win.lo >= 16) {
         const uint64_t a = p - (((uintptr_t)(pat + p)) & 15);  // aligned chunk start, as an offset
-        if (a <= p && a + 16 <= total && (((uintptr_t)(pat + a)) & 15) == 0) {
+        if (a <= p && a + 16 <= total) {
             win.w = __ldg((const uint4*)(pat + a));
             win.lo = a;
+            win.valid = true;
         } else {
             return pat[p];
         }

@@ -101,6 +101,12 @@ int qfm_count_stepwise(qfm_index* idx, const uint8_t* patterns, const uint64_t* 
 int qfm_count_noalloc(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,
                       uint64_t* out, void* stream);
 
+/* L2 policy of the persistent count kernel: 0 = plain read-only loads;
+ * 1 (default) = index lines and superblock entries loaded evict-last and the
+ * pattern / offset stream evict-first, so that the index stays L2-resident
+ * while the patterns stream through.  Errors: QR_EINVAL. */
+int qfm_set_policy(qfm_index* idx, int policy);
+
 /* Index facts.  Errors: QR_EINVAL. */
 int qfm_info(const qfm_index* idx, qfm_info_t* info);
 

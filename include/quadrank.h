@@ -77,7 +77,10 @@ typedef struct {
     int32_t load_mode;           /* 0: whole 64-byte line, 16-byte loads;               */
                                  /* 1: only the 32-byte sectors the query needs, 16-byte */
                                  /*    loads; 2: whole line, 32-byte loads; 3: needed    */
-                                 /*    sectors, 32-byte loads                            */
+                                 /*    sectors, 32-byte loads; 4: whole line, the two    */
+                                 /*    lanes of a pair load its two sectors in one       */
+                                 /*    instruction (one request per line)                */
+                                 /* The sector layout ignores it (one 32-byte load).    */
     int32_t grid_blocks;         /* 0: SM count x resident blocks per SM                */
 } qr_tuning_t;
 

@@ -229,6 +229,7 @@ _sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
 _sig("qfm_count", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_noalloc", [vp, vp, vp, u64, vp, vp])
+_sig("qfm_set_policy", [vp, i32])
 _sig("qfm_info", [vp, C.POINTER(qfm_info_t)])
 _sig("qfm_export", [vp, vp, vp, vp, vp])
 _sig("qfm_rank_index", [vp], vp)
@@ -269,6 +270,10 @@ def qfm_count_noalloc(idx: QFMIndex, patterns, offsets, out, stream=None) -> Non
     m = numel(offsets) - 1
     _check(lib.qfm_count_noalloc(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)),
            "qfm_count_noalloc")
+
+
+def qfm_set_policy(idx: QFMIndex, policy: int) -> None:
+    _check(lib.qfm_set_policy(idx, policy), "qfm_set_policy")
 
 
 def qfm_info(idx: QFMIndex) -> dict:

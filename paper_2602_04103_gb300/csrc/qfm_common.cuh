@@ -17,6 +17,7 @@ struct qfm_index {
     uint32_t* sa = nullptr;    // suffix array (only with QFM_KEEP_SA)
     uint32_t* status = nullptr;
     int device = 0;
+    int policy = 1;            // kFmPolicy* of the persistent count kernel
 };
 
 namespace qr {
@@ -31,18 +32,30 @@ struct FmView {
     uint64_t C[4];
 };
 
+// L2 policies of the persistent count kernel (qfm_index::policy).
+constexpr int kFmPolicyDefault = 0;   // read-only path, no L1 allocation
+constexpr int kFmPolicyKeepIndex = 1; // index evict-last, patterns/offsets evict-first
+
+// 16-byte index load with the chosen L2 policy (KEEP: the evict-last policy `pol`).
+template <bool KEEP>
+__device__ __forceinline__ uint4 fm_ld(const uint4* p, uint64_t pol) {
+    return KEEP ? ld_line16_hint(p, pol) : ld_line16(p);
+}
+
 // rank(q, c) over the BWT with the sentinel row counted as code 0.
-__device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, int c) {
+template <bool KEEP = false>
+__device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, int c, uint64_t pol = 0) {
     const uint64_t j = div224(q);
     const uint32_t slot = (uint32_t)(q - j * kB4) + 32;
     const uint4* L = v.lines + 4 * j;
-    const uint32_t s = __ldg((const uint32_t*)v.supers + 4 * (j >> 8) + c);
-    const uint4 v0 = ld_line16(L);
+    const uint32_t* sp = (const uint32_t*)v.supers + 4 * (j >> 8) + c;
+    const uint32_t s = KEEP ? ld_u32_hint(sp, pol) : __ldg(sp);
+    const uint4 v0 = fm_ld<KEEP>(L, pol);
     const bool upper = slot >= 128;
-    const uint4 va = ld_line16(L + (upper ? 2 : 1));
+    const uint4 va = fm_ld<KEEP>(L + (upper ? 2 : 1), pol);
     uint64_t x[4];
     if (upper) {
-        const uint4 vb = ld_line16(L + 3);
+        const uint4 vb = fm_ld<KEEP>(L + 3, pol);
         x[0] = lo64(va); x[1] = hi64(va); x[2] = lo64(vb); x[3] = hi64(vb);
     } else {
         x[0] = lo64(v0); x[1] = hi64(v0); x[2] = lo64(va); x[3] = hi64(va);
@@ -52,8 +65,9 @@ __device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, 
 
 // LF step of one interval end: C[c] + rank(q, c), where the $ row (stored as
 // code 0) is removed from the count of c = 0 when it lies before q.
-__device__ __forceinline__ uint64_t fm_lf(const FmView& v, uint64_t q, int c) {
-    uint64_t r = fm_rank_stored(v, q, c);
+template <bool KEEP = false>
+__device__ __forceinline__ uint64_t fm_lf(const FmView& v, uint64_t q, int c, uint64_t pol = 0) {
+    uint64_t r = fm_rank_stored<KEEP>(v, q, c, pol);
     if (c == 0 && q > v.dollar) r -= 1;
     return v.C[c] + r;
 }

@@ -64,11 +64,13 @@ struct PatWindow {
     bool valid = false;
 };
 
-__device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uint64_t total, uint64_t p, PatWindow& win) {
+template <bool STREAM>
+__device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uint64_t total, uint64_t p, PatWindow& win,
+                                            uint64_t pol_first) {
     if (!win.valid || p < win.lo || p - win.lo >= 16) {
         const uint64_t a = p - (((uintptr_t)(pat + p)) & 15);  // aligned chunk start, as an offset
         if (a <= p && a + 16 <= total) {
-            win.w = __ldg((const uint4*)(pat + a));
+            win.w = STREAM ? ld_line16_hint((const uint4*)(pat + a), pol_first) : __ldg((const uint4*)(pat + a));
             win.lo = a;
             win.valid = true;
         } else {
@@ -80,7 +82,11 @@ __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uin
     return (int)((word >> (8 * (k & 3))) & 0xFF);
 }
 
+template <int POLICY>
 __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
+    constexpr bool kKeep = POLICY == kFmPolicyKeepIndex;
+    const uint64_t pol_last = kKeep ? l2_policy_evict_last() : 0;
+    const uint64_t pol_first = kKeep ? l2_policy_evict_first() : 0;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t total = a.m ? a.off[a.m] : 0;  // bytes of the pattern buffer
@@ -108,8 +114,8 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
             if (!active) {
                 id = r < avail ? pool_next + r : base + (r - avail);
                 if (id < a.m) {
-                    start = a.off[id];
-                    const uint64_t end = a.off[id + 1];
+                    start = kKeep ? ld_u64_hint(a.off + id, pol_first) : a.off[id];
+                    const uint64_t end = kKeep ? ld_u64_hint(a.off + id + 1, pol_first) : a.off[id + 1];
                     if (end < start || !fm_start(a.v, a.pat + start, end - start, lo, hi, i)) {
                         a.out[id] = 0;  // malformed: offsets decrease or a byte > 3
                         bad |= kStatusBadSym;
@@ -133,19 +139,19 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
         // ---- one LF step for every active lane
         if (active) {
             if (i >= 0 && lo < hi) {
-                const int c = pattern_char(a.pat, total, start + (uint64_t)i, win);
+                const int c = pattern_char<kKeep>(a.pat, total, start + (uint64_t)i, win, pol_first);
                 if (c > 3) {
                     a.out[id] = 0;
                     bad |= kStatusBadSym;
                     active = false;
                 } else {
-                    lo = fm_lf(a.v, lo, c);
-                    hi = fm_lf(a.v, hi, c);
+                    lo = fm_lf<kKeep>(a.v, lo, c, pol_last);
+                    hi = fm_lf<kKeep>(a.v, hi, c, pol_last);
                     --i;
                 }
             }
             if (active && (i < 0 || lo >= hi)) {
-                a.out[id] = hi > lo ? hi - lo : 0;
+                st_stream_u64(a.out + id, hi > lo ? hi - lo : 0);
                 active = false;
             }
         }
@@ -200,14 +206,15 @@ __global__ void step_once(CountArgs a, StepState* __restrict__ st) {
     }
 }
 
-unsigned persistent_grid() {
-    static thread_local int per_sm = 0;
-    if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, count_persistent, kThreads, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
+unsigned persistent_grid(int policy) {
+    static thread_local int per_sm[2] = {0, 0};
+    int& k = per_sm[policy & 1];
+    if (k == 0) {
+        cudaError_t e = policy ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_persistent<1>, kThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_persistent<0>, kThreads, 0);
+        if (e != cudaSuccess || k < 1) k = 1;
     }
-    return (unsigned)(per_sm * device_props().sms);
+    return (unsigned)(k * device_props().sms);
 }
 
 }  // namespace
@@ -223,11 +230,12 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     a.queue = queue;
     a.status = idx->status;
     uint64_t warps_needed = (m + kChunk - 1) / kChunk;
-    uint64_t grid = persistent_grid();
+    uint64_t grid = persistent_grid(idx->policy);
     const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed) grid = blocks_needed;
     if (grid == 0) grid = 1;
-    count_persistent<<<(unsigned)grid, kThreads, 0, s>>>(a);
+    if (idx->policy == kFmPolicyKeepIndex) count_persistent<1><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    else count_persistent<0><<<(unsigned)grid, kThreads, 0, s>>>(a);
     QR_CUDA_TRY(cudaGetLastError());
     return QR_OK;
 }

@@ -42,7 +42,7 @@ static int tuning_ok(const qr_tuning_t& t) {
     const int k = t.queries_per_thread;
     if (k != 1 && k != 2 && k != 4 && k != 8) return 0;
     if (t.block_threads < 64 || t.block_threads > 512 || (t.block_threads & 31)) return 0;
-    if (t.load_mode < 0 || t.load_mode > 3) return 0;
+    if (t.load_mode < 0 || t.load_mode > 4) return 0;
     if (t.grid_blocks < 0) return 0;
     return 1;
 }
@@ -293,7 +293,7 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
     qr_tuning_t win = saved;
     float win_ms = 1e30f;
     const int ks[] = {1, 2, 4, 8}, ths[] = {128, 256, 512};
-    const int nload = idx->layout == QR_LAYOUT_SECTOR ? 1 : 4;
+    const int nload = idx->layout == QR_LAYOUT_SECTOR ? 1 : 5;
     int rc = QR_OK;
     for (int li = 0; li < nload && rc == QR_OK; li++)
         for (int k : ks)

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
         }
         // issue every load of the K queries before any arithmetic on them
         uint4 v0[K], va[K], vb[K];
+        u64x4 r1[K], r2[K];  // load mode 4: this lane's sector of its pair's two lines
         uint32_t s1[K];
         uint4 s4[K];
         uint32_t pos[K];  // p = q - jB (sigma 2) or slot = q - jB4 + 32 (sigma 4)
@@ -90,6 +91,15 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
                 const uint64_t e0 = upper ? s1.a : s0.c, e1 = upper ? s1.b : s0.d;
                 va[k] = make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
                 vb[k] = make_uint4((uint32_t)s1.c, (uint32_t)(s1.c >> 32), (uint32_t)s1.d, (uint32_t)(s1.d >> 32));
+            } else if (LOAD == 4) {
+                // pair-cooperative whole line: lanes 2i and 2i+1 load sector 0
+                // and sector 1 of the even lane's line in one instruction (one
+                // coalesced request for the 64-byte line), then the same for the
+                // odd lane's line; the halves are swapped after the loads land
+                const bool odd = threadIdx.x & 1;
+                const uint4* P = (const uint4*)__shfl_xor_sync(0xffffffffu, (unsigned long long)L, 1);
+                r1[k] = ld_line32((odd ? P : L) + 2 * odd);
+                r2[k] = ld_line32((odd ? L : P) + 2 * odd);
             } else {
                 // needed sectors, 32-byte loads: lower half = sector 0; upper half
                 // = sector 1 + the first 16 bytes (deltas)
@@ -104,6 +114,25 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
                     va[k] = make_uint4((uint32_t)s0.c, (uint32_t)(s0.c >> 32), (uint32_t)s0.d, (uint32_t)(s0.d >> 32));
                     vb[k] = make_uint4(0, 0, 0, 0);
                 }
+            }
+        }
+        if (LOAD == 4) {
+            const bool odd = threadIdx.x & 1;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                // even lane: sector 0 = r1, sector 1 = partner's r1; odd lane:
+                // sector 0 = partner's r2, sector 1 = r2
+                u64x4 send = odd ? r1[k] : r2[k], recv;
+                recv.a = __shfl_xor_sync(0xffffffffu, send.a, 1);
+                recv.b = __shfl_xor_sync(0xffffffffu, send.b, 1);
+                recv.c = __shfl_xor_sync(0xffffffffu, send.c, 1);
+                recv.d = __shfl_xor_sync(0xffffffffu, send.d, 1);
+                const u64x4 S0 = odd ? recv : r1[k], S1 = odd ? r2[k] : recv;
+                const bool upper = kQuad ? pos[k] >= 128 : pos[k] >= kMid2;
+                v0[k] = make_uint4((uint32_t)S0.a, (uint32_t)(S0.a >> 32), (uint32_t)S0.b, (uint32_t)(S0.b >> 32));
+                const uint64_t e0 = upper ? S1.a : S0.c, e1 = upper ? S1.b : S0.d;
+                va[k] = make_uint4((uint32_t)e0, (uint32_t)(e0 >> 32), (uint32_t)e1, (uint32_t)(e1 >> 32));
+                vb[k] = make_uint4((uint32_t)S1.c, (uint32_t)(S1.c >> 32), (uint32_t)S1.d, (uint32_t)(S1.d >> 32));
             }
         }
 #pragma unroll
@@ -253,6 +282,7 @@ KernelFn pick_load(int load) {
         case 1: return rank_kernel<K, 1, KIND>;
         case 2: return rank_kernel<K, 2, KIND>;
         case 3: return rank_kernel<K, 3, KIND>;
+        case 4: return rank_kernel<K, 4, KIND>;
         default: return nullptr;
     }
 }

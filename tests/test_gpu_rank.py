@@ -242,7 +242,7 @@ def test_out_of_range_and_bad_symbols():
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
-@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 1)])
+@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1)])
 @pytest.mark.parametrize("threads", [64, 256, 512])
 def test_every_tuning(k, load, layout, threads):
     from paper_2602_04103_gb300 import capi

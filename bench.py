@@ -369,6 +369,7 @@ def run_extras_other(args, stream, peak):
         torch.cuda.empty_cache()
     res.update(run_quadrank(args, stream, peak))
     res.update(run_fm(args, stream))
+    res.update(run_serving(args))
     return res
 
 
@@ -442,6 +443,53 @@ def run_fm(args, stream):
     return res
 
 
+def run_serving(args):
+    """QuadFm serving over a 2^28-char index: closed-loop capacity of the
+    continuous-batching server, then Poisson arrivals at fractions of that
+    capacity, for the batching server and the plain per-request path (one
+    request per launch, one at a time)."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    text, pats, off, first = workloads.serving_inputs(args.serve_requests, args.serve_log_n)
+    nreq = first.size - 1
+    npat = int(first[-1])
+    fidx = capi.qfm_build(torch.from_numpy(text).cuda(), text.size)
+    del text
+    res = {"serving_index_chars": 1 << args.serve_log_n, "serving_requests": nreq, "serving_patterns": npat,
+           "serving_mean_patterns_per_request": round(npat / nreq, 1)}
+    modes = {"batched": dict(slots=4), "per_request": dict(slots=1, max_requests_per_batch=1)}
+    ref = None
+
+    def replay(mode, arrival):
+        nonlocal ref
+        sv = capi.QFMServer(fidx, **modes[mode])
+        out = np.zeros(npat, np.uint64)
+        lat = np.zeros(nreq)
+        mk = sv.replay(pats, off, first, arrival, out, lat)
+        st = sv.stats()
+        sv.close()
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), "serving results differ between runs"
+        return {"patterns_per_s": round(npat / mk), "makespan_s": round(mk, 4),
+                "p50_ms": round(float(np.percentile(lat, 50)) / 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) / 1e3, 3),
+                "mean_requests_per_batch": round(st["mean_requests_per_batch"], 2)}
+
+    cap = {m: replay(m, np.zeros(nreq)) for m in modes}
+    res["serving_closed_loop"] = cap
+    capacity = cap["batched"]["patterns_per_s"]
+    rng = np.random.default_rng(55)
+    for f in (0.5, 0.8, 1.0, 1.2):
+        lam = f * capacity / (npat / nreq)                  # requests per second
+        arrival = np.cumsum(rng.exponential(1.0 / lam, nreq))
+        res[f"serving_poisson_{f}x"] = {m: replay(m, arrival) for m in modes}
+        log(f"[bench] serving {f}x: " + ", ".join(f"{m} {v['patterns_per_s'] / 1e6:.1f} M/s p99 {v['p99_ms']} ms"
+                                                  for m, v in res[f"serving_poisson_{f}x"].items()))
+    fidx.free()
+    return res
+
+
 def cpu_baseline(args, n, text, q):
     """The oracle as it stands on a bounded sample: the first 2^k queries,
     answered by one sort + linear sweep over the full text."""
@@ -503,14 +551,21 @@ def main():
     ap.add_argument("--layout", type=int, choices=[0, 1], default=None,
                     help="fixed layout for the headline (skips the tuned build and the probe)")
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
-    ap.add_argument("--only", choices=["fm", "quadrank"], default=None,
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-log-n", type=int, default=28)
+    ap.add_argument("--only", choices=["fm", "quadrank", "serving"], default=None,
                     help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
         stream = torch.cuda.current_stream()
-        res = run_fm(args, stream) if args.only == "fm" else run_quadrank(args, stream, peaks()[0])
+        if args.only == "fm":
+            res = run_fm(args, stream)
+        elif args.only == "serving":
+            res = run_serving(args)
+        else:
+            res = run_quadrank(args, stream, peaks()[0])
         print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":

@@ -1,7 +1,8 @@
 // Count-only backward search over the QuadFm index (paper App. E).
 //
 // qfm_count: one persistent launch.  Every warp takes pattern ids from a
-// device work queue (an atomic counter) in chunks of kChunk, keeps one search
+// device work queue (an atomic counter) in chunks of 64 (32 for small
+// batches), keeps one search
 // per lane, and refills a lane as soon as its search ends, so the lanes of a
 // warp stay busy despite uneven pattern lengths and early mismatches.  This is
 // the GPU form of the paper's query_batch: a batch of active searches where
@@ -18,7 +19,7 @@ namespace qr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kChunk = 64;  // pattern ids taken from the queue at once per warp
+constexpr uint32_t kChunkMax = 64;  // pattern ids taken from the queue at once per warp
 
 struct CountArgs {
     FmView v;
@@ -28,6 +29,7 @@ struct CountArgs {
     uint64_t* __restrict__ out;
     unsigned long long* queue;
     uint32_t* status;
+    uint32_t chunk;  // ids per queue grab: 64, or 32 when the batch is too small to fill the grid
 };
 
 // Start a search: the interval of the last 8 chars from the table (or the full
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
             uint64_t base = 0;
             if (avail < cnt) {
                 unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(a.queue, (unsigned long long)kChunk);
+                if (lane == 0) b = atomicAdd(a.queue, (unsigned long long)a.chunk);
                 base = __shfl_sync(0xffffffffu, (unsigned long long)b, 0);
             }
             if (!active) {
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
             }
             if (avail < cnt) {
                 pool_next = base + (cnt - avail);
-                pool_end = base + kChunk;
+                pool_end = base + a.chunk;
                 if (base >= a.m) drained = true;
             } else {
                 pool_next += cnt;
@@ -229,8 +231,11 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     a.out = out;
     a.queue = queue;
     a.status = idx->status;
-    uint64_t warps_needed = (m + kChunk - 1) / kChunk;
     uint64_t grid = persistent_grid(idx->policy);
+    // one queue grab per warp of 64 ids when there are enough patterns to
+    // keep every resident warp busy; smaller batches take 32 (one per lane)
+    a.chunk = m >= (uint64_t)grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
+    uint64_t warps_needed = (m + a.chunk - 1) / a.chunk;
     const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed) grid = blocks_needed;
     if (grid == 0) grid = 1;

@@ -57,6 +57,19 @@ def fm_inputs(log_n: int = 26, m: int = 10_000_000, len_min: int = 16, len_max: 
     return text, pats, off
 
 
+def serving_inputs(nreq: int = 2000, log_n: int = 28, seed_id: int = 5):
+    """(text codes, pattern bytes, offsets, request boundaries) of the serving
+    workload: request r holds patterns req_first[r] .. req_first[r+1], its size
+    uniform in 1..4096, pattern lengths uniform in 16..250, even patterns sampled
+    from the text with 1% substitutions, odd ones random."""
+    base = synth.base_seed(seed_id)
+    text = synth.fm_text(synth.substream(base, 1), 1 << log_n)
+    sizes = 1 + synth.queries(synth.substream(base, 6), 4095, nreq).astype(np.int64)   # 1..4096
+    req_first = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    pats, off = synth.patterns(synth.substream(base, 5), text, int(req_first[-1]), 16, 250, 0.01)
+    return text, pats, off, req_first
+
+
 def build_tuned(text_dev, n: int, sigma: int, q_dev, c=1, rank4: bool = False):
     """The benchmark's build: every layout within MAX_OVERHEAD[sigma], each
     autotuned on the first 2^24 queries, the fastest kept.

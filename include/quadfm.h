@@ -60,7 +60,8 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
  *   offsets   device array of m + 1 non-decreasing uint64.
  *   out       device array of m uint64.
  * The empty pattern counts n + 1 (every position 0..n).  A pattern holding a
- * byte > 3 yields 0 and sets QR_EBADSYM in the status.  The call allocates a
+ * byte > 3, or whose offsets are out of order (offsets[k+1] < offsets[k] or
+ * beyond offsets[m]), yields 0 and sets QR_EBADSYM in the status.  The call allocates a
  * 16-byte work-queue counter from the stream-ordered pool of the stream.
  * Errors: QR_EINVAL (null with m > 0), QR_ENOMEM, QR_ECUDA.
  */
@@ -170,7 +171,11 @@ int qfm_server_create(qfm_index* idx, const qfm_server_opts_t* opts, qfm_server*
 /* Queue one request of m >= 1 patterns (host memory, pattern k =
  * patterns[offsets[k] .. offsets[k+1])); counts go to out[0..m) (host).  The
  * buffers must stay untouched until the request completes.  Returns at once.
- * Errors: QR_EINVAL (NULL, decreasing offsets, larger than a slot). */
+ * When consecutive requests of a batch lie back to back in the same pinned
+ * buffers (patterns, offsets and out), the batch is copied straight from and
+ * to them; otherwise through the slot's pinned staging.  Malformed offsets
+ * give count 0 and QR_EBADSYM (see qfm_count).
+ * Errors: QR_EINVAL (NULL, offsets[m] < offsets[0], larger than a slot). */
 int qfm_server_submit(qfm_server* sv, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
                       uint64_t* request_id);
 

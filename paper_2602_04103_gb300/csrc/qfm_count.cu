@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
                 if (id < a.m) {
                     start = kKeep ? ld_u64_hint(a.off + id, pol_first) : a.off[id];
                     const uint64_t end = kKeep ? ld_u64_hint(a.off + id + 1, pol_first) : a.off[id + 1];
-                    if (end < start || !fm_start(a.v, a.pat + start, end - start, lo, hi, i)) {
-                        a.out[id] = 0;  // malformed: offsets decrease or a byte > 3
+                    if (end < start || end > total || !fm_start(a.v, a.pat + start, end - start, lo, hi, i)) {
+                        a.out[id] = 0;  // malformed: offsets out of order or a byte > 3
                         bad |= kStatusBadSym;
                     } else {
                         active = true;
@@ -172,7 +172,7 @@ __global__ void step_init(CountArgs a, StepState* __restrict__ st, unsigned long
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = a.off[k], e = a.off[k + 1];
         StepState x;
-        if (e < s || !fm_start(a.v, a.pat + s, e - s, x.lo, x.hi, x.i)) {
+        if (e < s || e > a.off[a.m] || !fm_start(a.v, a.pat + s, e - s, x.lo, x.hi, x.i)) {
             a.out[k] = 0;
             atomicOr(a.status, kStatusBadSym);
             x.i = -2;

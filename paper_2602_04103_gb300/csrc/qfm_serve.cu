@@ -45,6 +45,7 @@ struct Request {
     uint64_t* out = nullptr;          // host, m
     Clock::time_point t_submit, t_done;
     int status = 0;
+    bool pinned = false;              // pat, off and out are page-locked host memory
 };
 
 struct Slot {
@@ -59,6 +60,7 @@ struct Slot {
     cudaEvent_t done = nullptr;
     std::vector<Request*> reqs;
     bool busy = false;
+    bool direct = false;  // the batch was copied straight from / to the requests' buffers
 };
 
 }  // namespace
@@ -110,6 +112,20 @@ void free_slot(Slot& s) {
     if (s.done) cudaEventDestroy(s.done);
 }
 
+bool is_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// r follows prev back to back in the same buffers (patterns, offsets, out).
+bool adjacent(const Request* prev, const Request* r) {
+    return r->pinned && r->pat == prev->pat && r->off == prev->off + prev->m && r->out == prev->out + prev->m;
+}
+
 // Pack pending requests into slot s and launch; called with sv->mu held.
 int launch_batch(qfm_server* sv, Slot& s) {
     uint64_t np = 0, nb = 0;
@@ -118,26 +134,46 @@ int launch_batch(qfm_server* sv, Slot& s) {
         Request* r = sv->pending.front();
         if (np + r->m > sv->opt.max_batch_patterns || nb + r->bytes > sv->opt.max_batch_bytes) break;
         sv->pending.pop_front();
-        const uint64_t base = r->off[0];
-        std::memcpy(s.h_pat + nb, r->pat + base, r->bytes);
-        for (uint64_t k = 0; k < r->m; k++) s.h_off[np + k] = nb + (r->off[k] - base);
         np += r->m;
         nb += r->bytes;
         s.reqs.push_back(r);
     }
     if (s.reqs.empty()) return QR_OK;
-    s.h_off[np] = nb;
+    bool direct = s.reqs[0]->pinned;
+    for (size_t k = 1; k < s.reqs.size() && direct; k++) direct = adjacent(s.reqs[k - 1], s.reqs[k]);
+    s.direct = direct;
     sv->in_flight_requests += s.reqs.size();
     sv->batches++;
     sv->batched_requests += s.reqs.size();
     if (sv->opt.fail_after_batches > 0 && sv->batches > (uint64_t)sv->opt.fail_after_batches)
         return fail(QR_ECUDA, "qfm_server: injected launch failure (test hook)");
-    QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, s.h_pat, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
-    QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
+    const Request* r0 = s.reqs[0];
+    const uint8_t* d_pat = s.d_pat;
+    if (direct) {
+        // one copy of the pattern bytes and one of the offsets, straight from
+        // the requests' pinned buffers; the kernel sees the offsets as they
+        // are, through a pattern pointer shifted back by offsets[0]
+        const uint64_t base = r0->off[0];
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, r0->pat + base, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, r0->off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
+        d_pat = s.d_pat - base;
+    } else {
+        uint64_t p = 0, b = 0;
+        for (Request* r : s.reqs) {
+            const uint64_t base = r->off[0];
+            std::memcpy(s.h_pat + b, r->pat + base, r->bytes);
+            for (uint64_t k = 0; k < r->m; k++) s.h_off[p + k] = b + (r->off[k] - base);
+            p += r->m;
+            b += r->bytes;
+        }
+        s.h_off[np] = nb;
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, s.h_pat, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
+    }
     QR_CUDA_TRY(cudaMemsetAsync(s.d_queue, 0, 16, s.stream));
-    int rc = qr::launch_count(sv->idx, s.d_pat, s.d_off, np, s.d_out, s.d_queue, s.stream);
+    int rc = qr::launch_count(sv->idx, d_pat, s.d_off, np, s.d_out, s.d_queue, s.stream);
     if (rc) return rc;
-    QR_CUDA_TRY(cudaMemcpyAsync(s.h_out, s.d_out, np * 8, cudaMemcpyDeviceToHost, s.stream));
+    QR_CUDA_TRY(cudaMemcpyAsync(direct ? r0->out : s.h_out, s.d_out, np * 8, cudaMemcpyDeviceToHost, s.stream));
     QR_CUDA_TRY(cudaEventRecord(s.done, s.stream));
     s.busy = true;
     return QR_OK;
@@ -147,7 +183,7 @@ void finish_batch(qfm_server* sv, Slot& s, int status) {
     const auto now = Clock::now();
     uint64_t np = 0;
     for (Request* r : s.reqs) {
-        if (status == QR_OK) std::memcpy(r->out, s.h_out + np, r->m * 8);
+        if (status == QR_OK && !s.direct) std::memcpy(r->out, s.h_out + np, r->m * 8);
         np += r->m;
         r->status = status;
         r->t_done = now;
@@ -280,8 +316,7 @@ int qfm_server_submit(qfm_server* sv, const uint8_t* patterns, const uint64_t* o
                       uint64_t* request_id) {
     if (!sv || !offsets || (m > 0 && (!patterns || !out))) return fail(QR_EINVAL, "qfm_server_submit: NULL argument");
     if (m == 0) return fail(QR_EINVAL, "qfm_server_submit: empty request");
-    for (uint64_t k = 0; k < m; k++)
-        if (offsets[k + 1] < offsets[k]) return fail(QR_EINVAL, "qfm_server_submit: offsets decrease");
+    if (offsets[m] < offsets[0]) return fail(QR_EINVAL, "qfm_server_submit: offsets[m] < offsets[0]");
     const uint64_t bytes = offsets[m] - offsets[0];
     if (m > sv->opt.max_batch_patterns || bytes > sv->opt.max_batch_bytes)
         return fail(QR_EINVAL, "qfm_server_submit: request larger than a batch slot");
@@ -291,6 +326,7 @@ int qfm_server_submit(qfm_server* sv, const uint8_t* patterns, const uint64_t* o
     r->m = m;
     r->bytes = bytes;
     r->out = out;
+    r->pinned = is_pinned(patterns) && is_pinned(offsets) && is_pinned(out);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -46,20 +46,33 @@ def alone(idx, pats, off, first):
     return res
 
 
-@pytest.mark.parametrize("mode", ["batched", "per_request", "small_slots"])
+def pinned(a: np.ndarray) -> np.ndarray:
+    """A page-locked copy of a, as a numpy view of a pinned torch tensor."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t.numpy()
+
+
+@pytest.mark.parametrize("mode", ["batched", "per_request", "small_slots", "pinned_direct", "pinned_per_request"])
 def test_mixed_equals_alone(fm, mode):
     from paper_2602_04103_gb300 import capi
     text, idx = fm
     pats, off, first = make_requests(text, 200, 7)
     want = alone(idx, pats, off, first)
     opts = {"batched": dict(slots=4), "per_request": dict(slots=1, max_requests_per_batch=1),
-            "small_slots": dict(slots=3, max_batch_patterns=700, max_batch_bytes=700 * 250)}[mode]
+            "small_slots": dict(slots=3, max_batch_patterns=700, max_batch_bytes=700 * 250),
+            "pinned_direct": dict(slots=4), "pinned_per_request": dict(slots=1, max_requests_per_batch=1)}[mode]
     sv = capi.QFMServer(idx, **opts)
-    out = np.full(off.size - 1, np.uint64(2 ** 64 - 1))
+    if mode.startswith("pinned"):
+        # back-to-back requests in page-locked buffers: batches copy straight from them
+        pats, off = pinned(pats), pinned(off)
+        out = pinned(np.full(off.size - 1, np.uint64(2 ** 64 - 1)))
+    else:
+        out = np.full(off.size - 1, np.uint64(2 ** 64 - 1))
     offs = []
     for r in range(first.size - 1):
         a, b = int(first[r]), int(first[r + 1])
-        offs.append(np.ascontiguousarray(off[a:b + 1]))
+        offs.append(off[a:b + 1] if mode.startswith("pinned") else np.ascontiguousarray(off[a:b + 1]))
         sv.submit(pats, offs[-1], out[a:b])
     sv.drain(120)
     ids, lat, st = sv.poll(1000)
@@ -77,16 +90,19 @@ def test_mixed_equals_alone(fm, mode):
     assert np.array_equal(out[sample], oracle.count_brute_batch(text, sub, sub_off))
 
 
-def test_replay_poisson_trace(fm):
+@pytest.mark.parametrize("pin", [False, True])
+def test_replay_poisson_trace(fm, pin):
     from paper_2602_04103_gb300 import capi
     text, idx = fm
     pats, off, first = make_requests(text, 300, 11)
     want = alone(idx, pats, off, first)
+    if pin:
+        pats, off = pinned(pats), pinned(off)
     rng = np.random.default_rng(3)
     arrival = np.cumsum(rng.exponential(1e-4, 300))
     for opts in (dict(slots=4), dict(slots=1, max_requests_per_batch=1)):
         sv = capi.QFMServer(idx, **opts)
-        out = np.zeros(off.size - 1, np.uint64)
+        out = pinned(np.zeros(off.size - 1, np.uint64)) if pin else np.zeros(off.size - 1, np.uint64)
         lat = np.zeros(300)
         mk = sv.replay(pats, off, first, arrival, out, lat)
         assert np.array_equal(out, want)
@@ -105,8 +121,15 @@ def test_admission_limits_and_injected_failure(fm):
     if big.size - 1 > 100:
         with pytest.raises(capi.QRError):  # a request larger than a batch slot
             sv.submit(pats, big, np.zeros(big.size - 1, np.uint64))
-    with pytest.raises(capi.QRError):      # decreasing offsets
+    with pytest.raises(capi.QRError):      # offsets[m] < offsets[0]
         sv.submit(pats, np.array([5, 3], np.uint64), np.zeros(1, np.uint64))
+    # offsets out of order inside a request: that pattern counts 0 and sets the status bit
+    pats2 = np.zeros(64, np.uint8)
+    out2 = np.full(2, np.uint64(7))
+    sv.submit(pats2, np.array([0, 40, 20], np.uint64), out2)
+    sv.drain(30)
+    assert out2[0] == 0
+    assert capi.qfm_status(idx) == capi.QR_EBADSYM
     sv.close()
     # batches after the second fail on the host: their requests report the error
     sv = capi.QFMServer(idx, slots=1, max_requests_per_batch=1, fail_after_batches=2)

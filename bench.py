@@ -555,7 +555,7 @@ def main():
     ap.add_argument("--layout", type=int, choices=[0, 1], default=None,
                     help="fixed layout for the headline (skips the tuned build and the probe)")
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=8000)
     ap.add_argument("--serve-log-n", type=int, default=28)
     ap.add_argument("--only", choices=["fm", "quadrank", "serving"], default=None,
                     help="run one extra row alone and print it (profiling runs)")

@@ -63,6 +63,52 @@ __device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, 
     return quad_finish1(s, quad_delta(lo64(v0), hi64(v0), c), x, slot, c);
 }
 
+// The words one rank query needs from its line, fetched as 32-byte sectors:
+// sector 0 (deltas + the lower half) for slots below 128; the first 16 bytes
+// (deltas) and sector 1 for the upper half.
+struct FmLine {
+    uint64_t d0, d1;     // words 0 and 1 (deltas in their low 32 bits)
+    uint64_t x[4];       // the 4 words of the needed half
+};
+
+template <bool KEEP>
+__device__ __forceinline__ FmLine fm_fetch(const uint4* L, bool upper, uint64_t pol) {
+    FmLine f;
+    if (upper) {
+        const uint4 v0 = KEEP ? ld_line16_hint(L, pol) : ld_line16(L);
+        const u64x4 s1 = KEEP ? ld_line32_hint(L + 2, pol) : ld_line32(L + 2);
+        f.d0 = lo64(v0); f.d1 = hi64(v0);
+        f.x[0] = s1.a; f.x[1] = s1.b; f.x[2] = s1.c; f.x[3] = s1.d;
+    } else {
+        const u64x4 s0 = KEEP ? ld_line32_hint(L, pol) : ld_line32(L);
+        f.d0 = s0.a; f.d1 = s0.b;
+        f.x[0] = s0.a; f.x[1] = s0.b; f.x[2] = s0.c; f.x[3] = s0.d;
+    }
+    return f;
+}
+
+// LF of both interval ends for symbol c.  When lo and hi fall in the same
+// half-line (the interval is narrow, the usual case after a few steps) the
+// words are fetched once.  The $ row (stored as code 0) is removed from the
+// count of c = 0 when it lies before the position.
+template <bool KEEP>
+__device__ __forceinline__ void fm_lf_pair(const FmView& v, uint64_t& lo, uint64_t& hi, int c, uint64_t pol) {
+    const uint64_t jl = div224(lo), jh = div224(hi);
+    const uint32_t sl = (uint32_t)(lo - jl * kB4) + 32, sh = (uint32_t)(hi - jh * kB4) + 32;
+    const bool ul = sl >= 128, uh = sh >= 128;
+    const uint32_t* sp = (const uint32_t*)v.supers + c;
+    const uint32_t s_lo = KEEP ? ld_u32_hint(sp + 4 * (jl >> 8), pol) : __ldg(sp + 4 * (jl >> 8));
+    const uint32_t s_hi = jl >> 8 == jh >> 8 ? s_lo : (KEEP ? ld_u32_hint(sp + 4 * (jh >> 8), pol) : __ldg(sp + 4 * (jh >> 8)));
+    const FmLine fl = fm_fetch<KEEP>(v.lines + 4 * jl, ul, pol);
+    const FmLine fh = (jl == jh && ul == uh) ? fl : fm_fetch<KEEP>(v.lines + 4 * jh, uh, pol);
+    uint64_t rl = quad_finish1(s_lo, quad_delta(fl.d0, fl.d1, c), fl.x, sl, c);
+    uint64_t rh = quad_finish1(s_hi, quad_delta(fh.d0, fh.d1, c), fh.x, sh, c);
+    if (c == 0 && lo > v.dollar) rl -= 1;
+    if (c == 0 && hi > v.dollar) rh -= 1;
+    lo = v.C[c] + rl;
+    hi = v.C[c] + rh;
+}
+
 // LF step of one interval end: C[c] + rank(q, c), where the $ row (stored as
 // code 0) is removed from the count of c = 0 when it lies before q.
 template <bool KEEP = false>

@@ -147,8 +147,7 @@ __global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
                     bad |= kStatusBadSym;
                     active = false;
                 } else {
-                    lo = fm_lf<kKeep>(a.v, lo, c, pol_last);
-                    hi = fm_lf<kKeep>(a.v, hi, c, pol_last);
+                    fm_lf_pair<kKeep>(a.v, lo, hi, c, pol_last);
                     --i;
                 }
             }

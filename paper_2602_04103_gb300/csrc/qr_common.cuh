@@ -101,6 +101,11 @@ __device__ __forceinline__ uint4 ld_line16(const uint4* p) {
                  : "l"(p));
     return v;
 }
+// Four 64-bit words of one 32-byte sector.
+struct u64x4 {
+    uint64_t a, b, c, d;
+};
+
 // L2 cache policies (createpolicy, sm_80+) and loads that carry them: an
 // evict-last policy for an index that should stay L2-resident while other
 // data streams through, an evict-first policy for data read once.
@@ -118,6 +123,13 @@ __device__ __forceinline__ uint4 ld_line16_hint(const uint4* p, uint64_t pol) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ u64x4 ld_line32_hint(const uint4* p, uint64_t pol) {
+    u64x4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b64 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=l"(v.a), "=l"(v.b), "=l"(v.c), "=l"(v.d)
                  : "l"(p), "l"(pol));
     return v;
 }
@@ -146,9 +158,6 @@ __device__ __forceinline__ void st_stream_u64(uint64_t* p, uint64_t v) {
     asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 // 32-byte loads (sm_100+ 256-bit vector load): one instruction per sector.
-struct u64x4 {
-    uint64_t a, b, c, d;
-};
 __device__ __forceinline__ u64x4 ld_line32(const uint4* p) {
     u64x4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.b64 {%0,%1,%2,%3}, [%4];"

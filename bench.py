@@ -557,7 +557,7 @@ def main():
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
     ap.add_argument("--serve-requests", type=int, default=8000)
     ap.add_argument("--serve-log-n", type=int, default=28)
-    ap.add_argument("--only", choices=["fm", "quadrank", "serving"], default=None,
+    ap.add_argument("--only", choices=["fm", "quadrank", "serving", "probe"], default=None,
                     help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
@@ -568,6 +568,9 @@ def main():
             res = run_fm(args, stream)
         elif args.only == "serving":
             res = run_serving(args)
+        elif args.only == "probe":
+            res = {"random_32B_requests_G_per_s": round(probe_ceiling(stream), 3),
+                   "probe": "qr_probe_gather: 2^26 random 32-byte loads over a 4 GiB buffer, 4 in flight per thread"}
         else:
             res = run_quadrank(args, stream, peaks()[0])
         print(json.dumps(res), flush=True)

@@ -85,7 +85,7 @@ __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uin
 }
 
 template <int POLICY>
-__global__ void __launch_bounds__(kThreads) count_persistent(CountArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
     constexpr bool kKeep = POLICY == kFmPolicyKeepIndex;
     const uint64_t pol_last = kKeep ? l2_policy_evict_last() : 0;
     const uint64_t pol_first = kKeep ? l2_policy_evict_first() : 0;

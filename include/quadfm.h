@@ -4,7 +4,7 @@
  * backward search over a QuadRank16 structure holding the BWT.
  *
  * Source: R. Groot Koerkamp, "QuadRank: Engineering a High Throughput Rank",
- * arXiv 2602.04103, App. E ("QuadFm: A Batching FM-index").  Conventions
+ * arXiv 2602.04103, App. D ("QuadFm: A Batching FM-index").  Conventions
  * (return codes, streams, ownership, status bits) are those of quadrank.h.
  */
 #ifndef QUADFM_H
@@ -33,7 +33,7 @@ typedef struct {
 
 /*
  * qfm_build -- build the count-only FM-index of a DNA text.
- * Paper: App. E (QuadFm: one sentinel $ whose BWT position is stored, the
+ * Paper: App. D (QuadFm: one sentinel $ whose BWT position is stored, the
  * BWT held in a QuadRank16 structure, an 8-character prefix lookup table that
  * replaces the first 8 search steps).  The paper does not describe suffix
  * array construction; this library sorts the suffixes of T$ by prefix
@@ -52,7 +52,7 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
  * queue (an atomic counter), each lane runs one backward search (8-mer table,
  * then LF steps lo = C[c] + rank(lo, c) - [c = 0 and lo > dollar_row], same for
  * hi, while lo < hi), and a lane whose search ends is refilled at once.
- * Paper: App. E (query_batch: a batch of active searches, finished ones
+ * Paper: App. D (query_batch: a batch of active searches, finished ones
  * swapped out, rank + LF for the rest), Sec. 4 rank1.
  *   patterns  device bytes 0..3, pattern k = patterns[offsets[k] .. offsets[k+1]);
  *             the whole range [patterns, patterns + offsets[m]) must be readable
@@ -130,7 +130,7 @@ int qfm_free(qfm_index* idx);
 /* Continuous-batching server over one index                               */
 /* ---------------------------------------------------------------------- */
 /*
- * The paper processes reads in batches inside each thread (App. E); this
+ * The paper processes reads in batches inside each thread (App. D); this
  * server is the host runtime that turns a stream of independent count
  * requests into such batches on the GPU.  A worker thread owns `slots` batch
  * slots (device buffers carved from budget_bytes, pinned staging, a stream).

@@ -2,7 +2,7 @@
 
 ctypes wrapper over ``oracle.c``: plain CPU definitions of rank, rank_4, the
 suffix array / BWT of T$ and pattern occurrence counts (QuadRank paper,
-Sec. 1 rank definition, Sec. 4 rank_4, App. E count-only FM-index).
+Sec. 1 rank definition, Sec. 4 rank_4, App. D count-only FM-index).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path

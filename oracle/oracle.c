@@ -12,10 +12,10 @@
  *   rank(q)    = rank(q, 1) for the binary alphabet          (Sec. 1, Sec. 3)
  *   rank_4(q)  = (rank(q,0), rank(q,1), rank(q,2), rank(q,3)) (Sec. 4, rank_4)
  *   count(P)   = number of positions i with T[i .. i+|P|) = P, the quantity a
- *                count-only FM-index returns (App. E); equivalently the size
+ *                count-only FM-index returns (App. D); equivalently the size
  *                of the suffix-array interval of suffixes of T$ prefixed by P.
  * The suffix array is the textbook one: all suffixes of T$ sorted, with the
- * sentinel $ smaller than every symbol (App. E stores one sentinel).
+ * sentinel $ smaller than every symbol (App. D stores one sentinel).
  *
  * Formats: bit text  bit i = (w[i/64] >> (i%64)) & 1;
  *          DNA text  char i = (w[i/32] >> (2*(i%32))) & 3 (A=0,C=1,G=2,T=3);
@@ -215,7 +215,7 @@ int or_count_brute_batch(const uint8_t* codes, uint64_t n, const uint8_t* pats, 
 
 /*
  * Work of the count-only backward search with a k-character prefix table
- * (App. E): the table gives the interval of the last k pattern characters
+ * (App. D): the table gives the interval of the last k pattern characters
  * without any rank query, then one LF step (two rank queries) is taken per
  * remaining character while the interval is non-empty.  A pattern shorter than
  * k starts from the full interval and steps through all its characters.

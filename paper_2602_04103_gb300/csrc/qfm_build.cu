@@ -1,4 +1,4 @@
-// Builder of the count-only FM-index (paper App. E): suffix array of T$ by
+// Builder of the count-only FM-index (paper App. D): suffix array of T$ by
 // prefix doubling on the GPU, BWT with the sentinel's row recorded and its
 // symbol stored as code 0, a QuadRank16 index over the BWT, the C array, and
 // the 8-mer prefix table.  The paper does not describe suffix sorting; prefix

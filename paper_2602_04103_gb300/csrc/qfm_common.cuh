@@ -4,7 +4,7 @@
 
 #include "qr_common.cuh"
 
-constexpr int kQfmK = 8;                  // prefix-table length (paper App. E)
+constexpr int kQfmK = 8;                  // prefix-table length (paper App. D)
 constexpr uint64_t kQfmTable = 1ull << 16; // 4^8 entries
 
 // Opaque handle of a count-only FM-index (see quadfm.h).

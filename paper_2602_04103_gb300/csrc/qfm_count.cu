@@ -1,4 +1,4 @@
-// Count-only backward search over the QuadFm index (paper App. E).
+// Count-only backward search over the QuadFm index (paper App. D).
 //
 // qfm_count: one persistent launch.  Every warp takes pattern ids from a
 // device work queue (an atomic counter) in chunks of 64 (32 for small

@@ -2,7 +2,7 @@
 (2^26-char text with planted repeats, patterns of length 16..150, half
 sampled with 1% substitutions), computed by the oracle only.
 
-The count-only search (QuadRank paper, App. E) spends one LF step -- two rank
+The count-only search (QuadRank paper, App. D) spends one LF step -- two rank
 queries -- per pattern character after the 8-character table lookup while the
 interval is non-empty; oracle.fm_steps counts those steps from the suffix
 array of T$.  The benchmark multiplies the mean by the number of patterns to

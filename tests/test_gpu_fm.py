@@ -2,7 +2,7 @@
 
 The suffix array of T$ is unique, so the GPU's prefix-doubling SA is compared
 row by row with the oracle's comparison sort; the BWT, the $ row, C and the
-8-mer table follow from their definitions (QuadRank paper, App. E); counts
+8-mer table follow from their definitions (QuadRank paper, App. D); counts
 from the persistent kernel and the per-step baseline are compared with the
 oracle's SA-interval counts and brute-force counts.
 """

@@ -4,7 +4,7 @@ brute-force counts and the LF-step count.
 Ties: a hand-worked fixture (GATTACA), Python's own sort of suffix strings,
 ``re`` overlapping-match counts, closed forms on A^n and (ACGT)^r, and the
 extension invariant sum_c count(cP) = count(P) - [T starts with P]
-(QuadRank paper, App. E: count-only FM-index with one sentinel).
+(QuadRank paper, App. D: count-only FM-index with one sentinel).
 """
 import re
 

@@ -152,16 +152,23 @@ typedef struct {
     uint64_t max_batch_bytes;       /* pattern bytes per batch (same)                   */
     int32_t poll_us;                /* worker's completion-poll interval                */
     int32_t fail_after_batches;     /* test hook: > 0 makes batch k+1 fail on the host  */
+    int32_t use_graph;              /* 1: each batch is one launch of the slot's CUDA   */
+                                    /*    graph (copy in, reset queue, count, copy out) */
+                                    /*    with updated node parameters; 0: stream calls */
+    int32_t reserved;
 } qfm_server_opts_t;
 
 typedef struct {
     uint64_t submitted, completed, pending, in_flight, batches;
     double mean_requests_per_batch;
     int32_t error;                  /* first error of the server (QR_OK if none)        */
+    int32_t reserved;
+    uint64_t graph_batches;         /* batches launched as one CUDA graph                */
 } qfm_server_stats_t;
 
 /* Fill *opts with defaults: 1 GiB budget, 4 slots, 2^20 patterns and 64 MiB
- * of pattern bytes per batch, no limit on requests per batch, 20 us poll. */
+ * of pattern bytes per batch, no limit on requests per batch, 20 us poll,
+ * batches launched as CUDA graphs. */
 int qfm_server_default_opts(qfm_server_opts_t* opts);
 
 /* Start a server (allocates the slots; the index must outlive it).

@@ -299,12 +299,13 @@ def qfm_status(idx: QFMIndex, stream=None) -> int:
 class qfm_server_opts_t(C.Structure):
     _fields_ = [("budget_bytes", u64), ("slots", C.c_int32), ("max_requests_per_batch", C.c_int32),
                 ("max_batch_patterns", u64), ("max_batch_bytes", u64), ("poll_us", C.c_int32),
-                ("fail_after_batches", C.c_int32)]
+                ("fail_after_batches", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
 
 
 class qfm_server_stats_t(C.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("pending", u64), ("in_flight", u64), ("batches", u64),
-                ("mean_requests_per_batch", C.c_double), ("error", C.c_int32)]
+                ("mean_requests_per_batch", C.c_double), ("error", C.c_int32), ("reserved", C.c_int32),
+                ("graph_batches", u64)]
 
 
 _sig("qfm_server_default_opts", [C.POINTER(qfm_server_opts_t)])

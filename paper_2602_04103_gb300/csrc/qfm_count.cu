@@ -244,6 +244,37 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     return QR_OK;
 }
 
+// Kernel-node parameters of the same launch, for callers that put it in a CUDA
+// graph: `args` (at least sizeof(CountArgs) bytes, 16-byte aligned) receives
+// the argument block that p->kernelParams points to.
+int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
+                        unsigned long long* queue, void* args, size_t args_bytes, cudaKernelNodeParams* p,
+                        void** param_slot) {
+    if (args_bytes < sizeof(CountArgs)) return fail(QR_EINVAL, "count_kernel_params: argument block too small");
+    CountArgs* a = (CountArgs*)args;
+    fm_view(idx, &a->v);
+    a->pat = pat;
+    a->off = off;
+    a->m = m;
+    a->out = out;
+    a->queue = queue;
+    a->status = idx->status;
+    uint64_t grid = persistent_grid(idx->policy);
+    a->chunk = m >= grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
+    const uint64_t warps_needed = (m + a->chunk - 1) / a->chunk;
+    const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+    if (grid > blocks_needed) grid = blocks_needed;
+    if (grid == 0) grid = 1;
+    *param_slot = a;
+    p->func = idx->policy == kFmPolicyKeepIndex ? (void*)count_persistent<1> : (void*)count_persistent<0>;
+    p->gridDim = dim3((unsigned)grid);
+    p->blockDim = dim3(kThreads);
+    p->sharedMemBytes = 0;
+    p->kernelParams = param_slot;
+    p->extra = nullptr;
+    return QR_OK;
+}
+
 int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                           cudaStream_t s) {
     CountArgs a;

@@ -27,6 +27,9 @@
 namespace qr {
 int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                  unsigned long long* queue, cudaStream_t s);
+int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
+                        unsigned long long* queue, void* args, size_t args_bytes, cudaKernelNodeParams* p,
+                        void** param_slot);
 }
 using qr::cuda_fail;
 using qr::fail;
@@ -61,6 +64,13 @@ struct Slot {
     std::vector<Request*> reqs;
     bool busy = false;
     bool direct = false;  // the batch was copied straight from / to the requests' buffers
+    // the batch as one CUDA graph: copy in patterns, copy in offsets, reset
+    // the queue, count, copy out; each batch updates the node parameters
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_pat = nullptr, n_off = nullptr, n_set = nullptr, n_ker = nullptr, n_out = nullptr;
+    alignas(16) unsigned char args[512];
+    void* arg_slot = nullptr;
 };
 
 }  // namespace
@@ -74,7 +84,7 @@ struct qfm_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> pending;
     std::deque<Request*> finished;   // completed, not yet polled
-    uint64_t next_id = 0, submitted = 0, completed = 0, batches = 0, batched_requests = 0;
+    uint64_t next_id = 0, submitted = 0, completed = 0, batches = 0, batched_requests = 0, graph_batches = 0;
     uint64_t in_flight_requests = 0;
     int error = QR_OK;
     std::string error_msg;
@@ -96,11 +106,59 @@ int alloc_slot(qfm_server* sv, Slot& s) {
     QR_CUDA_TRY(cudaMallocHost((void**)&s.h_out, P * 8));
     QR_CUDA_TRY(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
     QR_CUDA_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    if (sv->opt.use_graph) {
+        // nodes sized for a full slot; every batch overwrites their parameters
+        QR_CUDA_TRY(cudaGraphCreate(&s.graph, 0));
+        QR_CUDA_TRY(cudaGraphAddMemcpyNode1D(&s.n_pat, s.graph, nullptr, 0, s.d_pat, s.h_pat, Bb,
+                                             cudaMemcpyHostToDevice));
+        QR_CUDA_TRY(cudaGraphAddMemcpyNode1D(&s.n_off, s.graph, &s.n_pat, 1, s.d_off, s.h_off, (P + 1) * 8,
+                                             cudaMemcpyHostToDevice));
+        cudaMemsetParams ms{};
+        ms.dst = s.d_queue;
+        ms.elementSize = 4;
+        ms.width = 4;
+        ms.height = 1;
+        ms.value = 0;
+        QR_CUDA_TRY(cudaGraphAddMemsetNode(&s.n_set, s.graph, &s.n_off, 1, &ms));
+        cudaKernelNodeParams kp{};
+        int rc = qr::count_kernel_params(sv->idx, s.d_pat, s.d_off, P, s.d_out, s.d_queue, s.args, sizeof(s.args),
+                                         &kp, &s.arg_slot);
+        if (rc) return rc;
+        QR_CUDA_TRY(cudaGraphAddKernelNode(&s.n_ker, s.graph, &s.n_set, 1, &kp));
+        QR_CUDA_TRY(cudaGraphAddMemcpyNode1D(&s.n_out, s.graph, &s.n_ker, 1, s.h_out, s.d_out, P * 8,
+                                             cudaMemcpyDeviceToHost));
+        QR_CUDA_TRY(cudaGraphInstantiate(&s.exec, s.graph, 0));
+    }
     return QR_OK;
+}
+
+// Point the slot's graph at this batch and launch it; false if the driver
+// refused an update (the caller then launches the batch on the stream).
+bool launch_graph(qfm_server* sv, Slot& s, const void* src_pat, uint64_t nb, const uint64_t* src_off, uint64_t np,
+                  const uint8_t* d_pat, uint64_t* dst_out) {
+    if (!s.exec) return false;
+    cudaKernelNodeParams kp{};
+    if (qr::count_kernel_params(sv->idx, d_pat, s.d_off, np, s.d_out, s.d_queue, s.args, sizeof(s.args), &kp,
+                                &s.arg_slot) != QR_OK)
+        return false;
+    bool ok = cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_pat, s.d_pat, src_pat, nb ? nb : 1,
+                                                 cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_off, s.d_off, src_off, (np + 1) * 8,
+                                                 cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaGraphExecKernelNodeSetParams(s.exec, s.n_ker, &kp) == cudaSuccess &&
+              cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_out, dst_out, s.d_out, np * 8,
+                                                 cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return false;
+    }
+    return cudaGraphLaunch(s.exec, s.stream) == cudaSuccess;
 }
 
 void free_slot(Slot& s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
     cudaFree(s.d_pat);
     cudaFree(s.d_off);
     cudaFree(s.d_out);
@@ -149,15 +207,7 @@ int launch_batch(qfm_server* sv, Slot& s) {
         return fail(QR_ECUDA, "qfm_server: injected launch failure (test hook)");
     const Request* r0 = s.reqs[0];
     const uint8_t* d_pat = s.d_pat;
-    if (direct) {
-        // one copy of the pattern bytes and one of the offsets, straight from
-        // the requests' pinned buffers; the kernel sees the offsets as they
-        // are, through a pattern pointer shifted back by offsets[0]
-        const uint64_t base = r0->off[0];
-        QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, r0->pat + base, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
-        QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, r0->off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
-        d_pat = s.d_pat - base;
-    } else {
+    if (!direct) {
         uint64_t p = 0, b = 0;
         for (Request* r : s.reqs) {
             const uint64_t base = r->off[0];
@@ -167,6 +217,26 @@ int launch_batch(qfm_server* sv, Slot& s) {
             b += r->bytes;
         }
         s.h_off[np] = nb;
+    }
+    if (sv->opt.use_graph) {
+        const uint64_t base = direct ? r0->off[0] : 0;
+        if (launch_graph(sv, s, direct ? (const void*)(r0->pat + base) : (const void*)s.h_pat, nb,
+                         direct ? r0->off : s.h_off, np, s.d_pat - base, direct ? r0->out : s.h_out)) {
+            QR_CUDA_TRY(cudaEventRecord(s.done, s.stream));
+            s.busy = true;
+            sv->graph_batches++;
+            return QR_OK;
+        }
+    }
+    if (direct) {
+        // one copy of the pattern bytes and one of the offsets, straight from
+        // the requests' pinned buffers; the kernel sees the offsets as they
+        // are, through a pattern pointer shifted back by offsets[0]
+        const uint64_t base = r0->off[0];
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, r0->pat + base, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
+        QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, r0->off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
+        d_pat = s.d_pat - base;
+    } else {
         QR_CUDA_TRY(cudaMemcpyAsync(s.d_pat, s.h_pat, nb ? nb : 1, cudaMemcpyHostToDevice, s.stream));
         QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
     }
@@ -280,6 +350,7 @@ int qfm_server_default_opts(qfm_server_opts_t* o) {
     o->max_batch_bytes = 64ull << 20;
     o->poll_us = 20;
     o->fail_after_batches = 0;
+    o->use_graph = 1;
     return QR_OK;
 }
 
@@ -384,6 +455,7 @@ int qfm_server_stats(qfm_server* sv, qfm_server_stats_t* st) {
     st->in_flight = sv->in_flight_requests;
     st->batches = sv->batches;
     st->mean_requests_per_batch = sv->batches ? (double)sv->batched_requests / sv->batches : 0.0;
+    st->graph_batches = sv->graph_batches;
     st->error = sv->error;
     return QR_OK;
 }

@@ -53,7 +53,8 @@ def pinned(a: np.ndarray) -> np.ndarray:
     return t.numpy()
 
 
-@pytest.mark.parametrize("mode", ["batched", "per_request", "small_slots", "pinned_direct", "pinned_per_request"])
+@pytest.mark.parametrize("mode", ["batched", "per_request", "small_slots", "pinned_direct", "pinned_per_request",
+                                  "stream_calls", "pinned_stream_calls"])
 def test_mixed_equals_alone(fm, mode):
     from paper_2602_04103_gb300 import capi
     text, idx = fm
@@ -61,7 +62,8 @@ def test_mixed_equals_alone(fm, mode):
     want = alone(idx, pats, off, first)
     opts = {"batched": dict(slots=4), "per_request": dict(slots=1, max_requests_per_batch=1),
             "small_slots": dict(slots=3, max_batch_patterns=700, max_batch_bytes=700 * 250),
-            "pinned_direct": dict(slots=4), "pinned_per_request": dict(slots=1, max_requests_per_batch=1)}[mode]
+            "pinned_direct": dict(slots=4), "pinned_per_request": dict(slots=1, max_requests_per_batch=1),
+            "stream_calls": dict(slots=4, use_graph=0), "pinned_stream_calls": dict(slots=4, use_graph=0)}[mode]
     sv = capi.QFMServer(idx, **opts)
     if mode.startswith("pinned"):
         # back-to-back requests in page-locked buffers: batches copy straight from them
@@ -80,6 +82,11 @@ def test_mixed_equals_alone(fm, mode):
     assert np.array_equal(out, want)
     stats = sv.stats()
     assert stats["completed"] == 200 and stats["error"] == 0
+    # each batch is one launch of the slot's CUDA graph unless graphs are off
+    if "stream_calls" in mode:
+        assert stats["graph_batches"] == 0
+    else:
+        assert stats["graph_batches"] == stats["batches"]
     if mode == "per_request":
         assert stats["mean_requests_per_batch"] == 1.0
     sv.close()

@@ -462,6 +462,8 @@ def run_serving(args):
     res = {"serving_index_chars": 1 << args.serve_log_n, "serving_requests": nreq, "serving_patterns": npat,
            "serving_mean_patterns_per_request": round(npat / nreq, 1)}
     modes = {"batched": dict(slots=4), "per_request": dict(slots=1, max_requests_per_batch=1)}
+    if args.serve_stream_calls:
+        modes["batched_stream_calls"] = dict(slots=4, use_graph=0)
     ref = None
 
     def replay(mode, arrival):
@@ -557,6 +559,8 @@ def main():
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
     ap.add_argument("--serve-requests", type=int, default=8000)
     ap.add_argument("--serve-log-n", type=int, default=28)
+    ap.add_argument("--serve-stream-calls", action="store_true",
+                    help="also run the batching server without CUDA graphs")
     ap.add_argument("--only", choices=["fm", "quadrank", "serving", "probe"], default=None,
                     help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()

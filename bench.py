@@ -520,7 +520,7 @@ def run_reference(args):
         return
     n = 1 << args.log_n
     text, q = workloads.birank_inputs(args.log_n, args.log_m)
-    sample = q[: 1 << args.cpu_log_sample].copy()
+    sample = q[: 1 << args.ref_log_sample].copy()
     for _ in range(args.warmup):
         oracle.rank(text, n, 2, sample[: 1 << 12], 1)
     t0 = time.perf_counter()
@@ -534,7 +534,7 @@ def run_reference(args):
             "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
                                    f"uniform uint64 queries per GPU", "n_bits": n, "queries_per_gpu": 1 << args.log_m},
             "cpu_baseline": {"value": round(value, 6), "unit": "Gqueries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"2^{args.cpu_log_sample} of the queries per step (sort + one sweep over "
+                             "sample": f"2^{args.ref_log_sample} of the queries per step (sort + one sweep over "
                                        f"the full text)"},
             "e2e": {"value": round(value, 6), "unit": "Gqueries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -551,7 +551,10 @@ def main():
     ap.add_argument("--log-n4", type=int, default=32)
     ap.add_argument("--fm-log-n", type=int, default=26)
     ap.add_argument("--fm-m", type=int, default=10_000_000)
-    ap.add_argument("--cpu-log-sample", type=int, default=22)
+    ap.add_argument("--cpu-log-sample", type=int, default=25,
+                    help="log2 of the queries the CPU oracle answers for cpu_baseline (~10 s on one core)")
+    ap.add_argument("--ref-log-sample", type=int, default=23,
+                    help="log2 of the queries per step of --impl reference")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--layout", type=int, choices=[0, 1], default=None,

@@ -426,9 +426,16 @@ def run_fm(args, stream):
     ref = o.clone()
     ms_s = best_ms(lambda: capi.qfm_count_stepwise(fidx, dp, doff, o), stream)
     assert torch.equal(ref, o)
+    # both strands in one launch (the paper's read-counting benchmark counts each read forward
+    # and reverse-complemented)
+    o2 = torch.empty(2 * m, dtype=torch.int64, device="cuda")
+    ms_b = best_ms(lambda: capi.qfm_count_ex(fidx, dp, doff, o2, capi.QFM_BOTH_STRANDS), stream)
+    assert torch.equal(o2[:m], ref)
     assert capi.qfm_status(fidx) == 0
     res = {"qfm_count_persistent": {"patterns_per_s": round(m / (ms_p * 1e-3)), "ms": round(ms_p, 3)},
            "qfm_count_stepwise": {"patterns_per_s": round(m / (ms_s * 1e-3)), "ms": round(ms_s, 3)},
+           "qfm_count_both_strands": {"reads_per_s": round(m / (ms_b * 1e-3)), "searches_per_s": round(2 * m / (ms_b * 1e-3)),
+                                      "ms": round(ms_b, 3)},
            "qfm_speedup_persistent_vs_stepwise": round(ms_s / ms_p, 2),
            "qfm_build_s": round(t_build, 3), "qfm_index_bytes": info["bytes_rank"] + info["bytes_table"]}
     work = ROOT / "tests" / "golden" / "fm_work_config4.json"

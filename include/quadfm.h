@@ -69,6 +69,19 @@ int qfm_count(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, 
               void* stream);
 
 /*
+ * qfm_count_ex -- qfm_count with flags.  QFM_BOTH_STRANDS also counts the
+ * reverse complement of every pattern (A<->T, C<->G, reversed), as the paper's
+ * QuadFm benchmark counts each read in both directions (App. D): out then
+ * holds 2 m counts, out[k] for pattern k and out[m + k] for its reverse
+ * complement, all from the same persistent launch (the reverse complement is
+ * read from the pattern bytes on the fly).  Other arguments and errors as
+ * qfm_count; unknown flags give QR_EINVAL.
+ */
+#define QFM_BOTH_STRANDS 2
+int qfm_count_ex(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
+                 int flags, void* stream);
+
+/*
  * qfm_count_stepwise -- the same counts with one kernel launch per search step
  * (the plain form: a table-lookup launch, then launches that each advance
  * every active search by one character).  Kept as the comparison baseline.

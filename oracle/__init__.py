@@ -59,6 +59,7 @@ def _load():
         lib.or_count_brute.argtypes = [_P, u64, _P, u64]
         lib.or_count_sa.argtypes = [_P, u64, _P, _P, _P, u64, _P]
         lib.or_count_brute_batch.argtypes = [_P, u64, _P, _P, u64, _P]
+        lib.or_revcomp.argtypes = [_P, u64, _P]
         lib.or_fm_steps.restype = u64
         lib.or_fm_steps.argtypes = [_P, u64, _P, _P, _P, u64, u64, _P]
         _lib = lib
@@ -165,3 +166,21 @@ def fm_steps(codes: np.ndarray, sa: np.ndarray, pats: np.ndarray, offsets: np.nd
     total = _load().or_fm_steps(_p(codes), codes.size, _p(sa), _p(pats) if pats.size else None,
                                 _p(offsets), m, k, _p(steps))
     return int(total), steps
+
+
+def revcomp(p: np.ndarray) -> np.ndarray:
+    p = _u8(p)
+    out = np.empty(p.size, dtype=np.uint8)
+    if p.size:
+        _load().or_revcomp(_p(p), p.size, _p(out))
+    return out
+
+
+def revcomp_batch(pats: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Reverse complement of every pattern of a batch (same offsets)."""
+    pats, offsets = _u8(pats), _u64(offsets)
+    out = np.empty_like(pats)
+    for k in range(offsets.size - 1):
+        a, b = int(offsets[k]), int(offsets[k + 1])
+        out[a:b] = revcomp(pats[a:b])
+    return out

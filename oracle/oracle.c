@@ -194,6 +194,13 @@ uint64_t or_count_brute(const uint8_t* codes, uint64_t n, const uint8_t* p, uint
     return cnt;
 }
 
+/* Reverse complement of a DNA pattern: out[i] = 3 - p[len-1-i]
+ * (A<->T, C<->G, read backwards), the other strand of the read (App. D). */
+int or_revcomp(const uint8_t* p, uint64_t len, uint8_t* out) {
+    for (uint64_t i = 0; i < len; i++) out[i] = (uint8_t)(3 - p[len - 1 - i]);
+    return OR_OK;
+}
+
 /* count for m patterns (offsets[m+1]) via the suffix-array interval. */
 int or_count_sa(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint8_t* pats,
                 const uint64_t* offsets, uint64_t m, uint64_t* out) {

@@ -21,6 +21,7 @@ QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA = 0, 1, 2, 3
 QR_ERANGE, QR_EBADSYM, QR_ETIMEOUT = 4, 8, 16
 QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR = 0, 1
 QFM_KEEP_SA = 1
+QFM_BOTH_STRANDS = 2
 
 u64, i32, vp = C.c_uint64, C.c_int, C.c_void_p
 
@@ -227,6 +228,7 @@ class qfm_info_t(C.Structure):
 
 _sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
 _sig("qfm_count", [vp, vp, vp, u64, vp, vp])
+_sig("qfm_count_ex", [vp, vp, vp, u64, vp, i32, vp])
 _sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_noalloc", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_set_policy", [vp, i32])
@@ -257,6 +259,13 @@ def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None) -> QFMIn
 def qfm_count(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:
     m = numel(offsets) - 1
     _check(lib.qfm_count(idx, ptr(patterns), ptr(offsets), m, ptr(out), stream_ptr(stream)), "qfm_count")
+
+
+def qfm_count_ex(idx: QFMIndex, patterns, offsets, out, flags: int = 0, stream=None) -> None:
+    """flags = QFM_BOTH_STRANDS: out holds 2m counts (forward, then reverse complements)."""
+    m = numel(offsets) - 1
+    _check(lib.qfm_count_ex(idx, ptr(patterns), ptr(offsets), m, ptr(out), flags, stream_ptr(stream)),
+           "qfm_count_ex")
 
 
 def qfm_count_stepwise(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:

@@ -5,7 +5,7 @@
 namespace qr {
 int build_fm(qfm_index* idx, const uint8_t* d_t, uint64_t n, cudaStream_t s);
 int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s);
+                 unsigned long long* queue, cudaStream_t s, int strands);
 int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                           cudaStream_t s);
 
@@ -85,18 +85,25 @@ static int check_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, 
     return QR_OK;
 }
 
-int qfm_count(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
-              void* stream) {
+int qfm_count_ex(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
+                 int flags, void* stream) {
     int rc = check_count(idx, patterns, offsets, m, out, "qfm_count");
     if (rc || m == 0) return rc;
+    if (flags & ~QFM_BOTH_STRANDS) return fail(QR_EINVAL, "qfm_count_ex: unknown flag");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long* queue = nullptr;
     QR_CUDA_TRY(cudaMallocAsync((void**)&queue, 16, s));
     cudaError_t e = cudaMemsetAsync(queue, 0, 16, s);
-    if (e == cudaSuccess) rc = launch_count(idx, patterns, offsets, m, out, queue, s);
+    if (e == cudaSuccess)
+        rc = launch_count(idx, patterns, offsets, m, out, queue, s, (flags & QFM_BOTH_STRANDS) ? 2 : 1);
     cudaFreeAsync(queue, s);
     if (e != cudaSuccess) return cuda_fail(e, "qfm_count: queue reset");
     return rc;
+}
+
+int qfm_count(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* out,
+              void* stream) {
+    return qfm_count_ex(idx, patterns, offsets, m, out, 0, stream);
 }
 
 int qfm_count_stepwise(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m,

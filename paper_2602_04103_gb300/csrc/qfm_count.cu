@@ -30,19 +30,22 @@ struct CountArgs {
     unsigned long long* queue;
     uint32_t* status;
     uint32_t chunk;  // ids per queue grab: 64, or 32 when the batch is too small to fill the grid
+    uint32_t strands;  // 1: patterns as given; 2: also their reverse complements (ids m..2m-1)
 };
 
 // Start a search: the interval of the last 8 chars from the table (or the full
-// interval for shorter patterns).  Returns false for a malformed pattern.
-__device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restrict__ p, uint64_t len, uint64_t& lo,
-                                         uint64_t& hi, int64_t& i) {
+// interval for shorter patterns).  With rc the searched string is the reverse
+// complement of p (char k = 3 - p[len-1-k]), so its last 8 chars are the
+// complements of p[7], p[6], ..., p[0].  Returns false for a malformed pattern.
+__device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restrict__ p, uint64_t len, bool rc,
+                                         uint64_t& lo, uint64_t& hi, int64_t& i) {
     if (len >= (uint64_t)kQfmK) {
         uint32_t w = 0, badc = 0;
 #pragma unroll
         for (int d = 0; d < kQfmK; d++) {
-            const uint32_t c = p[len - kQfmK + d];
-            badc |= c;
-            w = (w << 2) | (c & 3);
+            const uint32_t raw = rc ? p[kQfmK - 1 - d] : p[len - kQfmK + d];
+            badc |= raw;
+            w = (w << 2) | ((rc ? 3 - raw : raw) & 3);
         }
         if (badc > 3) return false;
         lo = __ldg(v.table + 2 * w);
@@ -92,13 +95,15 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t total = a.m ? a.off[a.m] : 0;  // bytes of the pattern buffer
+    const uint64_t work = a.m * a.strands;         // search ids: [0, m) forward, [m, 2m) reverse complement
     PatWindow win;
     // warp-local pool of pattern ids [pool_next, pool_end)
     uint64_t pool_next = 0, pool_end = 0;
     bool drained = false;  // the queue has no ids left for this warp
     bool active = false;
-    uint64_t id = 0, lo = 0, hi = 0, start = 0;
+    uint64_t id = 0, lo = 0, hi = 0, start = 0, len = 0;
     int64_t i = -1;
+    bool rc = false;
     uint32_t bad = 0;
     while (true) {
         // ---- refill lanes whose search ended
@@ -115,10 +120,13 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
             }
             if (!active) {
                 id = r < avail ? pool_next + r : base + (r - avail);
-                if (id < a.m) {
-                    start = kKeep ? ld_u64_hint(a.off + id, pol_first) : a.off[id];
-                    const uint64_t end = kKeep ? ld_u64_hint(a.off + id + 1, pol_first) : a.off[id + 1];
-                    if (end < start || end > total || !fm_start(a.v, a.pat + start, end - start, lo, hi, i)) {
+                if (id < work) {
+                    rc = id >= a.m;
+                    const uint64_t pid = rc ? id - a.m : id;
+                    start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
+                    const uint64_t end = kKeep ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
+                    len = end - start;
+                    if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo, hi, i)) {
                         a.out[id] = 0;  // malformed: offsets out of order or a byte > 3
                         bad |= kStatusBadSym;
                     } else {
@@ -129,19 +137,22 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
             if (avail < cnt) {
                 pool_next = base + (cnt - avail);
                 pool_end = base + a.chunk;
-                if (base >= a.m) drained = true;
+                if (base >= work) drained = true;
             } else {
                 pool_next += cnt;
             }
         }
         if (!__any_sync(0xffffffffu, active)) {
-            if (drained || pool_next >= a.m) break;
+            if (drained || pool_next >= work) break;
             continue;
         }
         // ---- one LF step for every active lane
         if (active) {
             if (i >= 0 && lo < hi) {
-                const int c = pattern_char<kKeep>(a.pat, total, start + (uint64_t)i, win, pol_first);
+                // char i of the searched string: p[i], or 3 - p[len-1-i] for the reverse complement
+                const uint64_t pos = rc ? start + (len - 1 - (uint64_t)i) : start + (uint64_t)i;
+                const int raw = pattern_char<kKeep>(a.pat, total, pos, win, pol_first);
+                const int c = rc && raw <= 3 ? 3 - raw : raw;
                 if (c > 3) {
                     a.out[id] = 0;
                     bad |= kStatusBadSym;
@@ -171,7 +182,7 @@ __global__ void step_init(CountArgs a, StepState* __restrict__ st, unsigned long
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = a.off[k], e = a.off[k + 1];
         StepState x;
-        if (e < s || e > a.off[a.m] || !fm_start(a.v, a.pat + s, e - s, x.lo, x.hi, x.i)) {
+        if (e < s || e > a.off[a.m] || !fm_start(a.v, a.pat + s, e - s, false, x.lo, x.hi, x.i)) {
             a.out[k] = 0;
             atomicOr(a.status, kStatusBadSym);
             x.i = -2;
@@ -221,8 +232,9 @@ unsigned persistent_grid(int policy) {
 }  // namespace
 
 int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s) {
+                 unsigned long long* queue, cudaStream_t s, int strands) {
     CountArgs a;
+    a.strands = strands == 2 ? 2 : 1;
     fm_view(idx, &a.v);
     a.pat = pat;
     a.off = off;
@@ -231,10 +243,11 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     a.queue = queue;
     a.status = idx->status;
     uint64_t grid = persistent_grid(idx->policy);
-    // one queue grab per warp of 64 ids when there are enough patterns to
+    const uint64_t work = m * a.strands;
+    // one queue grab per warp of 64 ids when there are enough searches to
     // keep every resident warp busy; smaller batches take 32 (one per lane)
-    a.chunk = m >= (uint64_t)grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
-    uint64_t warps_needed = (m + a.chunk - 1) / a.chunk;
+    a.chunk = work >= (uint64_t)grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
+    uint64_t warps_needed = (work + a.chunk - 1) / a.chunk;
     const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed) grid = blocks_needed;
     if (grid == 0) grid = 1;
@@ -259,6 +272,7 @@ int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off,
     a->out = out;
     a->queue = queue;
     a->status = idx->status;
+    a->strands = 1;
     uint64_t grid = persistent_grid(idx->policy);
     a->chunk = m >= grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
     const uint64_t warps_needed = (m + a->chunk - 1) / a->chunk;
@@ -370,5 +384,5 @@ extern "C" int qfm_count_noalloc(qfm_index* idx, const uint8_t* patterns, const 
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's counter: start this call's queue at 0
     QR_CUDA_TRY(cudaMemsetAsync(queue, 0, kNoallocQueueBytes, s));
-    return launch_count(idx, patterns, offsets, m, out, queue, s);
+    return launch_count(idx, patterns, offsets, m, out, queue, s, 1);
 }

@@ -26,7 +26,7 @@
 
 namespace qr {
 int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s);
+                 unsigned long long* queue, cudaStream_t s, int strands);
 int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                         unsigned long long* queue, void* args, size_t args_bytes, cudaKernelNodeParams* p,
                         void** param_slot);
@@ -241,7 +241,7 @@ int launch_batch(qfm_server* sv, Slot& s) {
         QR_CUDA_TRY(cudaMemcpyAsync(s.d_off, s.h_off, (np + 1) * 8, cudaMemcpyHostToDevice, s.stream));
     }
     QR_CUDA_TRY(cudaMemsetAsync(s.d_queue, 0, 16, s.stream));
-    int rc = qr::launch_count(sv->idx, d_pat, s.d_off, np, s.d_out, s.d_queue, s.stream);
+    int rc = qr::launch_count(sv->idx, d_pat, s.d_off, np, s.d_out, s.d_queue, s.stream, 1);
     if (rc) return rc;
     QR_CUDA_TRY(cudaMemcpyAsync(direct ? r0->out : s.h_out, s.d_out, np * 8, cudaMemcpyDeviceToHost, s.stream));
     QR_CUDA_TRY(cudaEventRecord(s.done, s.stream));

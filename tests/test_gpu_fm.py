@@ -147,3 +147,23 @@ def test_build_rejects_bad_text():
     from paper_2602_04103_gb300 import capi
     with pytest.raises(capi.QRError):
         build_fm(np.array([0, 1, 4, 2], dtype=np.uint8))
+
+
+def test_counts_both_strands():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 18
+    t = synth.fm_text(41, n, repeat_cover=0.2, len_min=300, len_max=2000, sub_rate=0.02)
+    idx = build_fm(t, keep_sa=False)
+    pats, off = synth.patterns(42, t, 30_000, 1, 150, sub_rate=0.01)
+    m = off.size - 1
+    out = torch.empty(2 * m, dtype=torch.int64, device="cuda")
+    capi.qfm_count_ex(idx, dev_u8(pats), dev_u64(off), out, capi.QFM_BOTH_STRANDS)
+    got = host_u64(out)
+    assert np.array_equal(got[:m], counts(idx, pats, off))
+    sa = oracle.suffix_array(t)
+    rc = oracle.revcomp_batch(pats, off)
+    assert np.array_equal(got[m:], oracle.count_sa(t, sa, rc, off))
+    assert capi.qfm_status(idx) == 0
+    with pytest.raises(capi.QRError):
+        capi.qfm_count_ex(idx, dev_u8(pats), dev_u64(off), out, 4)

@@ -154,3 +154,21 @@ def test_batch_counts_and_steps():
                 s_ += 1
                 nonempty = oracle.count_brute(t, p[i:]) > 0
         assert int(steps[j]) == s_, j
+
+
+def test_revcomp_pins():
+    # hand-worked: AACG -> reverse CGAA -> complement (A<->T, C<->G) GCTT
+    assert dec(oracle.revcomp(enc("AACG"))) == "CGTT"
+    assert dec(oracle.revcomp(enc("GATTACA"))) == "TGTAATC"
+    rng = np.random.default_rng(21)
+    p = rng.integers(0, 4, 57).astype(np.uint8)
+    assert np.array_equal(oracle.revcomp(oracle.revcomp(p)), p)          # an involution
+    assert oracle.revcomp(np.zeros(0, np.uint8)).size == 0
+    # counting the reverse complement in T = counting the pattern in the other strand of T
+    t = synth.fm_text(23, 3000, repeat_cover=0.2, len_min=50, len_max=300, sub_rate=0.02)
+    t_rc = oracle.revcomp(t)
+    for L in [1, 3, 6, 10]:
+        for _ in range(10):
+            st = int(rng.integers(0, t.size - L))
+            q = t[st:st + L]
+            assert oracle.count_brute(t, oracle.revcomp(q)) == oracle.count_brute(t_rc, q)

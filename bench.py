@@ -175,9 +175,9 @@ def traffic_record(kernel: str):
 def bytes_per_query(sigma: int, layout: int, load_mode: int, rank4: bool = False, per_query_c: bool = False):
     """Algorithmic bytes of one query: the index bytes it must read (the
     32-byte half-line of the sector layout, the 64-byte line of the paper
-    layout) + the 8-byte query + the result (8, or 32 for rank_4) + 1 byte
-    of symbol when symbols are per query."""
-    index = 32 if layout == 1 else 64
+    layout, the 128-byte line of the line layout) + the 8-byte query + the
+    result (8, or 32 for rank_4) + 1 byte of symbol when symbols are per query."""
+    index = {0: 64, 1: 32, 2: 128}[layout]
     return index + 8 + (32 if rank4 else 8) + (1 if per_query_c else 0)
 
 
@@ -186,7 +186,7 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
     are L2-resident): the sector layout reads one sector; the paper layout
     reads one sector below the block middle and two above it (both with
     whole-line load modes 0 and 2)."""
-    if layout == 1:
+    if layout in (1, 2):
         return 1.0
     if load_mode in (0, 2):
         return 2.0
@@ -258,13 +258,14 @@ def run_ours(args):
     rpq = requests_per_query(2, layout, tuning["load_mode"])
     achieved = bpq * m / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    kname = "birank_rank_sector" if layout == 1 else "birank_rank_paper"
+    kname = {0: "birank_rank_paper", 1: "birank_rank_sector", 2: "birank_rank_line128"}[layout]
     tr = traffic_record(kname)
     gq_launch = m / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
                 "peak_kind": f"of {peak_kind} (copy bandwidth)",
-                "kernel": "rank_sector_kernel<K,kBiScalar>" if layout == 1 else "rank_kernel<K,LOAD,kBiScalar>",
+                "kernel": {0: "rank_kernel<K,LOAD,kBiScalar>", 1: "rank_sector_kernel<K,kBiScalar>",
+                           2: "rank_line_kernel<K,kBiScalar>"}[layout],
                 "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
                 "random_requests_per_query": round(rpq, 3),
                 "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
@@ -302,8 +303,8 @@ def run_ours(args):
         "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
                                f"uniform uint64 queries per GPU",
                    "n_bits": n, "queries_per_gpu": m,
-                   "layout": ("BiRank16x2 sector layout (6.72% overhead)" if layout == 1
-                              else "BiRank16 (3.28% overhead)"),
+                   "layout": {0: "BiRank16 (3.28% overhead)", 1: "BiRank16x2 sector layout (6.72% overhead)",
+                              2: "BiRank16 on 128-byte lines (1.69% overhead)"}[layout],
                    "index_bytes": info["bytes_blocks"] + info["bytes_super"], "tuning": tuning,
                    "tuned_build_s": round(t_tune, 2),
                    "l2": "inputs larger than L2 (2 GiB queries, 2.3 GB index; L2 129 MB)",
@@ -564,7 +565,7 @@ def main():
                     help="log2 of the queries per step of --impl reference")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--layout", type=int, choices=[0, 1], default=None,
+    ap.add_argument("--layout", type=int, choices=[0, 1, 2], default=None,
                     help="fixed layout for the headline (skips the tuned build and the probe)")
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
     ap.add_argument("--serve-requests", type=int, default=8000)

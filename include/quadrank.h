@@ -48,6 +48,11 @@ extern "C" {
 #define QR_EBADSYM 8   /* status bit: some pattern byte was > 3                   */
 
 #define QR_LAYOUT_PAPER 0   /* BiRank16 / QuadRank16 exactly as in the paper      */
+#define QR_LAYOUT_LINE128 2 /* one 128-byte line per query (the GPU's DRAM fill   */
+                            /* unit), read by 4 lanes in one instruction: sigma 2 */
+                            /* = 16-bit delta + 1008 bits (1.69%), sigma 4 = four */
+                            /* deltas + 480 transposed chars (6.88%), deltas to   */
+                            /* the line middle                                     */
 #define QR_LAYOUT_SECTOR 1  /* one self-contained 32-byte sector per query:       */
                             /* sigma 2 = the paper's BiRank16x2 (two 16-bit deltas */
                             /* at 1/4 and 3/4 of a 480-bit block, 6.72%), each     */
@@ -61,18 +66,21 @@ typedef struct {
     uint64_t n;             /* text length (bits or chars)                           */
     int32_t sigma;          /* 2 or 4                                                */
     int32_t layout;         /* QR_LAYOUT_*                                           */
-    uint64_t block_chars;   /* chars per 64-byte line: 496 / 224 (paper layout),      */
-                            /* 480 / 192 (sector layout) for sigma 2 / 4             */
-    uint64_t super_blocks;  /* blocks per superblock: 128 (sigma 2) or 256 (sigma 4) */
-    uint64_t nblocks;       /* floor(n / B) + 1 cache lines of 64 bytes              */
+    uint64_t block_chars;   /* chars per line: 496 / 224 (paper layout), 480 / 192   */
+                            /* (sector), 1008 / 480 (128-byte lines) for sigma 2 / 4 */
+    uint64_t super_blocks;  /* lines per superblock: 128 / 256 (paper, sector),      */
+                            /* 32 / 64 (128-byte lines) for sigma 2 / 4              */
+    uint64_t line_bytes;    /* 64, or 128 for QR_LAYOUT_LINE128                      */
+    uint64_t nblocks;       /* floor(n / B) + 1 lines                                */
     uint64_t nsuper;        /* ceil(nblocks / super_blocks) superblock entries        */
-    uint64_t bytes_blocks;  /* 64 * nblocks                                          */
+    uint64_t bytes_blocks;  /* line_bytes * nblocks                                  */
     uint64_t bytes_super;   /* 4 * nsuper (sigma 2) or 16 * nsuper (sigma 4)          */
 } qr_info_t;
 
 /* Per-handle launch tuning of the rank kernels (chosen by the autotuner). */
 typedef struct {
     int32_t queries_per_thread;  /* independent queries in flight per thread: 1,2,4,8 */
+                                 /* (1 or 2 for QR_LAYOUT_LINE128)                   */
     int32_t block_threads;       /* 64..512, multiple of 32                            */
     int32_t load_mode;           /* 0: whole 64-byte line, 16-byte loads;               */
                                  /* 1: only the 32-byte sectors the query needs, 16-byte */
@@ -203,8 +211,9 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
  * most max_overhead (fraction of the text size, e.g. 0.10), autotune each on
  * the given queries as qr_autotune does, and return the fastest; the others
  * are freed.  *layout_out (may be NULL) receives the chosen QR_LAYOUT_*.
- * Overheads: sigma 2 paper 3.28%, sector 6.72%; sigma 4 paper 14.40%, sector
- * 33.46%.  Errors: QR_EINVAL (no layout within max_overhead), as qr_build.
+ * Overheads: sigma 2 paper 3.28%, sector 6.72%, 128-byte lines 1.69%; sigma 4
+ * paper 14.40%, sector 33.46%, 128-byte lines 6.88%.
+ * Errors: QR_EINVAL (no layout within max_overhead), as qr_build.
  */
 int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_device, double max_overhead,
                    const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out, void* stream,

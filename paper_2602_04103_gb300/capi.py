@@ -19,7 +19,7 @@ lib = C.CDLL(str(_SO))
 
 QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA = 0, 1, 2, 3
 QR_ERANGE, QR_EBADSYM, QR_ETIMEOUT = 4, 8, 16
-QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR = 0, 1
+QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128 = 0, 1, 2
 QFM_KEEP_SA = 1
 QFM_BOTH_STRANDS = 2
 
@@ -28,8 +28,8 @@ u64, i32, vp = C.c_uint64, C.c_int, C.c_void_p
 
 class qr_info_t(C.Structure):
     _fields_ = [("n", u64), ("sigma", C.c_int32), ("layout", C.c_int32), ("block_chars", u64),
-                ("super_blocks", u64), ("nblocks", u64), ("nsuper", u64), ("bytes_blocks", u64),
-                ("bytes_super", u64)]
+                ("super_blocks", u64), ("line_bytes", u64), ("nblocks", u64), ("nsuper", u64),
+                ("bytes_blocks", u64), ("bytes_super", u64)]
 
 
 class qr_tuning_t(C.Structure):

@@ -87,15 +87,16 @@ __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uin
     return (int)((word >> (8 * (k & 3))) & 0xFF);
 }
 
-template <int POLICY>
+template <int POLICY, int STRANDS>
 __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
     constexpr bool kKeep = POLICY == kFmPolicyKeepIndex;
+    constexpr bool kBoth = STRANDS == 2;
     const uint64_t pol_last = kKeep ? l2_policy_evict_last() : 0;
     const uint64_t pol_first = kKeep ? l2_policy_evict_first() : 0;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t total = a.m ? a.off[a.m] : 0;  // bytes of the pattern buffer
-    const uint64_t work = a.m * a.strands;         // search ids: [0, m) forward, [m, 2m) reverse complement
+    const uint64_t work = a.m * STRANDS;           // search ids: [0, m) forward, [m, 2m) reverse complement
     PatWindow win;
     // warp-local pool of pattern ids [pool_next, pool_end)
     uint64_t pool_next = 0, pool_end = 0;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
             if (!active) {
                 id = r < avail ? pool_next + r : base + (r - avail);
                 if (id < work) {
-                    rc = id >= a.m;
+                    rc = kBoth && id >= a.m;
                     const uint64_t pid = rc ? id - a.m : id;
                     start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
                     const uint64_t end = kKeep ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
@@ -218,12 +219,18 @@ __global__ void step_once(CountArgs a, StepState* __restrict__ st) {
     }
 }
 
-unsigned persistent_grid(int policy) {
-    static thread_local int per_sm[2] = {0, 0};
-    int& k = per_sm[policy & 1];
+using CountFn = void (*)(CountArgs);
+
+CountFn count_fn(int policy, int strands) {
+    if (policy == kFmPolicyKeepIndex) return strands == 2 ? count_persistent<1, 2> : count_persistent<1, 1>;
+    return strands == 2 ? count_persistent<0, 2> : count_persistent<0, 1>;
+}
+
+unsigned persistent_grid(int policy, int strands = 1) {
+    static thread_local int per_sm[2][2] = {{0, 0}, {0, 0}};
+    int& k = per_sm[policy & 1][strands == 2];
     if (k == 0) {
-        cudaError_t e = policy ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_persistent<1>, kThreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_persistent<0>, kThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_fn(policy, strands), kThreads, 0);
         if (e != cudaSuccess || k < 1) k = 1;
     }
     return (unsigned)(k * device_props().sms);
@@ -242,7 +249,7 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     a.out = out;
     a.queue = queue;
     a.status = idx->status;
-    uint64_t grid = persistent_grid(idx->policy);
+    uint64_t grid = persistent_grid(idx->policy, a.strands);
     const uint64_t work = m * a.strands;
     // one queue grab per warp of 64 ids when there are enough searches to
     // keep every resident warp busy; smaller batches take 32 (one per lane)
@@ -251,8 +258,7 @@ int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64
     const uint64_t blocks_needed = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed) grid = blocks_needed;
     if (grid == 0) grid = 1;
-    if (idx->policy == kFmPolicyKeepIndex) count_persistent<1><<<(unsigned)grid, kThreads, 0, s>>>(a);
-    else count_persistent<0><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    count_fn(idx->policy, a.strands)<<<(unsigned)grid, kThreads, 0, s>>>(a);
     QR_CUDA_TRY(cudaGetLastError());
     return QR_OK;
 }
@@ -280,7 +286,7 @@ int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off,
     if (grid > blocks_needed) grid = blocks_needed;
     if (grid == 0) grid = 1;
     *param_slot = a;
-    p->func = idx->policy == kFmPolicyKeepIndex ? (void*)count_persistent<1> : (void*)count_persistent<0>;
+    p->func = (void*)count_fn(idx->policy, 1);
     p->gridDim = dim3((unsigned)grid);
     p->blockDim = dim3(kThreads);
     p->sharedMemBytes = 0;

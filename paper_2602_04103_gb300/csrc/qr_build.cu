@@ -424,6 +424,185 @@ __global__ void layout4s_kernel(const uint64_t* __restrict__ text, uint64_t n, u
     }
 }
 
+// ---------------------------------------------------------------- 128-byte line layout
+// sigma 2: line j holds its delta in bits 0..15 and data bits [1008 j, +1008)
+// in bits 16..1023.  A warp builds one superblock of 32 lines, one per lane.
+struct Line2L {
+    uint64_t w[16];
+    uint32_t cnt, half;  // ones of the 1008 bits / of their first 504
+};
+
+__device__ __forceinline__ Line2L make_line2l(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    Line2L L;
+    const uint64_t base = j * kB2L;
+    L.w[0] = bits64(t, n, base) << 16;
+#pragma unroll
+    for (int k = 1; k < 16; k++) L.w[k] = bits64(t, n, base + 64 * k - 16);
+    uint32_t h = 0, c = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const uint32_t pc = popc64(L.w[k]);
+        c += pc;
+        if (k < 8) h += pc;
+    }
+    L.half = h + popc64(L.w[8] & 0xFFull);  // line bits 16 .. 519 = data bits 0 .. 503
+    L.cnt = c;
+    return L;
+}
+
+__global__ void count2l_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               uint64_t* __restrict__ super_cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        const uint64_t j = i * kSuper2L + lane;
+        uint64_t sum = j < nblocks ? make_line2l(text, n, j).cnt : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) super_cnt[i] = sum;
+    }
+}
+
+__global__ void layout2l_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                                const uint64_t* __restrict__ super_base, uint4* __restrict__ lines,
+                                uint32_t* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        const uint64_t base = super_base[i];
+        const uint64_t s = base >> kShift2;
+        if (lane == 0) supers[i] = (uint32_t)s;
+        const uint64_t j = i * kSuper2L + lane;
+        const bool live = j < nblocks;
+        Line2L L;
+        if (live) L = make_line2l(text, n, j);
+        const uint32_t v = live ? L.cnt : 0;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (live) {
+            L.w[0] |= (base - (s << kShift2)) + (incl - v) + L.half;  // rank(jB + 504) - 2^11 s_i
+            uint4* dst = lines + 8 * j;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                    (uint32_t)(L.w[2 * k + 1] >> 32));
+        }
+    }
+}
+
+// sigma 4: line j holds chars [480 j, +480): groups g = 0..6 of 64 chars in
+// words 2+2g / 3+2g, the 32-char tail in word 1, the deltas in word 0.  A
+// warp builds one superblock of 64 lines, two per lane.
+struct Line4L {
+    uint64_t w[16];
+    uint32_t cnt[4], half[4];  // per-symbol counts of the 480 chars / of the first 240
+};
+
+__device__ __forceinline__ Line4L make_line4l(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    Line4L R;
+    const uint64_t nbits = 2 * n, c0 = j * kB4L;
+    uint32_t cnt[4] = {0, 0, 0, 0}, half[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int g = 0; g < 7; g++) {
+        const uint64_t first = c0 + 64 * g;
+        const uint64_t x0 = bits64(t, nbits, 2 * first), x1 = bits64(t, nbits, 2 * first + 64);
+        const uint64_t L = (uint64_t)even_bits(x0) | ((uint64_t)even_bits(x1) << 32);
+        const uint64_t H = (uint64_t)even_bits(x0 >> 1) | ((uint64_t)even_bits(x1 >> 1) << 32);
+        R.w[2 + 2 * g] = ~L;
+        R.w[3 + 2 * g] = ~H;
+        count_group(L, H, ~0ull, cnt);
+        if (g < 3) count_group(L, H, ~0ull, half);
+        if (g == 3) count_group(L, H, 0x0000FFFFFFFFFFFFull, half);  // chars 192 .. 239
+    }
+    const uint64_t x = bits64(t, nbits, 2 * (c0 + 448));
+    const uint64_t LB = even_bits(x), HB = even_bits(x >> 1);
+    R.w[1] = (~LB & 0xFFFFFFFFull) | ((~HB & 0xFFFFFFFFull) << 32);
+    count_group(LB, HB, 0xFFFFFFFFull, cnt);
+    R.w[0] = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        R.cnt[c] = cnt[c];
+        R.half[c] = half[c];
+    }
+    return R;
+}
+
+__global__ void count4l_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                               uint64_t* __restrict__ super_cnt /* [4][nsuper] */) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t sum[4] = {0, 0, 0, 0};
+        for (int r = 0; r < (int)(kSuper4L / 32); r++) {
+            const uint64_t j = i * kSuper4L + r * 32 + lane;
+            if (j < nblocks) {
+                const Line4L L = make_line4l(text, n, j);
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum[c] += L.cnt[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+            if (lane == 0) super_cnt[c * nsuper + i] = sum[c];
+        }
+    }
+}
+
+__global__ void layout4l_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nsuper,
+                                const uint64_t* __restrict__ super_base, uint4* __restrict__ lines,
+                                uint4* __restrict__ supers) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nsuper; i += nwarps) {
+        uint64_t running[4];
+        uint32_t s[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint64_t base = super_base[c * nsuper + i];
+            s[c] = (uint32_t)(base >> kShift4);
+            running[c] = base - ((uint64_t)s[c] << kShift4);
+        }
+        if (lane == 0) supers[i] = make_uint4(s[0], s[1], s[2], s[3]);
+        for (int r = 0; r < (int)(kSuper4L / 32); r++) {
+            const uint64_t j = i * kSuper4L + r * 32 + lane;
+            const bool live = j < nblocks;
+            Line4L L;
+            if (live) L = make_line4l(text, n, j);
+            uint64_t d = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const uint32_t v = live ? L.cnt[c] : 0;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (live) d |= (running[c] + (incl - v) + L.half[c]) << (16 * c);  // rank(jB + 240, c) - 2^13 s
+                running[c] += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (live) {
+                L.w[0] = d;
+                uint4* dst = lines + 8 * j;
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                        (uint32_t)(L.w[2 * k + 1] >> 32));
+            }
+        }
+    }
+}
+
 unsigned grid_for_warps(uint64_t nwarps) {
     uint64_t blocks = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const uint64_t cap = (uint64_t)device_props().sms * 64;
@@ -449,7 +628,23 @@ int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
     const unsigned threads = 32 * kWarpsPerBlock;
     int rc = QR_OK;
     const bool sector = idx->layout == QR_LAYOUT_SECTOR;
-    if (idx->sigma == 2) {
+    const bool line128 = idx->layout == QR_LAYOUT_LINE128;
+    if (line128) {
+        if (idx->sigma == 2) {
+            count2l_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+            rc = exclusive_scan_u64(cnt, base, nsuper, s);
+            if (rc == QR_OK)
+                layout2l_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                         (uint32_t*)idx->supers);
+        } else {
+            count4l_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
+            for (int c = 0; c < 4 && rc == QR_OK; c++)
+                rc = exclusive_scan_u64(cnt + c * nsuper, base + c * nsuper, nsuper, s);
+            if (rc == QR_OK)
+                layout4l_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, base, idx->lines,
+                                                         (uint4*)idx->supers);
+        }
+    } else if (idx->sigma == 2) {
         if (sector) count2s_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
         else count2_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nsuper, cnt);
         rc = exclusive_scan_u64(cnt, base, nsuper, s);

@@ -38,6 +38,17 @@ const DeviceProps& device_props() {
     return p;
 }
 
+uint64_t block_chars(int sigma, int layout) {
+    if (layout == QR_LAYOUT_SECTOR) return sigma == 2 ? kB2s : kB4s;
+    if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kB2L : kB4L;
+    return sigma == 2 ? kB2 : kB4;
+}
+uint64_t super_lines(int sigma, int layout) {
+    if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kSuper2L : kSuper4L;
+    return sigma == 2 ? kSuper2 : kSuper4;
+}
+uint64_t line_bytes(int layout) { return layout == QR_LAYOUT_LINE128 ? 128 : 64; }
+
 static int tuning_ok(const qr_tuning_t& t) {
     const int k = t.queries_per_thread;
     if (k != 1 && k != 2 && k != 4 && k != 8) return 0;
@@ -75,7 +86,8 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     if (!out) return fail(QR_EINVAL, "qr_build: out is NULL");
     *out = nullptr;
     if (sigma != 2 && sigma != 4) return fail(QR_EINVAL, "qr_build: sigma must be 2 or 4");
-    if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR) return fail(QR_EINVAL, "qr_build: unknown layout");
+    if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR && layout != QR_LAYOUT_LINE128)
+        return fail(QR_EINVAL, "qr_build: unknown layout");
     if (sigma == 2 && n >= (1ull << 43)) return fail(QR_EINVAL, "qr_build: sigma 2 needs n < 2^43");
     if (sigma == 4 && n >= (1ull << 45)) return fail(QR_EINVAL, "qr_build: sigma 4 needs n < 2^45");
     if (!text && n > 0) return fail(QR_EINVAL, "qr_build: text is NULL");
@@ -85,12 +97,14 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     idx->sigma = sigma;
     idx->layout = layout;
     idx->n = n;
-    const bool sector = layout == QR_LAYOUT_SECTOR;
-    const uint64_t B = sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
-    const uint64_t per = sigma == 2 ? kSuper2 : kSuper4;
+    // default launch tuning per layout (the best measured on GB300; qr_autotune refines it)
+    if (layout == QR_LAYOUT_PAPER) idx->tune = qr_tuning_t{4, 512, 4, 0};
+    else idx->tune = qr_tuning_t{1, 512, 0, 0};
+    const uint64_t B = block_chars(sigma, layout);
+    const uint64_t per = super_lines(sigma, layout);
     idx->nblocks = n / B + 1;
     idx->nsuper = (idx->nblocks + per - 1) / per;
-    cudaError_t e = cudaMalloc((void**)&idx->lines, 64 * idx->nblocks);
+    cudaError_t e = cudaMalloc((void**)&idx->lines, line_bytes(layout) * idx->nblocks);
     if (e == cudaSuccess) e = cudaMalloc(&idx->supers, (sigma == 2 ? 4 : 16) * idx->nsuper);
     if (e == cudaSuccess) e = cudaMalloc((void**)&idx->status, 64);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx->status, 0, 64, s);
@@ -230,12 +244,12 @@ int qr_info(const qr_index* idx, qr_info_t* info) {
     info->n = idx->n;
     info->sigma = idx->sigma;
     info->layout = idx->layout;
-    const bool sector = idx->layout == QR_LAYOUT_SECTOR;
-    info->block_chars = idx->sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
-    info->super_blocks = idx->sigma == 2 ? kSuper2 : kSuper4;
+    info->block_chars = block_chars(idx->sigma, idx->layout);
+    info->super_blocks = super_lines(idx->sigma, idx->layout);
+    info->line_bytes = line_bytes(idx->layout);
     info->nblocks = idx->nblocks;
     info->nsuper = idx->nsuper;
-    info->bytes_blocks = 64 * idx->nblocks;
+    info->bytes_blocks = info->line_bytes * idx->nblocks;
     info->bytes_super = (idx->sigma == 2 ? 4 : 16) * idx->nsuper;
     return QR_OK;
 }
@@ -250,7 +264,8 @@ int qr_layout_ptrs(const qr_index* idx, const void** lines, const void** supers)
 int qr_copy_layout(const qr_index* idx, void* lines_dst, void* supers_dst, void* stream) {
     if (!idx) return fail(QR_EINVAL, "qr_copy_layout: NULL index");
     cudaStream_t s = (cudaStream_t)stream;
-    if (lines_dst) QR_CUDA_TRY(cudaMemcpyAsync(lines_dst, idx->lines, 64 * idx->nblocks, cudaMemcpyDefault, s));
+    if (lines_dst)
+        QR_CUDA_TRY(cudaMemcpyAsync(lines_dst, idx->lines, line_bytes(idx->layout) * idx->nblocks, cudaMemcpyDefault, s));
     if (supers_dst)
         QR_CUDA_TRY(cudaMemcpyAsync(supers_dst, idx->supers, (idx->sigma == 2 ? 4 : 16) * idx->nsuper,
                                     cudaMemcpyDefault, s));
@@ -267,6 +282,8 @@ int qr_get_tuning(const qr_index* idx, qr_tuning_t* t) {
 int qr_set_tuning(qr_index* idx, const qr_tuning_t* t) {
     if (!idx || !t) return fail(QR_EINVAL, "qr_set_tuning: NULL argument");
     if (!tuning_ok(*t)) return fail(QR_EINVAL, "qr_set_tuning: invalid tuning");
+    if (idx->layout == QR_LAYOUT_LINE128 && t->queries_per_thread > 2)
+        return fail(QR_EINVAL, "qr_set_tuning: the 128-byte line layout takes 1 or 2 queries per thread");
     idx->tune = *t;
     return QR_OK;
 }
@@ -293,11 +310,12 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
     qr_tuning_t win = saved;
     float win_ms = 1e30f;
     const int ks[] = {1, 2, 4, 8}, ths[] = {128, 256, 512};
-    const int nload = idx->layout == QR_LAYOUT_SECTOR ? 1 : 5;
+    const int nload = idx->layout == QR_LAYOUT_PAPER ? 5 : 1;
     int rc = QR_OK;
     for (int li = 0; li < nload && rc == QR_OK; li++)
         for (int k : ks)
             for (int th : ths) {
+                if (idx->layout == QR_LAYOUT_LINE128 && k > 2) continue;  // 1 or 2 lines per lane
                 idx->tune = qr_tuning_t{k, th, li, 0};
                 rc = run_mode(idx, q, m, mode, c, c_vec, out, s);  // warm-up
                 float bestk = 1e30f;
@@ -325,11 +343,9 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
 }
 
 static double layout_overhead(int sigma, int layout, uint64_t n) {
-    const bool sector = layout == QR_LAYOUT_SECTOR;
-    const uint64_t B = sigma == 2 ? (sector ? kB2s : kB2) : (sector ? kB4s : kB4);
-    const uint64_t per = sigma == 2 ? kSuper2 : kSuper4;
+    const uint64_t B = block_chars(sigma, layout), per = super_lines(sigma, layout);
     const uint64_t nb = n / B + 1, ns = (nb + per - 1) / per;
-    const double bytes = 64.0 * nb + (sigma == 2 ? 4.0 : 16.0) * ns;
+    const double bytes = (double)line_bytes(layout) * nb + (sigma == 2 ? 4.0 : 16.0) * ns;
     const double text = sigma == 2 ? n / 8.0 : n / 4.0;
     return n ? bytes / text - 1.0 : 0.0;
 }
@@ -343,7 +359,7 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
     int best_layout = -1;
     float best_ms = 1e30f;
     cudaStream_t s = (cudaStream_t)stream;
-    for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR}) {
+    for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128}) {
         if (sigma == 2 || sigma == 4) {
             if (layout_overhead(sigma, layout, n < 4096 ? 1u << 30 : n) > max_overhead) continue;
         }

@@ -53,6 +53,20 @@ constexpr uint64_t kB4s = 192;
 constexpr uint64_t kHalf4s = 96;
 constexpr uint64_t kMid4s = 48;
 
+// 128-byte line layout (QR_LAYOUT_LINE128): one DRAM line fill per query,
+// read by the four lanes of a quad in one instruction.  sigma 2: a 16-bit
+// delta + 1008 data bits per line (data bit d at line bit 16 + d), 32 lines
+// per superblock, the delta points to data offset 504 (line bit 520).
+// sigma 4: word 0 = four 16-bit deltas, word 1 = ~low | ~high << 32 of chars
+// 448..479, words 2+2g / 3+2g = ~low / ~high bits of chars 64g..64g+63 for
+// g = 0..6; 480 chars per line, 64 lines per superblock, deltas to char 240.
+constexpr uint64_t kB2L = 1008;
+constexpr uint64_t kMid2L = 504;
+constexpr uint64_t kSuper2L = 32;
+constexpr uint64_t kB4L = 480;
+constexpr uint64_t kMid4L = 240;
+constexpr uint64_t kSuper4L = 64;
+
 // Status bits written by kernels (same values as the QR_E* status codes).
 constexpr uint32_t kStatusRange = QR_ERANGE;
 constexpr uint32_t kStatusBadSym = QR_EBADSYM;
@@ -80,6 +94,9 @@ __host__ __device__ __forceinline__ uint64_t div224(uint64_t q) { return mulhi64
 constexpr uint64_t kMagic15 = 0x8888888888888889ull;  // ceil(2^67 / 15)
 constexpr uint64_t kMagic3 = 0xAAAAAAAAAAAAAAABull;   // ceil(2^65 / 3)
 __host__ __device__ __forceinline__ uint64_t div480(uint64_t q) { return mulhi64(q >> 5, kMagic15) >> 3; }
+// 1008 = 16 * 63 (error term 55).
+constexpr uint64_t kMagic63 = 0x8208208208208209ull;  // ceil(2^69 / 63)
+__host__ __device__ __forceinline__ uint64_t div1008(uint64_t q) { return mulhi64(q >> 4, kMagic63) >> 5; }
 __host__ __device__ __forceinline__ uint64_t div192(uint64_t q) { return mulhi64(q >> 6, kMagic3) >> 1; }
 
 // ---------------------------------------------------------------- bit helpers
@@ -292,6 +309,44 @@ __device__ __forceinline__ void quad_sector_finish4(const uint32_t s[4], const u
     }
 }
 
+// ---------------------------------------------------------------- 128-byte line queries
+// The quad lane `sub` holds sector `sub` (words 4 sub .. 4 sub + 3) of the line.
+// sigma 2: the ones of line bits [a, b) that fall in this sector.
+__device__ __forceinline__ uint32_t line128_count2(const u64x4& W, int sub, int32_t a, int32_t b) {
+    const int32_t o = 256 * sub;
+    return popc64(W.a & range_mask(a - o, b - o, 0)) + popc64(W.b & range_mask(a - o, b - o, 1)) +
+           popc64(W.c & range_mask(a - o, b - o, 2)) + popc64(W.d & range_mask(a - o, b - o, 3));
+}
+// sigma 4: raw low/high bits of chars [a, b) in this sector: its 64-char
+// groups (sector 0: group 0 in words 2, 3 and the 32-char tail in word 1;
+// sector k >= 1: groups 2k - 1 and 2k).  Returns the match count for symbol c,
+// or (with c < 0) fills nl = |L|, nh = |H|, n3 = |L & H|.
+__device__ __forceinline__ void line128_group(uint64_t lo_n, uint64_t hi_n, uint64_t m, int c, uint32_t& cnt,
+                                              uint32_t& nl, uint32_t& nh, uint32_t& n3) {
+    if (c >= 0) {
+        const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
+        cnt += popc64((lo_n ^ cl) & (hi_n ^ ch) & m);
+    } else {
+        const uint64_t L = ~lo_n & m, H = ~hi_n & m;
+        nl += popc64(L);
+        nh += popc64(H);
+        n3 += popc64(L & H);
+    }
+}
+__device__ __forceinline__ void line128_count4(const u64x4& W, int sub, int32_t a, int32_t b, int c, uint32_t& cnt,
+                                               uint32_t& nl, uint32_t& nh, uint32_t& n3) {
+    if (sub == 0) {
+        // tail: chars 448..479 in word 1 (low half ~low bits, high half ~high bits)
+        const uint64_t mt = range_mask(a - 448, b - 448, 0) & 0xFFFFFFFFull;
+        line128_group(W.b & 0xFFFFFFFFull, W.b >> 32, mt, c, cnt, nl, nh, n3);
+        line128_group(W.c, W.d, range_mask(a, b, 0), c, cnt, nl, nh, n3);          // group 0
+    } else {
+        const int g0 = 2 * sub - 1;                                                 // groups g0, g0 + 1
+        line128_group(W.a, W.b, range_mask(a - 64 * g0, b - 64 * g0, 0), c, cnt, nl, nh, n3);
+        line128_group(W.c, W.d, range_mask(a - 64 * g0 - 64, b - 64 * g0 - 64, 0), c, cnt, nl, nh, n3);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct DeviceProps {
     int device = -1;
@@ -322,6 +377,9 @@ struct qr_index {
 };
 
 namespace qr {
+uint64_t block_chars(int sigma, int layout);
+uint64_t super_lines(int sigma, int layout);
+uint64_t line_bytes(int layout);
 // Build the layout into an already sized index from a device text.
 int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
 // Launch the rank kernels (no argument checks beyond the mode).

@@ -272,6 +272,144 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
     if (bad_flags) atomicOr(a.status, bad_flags);
 }
 
+// 128-byte line layout (QR_LAYOUT_LINE128): the four lanes of a quad answer
+// their four queries together.  In round r every lane of the quad loads its
+// sector (32 bytes) of the line of lane r's query -- one instruction, one
+// request, one 128-byte fill per query -- and counts the bits (or chars) of
+// the query's range that fall in its sector; two shuffles sum the four
+// partial counts and lane r keeps the result.
+template <int K, int KIND>
+__global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
+    constexpr bool kQuad = KIND >= kQuadScalar;
+    constexpr uint32_t kAll = 0xffffffffu;
+    const int sub = threadIdx.x & 3;
+    const uint64_t tile = (uint64_t)blockDim.x * K;
+    uint32_t bad_flags = 0;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < a.m; t0 += (uint64_t)gridDim.x * tile) {
+        uint64_t qv[K];
+        int cv[K];
+        bool live[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            live[k] = i < a.m;
+            qv[k] = live[k] ? ld_stream_u64(a.q + i) : 0;
+            if (KIND == kBiVec || KIND == kQuadVec) cv[k] = live[k] ? (int)ld_stream_u8(a.cvec + i) : 0;
+            else cv[k] = a.c;
+        }
+        uint32_t pos[K];
+        uint32_t s1[K];
+        uint4 s4[K];
+        u64x4 W[K][4];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t qq = qv[k] <= a.n ? qv[k] : 0;
+            uint64_t j;
+            if (!kQuad) {
+                j = div1008(qq);
+                pos[k] = (uint32_t)(qq - j * kB2L);
+                s1[k] = __ldg((const uint32_t*)a.supers + (j >> 5));
+            } else {
+                j = div480(qq);
+                pos[k] = (uint32_t)(qq - j * kB4L);
+                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 6));
+                else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 6) + (cv[k] & 3));
+            }
+            const unsigned long long L = (unsigned long long)(a.lines + 8 * j);
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const uint4* Lr = (const uint4*)__shfl_sync(kAll, L, r, 4);
+                W[k][r] = ld_line32(Lr + 2 * sub);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            uint64_t res[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const uint32_t pr = __shfl_sync(kAll, pos[k], r, 4);
+                if (!kQuad) {
+                    const bool upper = pr >= kMid2L;
+                    const int32_t lo = upper ? (int32_t)(16 + kMid2L) : (int32_t)(16 + pr);
+                    const int32_t hi = upper ? (int32_t)(16 + pr) : (int32_t)(16 + kMid2L);
+                    uint32_t t = line128_count2(W[k][r], sub, lo, hi);
+                    t += __shfl_xor_sync(kAll, t, 1, 4);
+                    t += __shfl_xor_sync(kAll, t, 2, 4);
+                    const uint64_t d = __shfl_sync(kAll, (unsigned long long)(W[k][r].a & 0xFFFFull), 0, 4);
+                    if (sub == r) {
+                        const uint64_t mid = ((uint64_t)s1[k] << kShift2) + d;
+                        res[0] = upper ? mid + t : mid - t;
+                    }
+                } else {
+                    const bool upper = pr >= kMid4L;
+                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr;
+                    const int32_t hi = upper ? (int32_t)pr : (int32_t)kMid4L;
+                    const unsigned long long d0 = __shfl_sync(kAll, (unsigned long long)W[k][r].a, 0, 4);
+                    if (KIND == kQuad4) {
+                        uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
+                        line128_count4(W[k][r], sub, lo, hi, -1, cnt, nl, nh, n3);
+                        nl += __shfl_xor_sync(kAll, nl, 1, 4);
+                        nl += __shfl_xor_sync(kAll, nl, 2, 4);
+                        nh += __shfl_xor_sync(kAll, nh, 1, 4);
+                        nh += __shfl_xor_sync(kAll, nh, 2, 4);
+                        n3 += __shfl_xor_sync(kAll, n3, 1, 4);
+                        n3 += __shfl_xor_sync(kAll, n3, 2, 4);
+                        if (sub == r) {
+                            const uint32_t nm = (uint32_t)(hi - lo);
+                            const uint32_t nc[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+#pragma unroll
+                            for (int c = 0; c < 4; c++) {
+                                const uint64_t mid = ((uint64_t)(&s4[k].x)[c] << kShift4) + ((d0 >> (16 * c)) & 0xFFFFull);
+                                res[c] = upper ? mid + nc[c] : mid - nc[c];
+                            }
+                        }
+                    } else {
+                        const int cr = __shfl_sync(kAll, cv[k], r, 4) & 3;
+                        uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
+                        line128_count4(W[k][r], sub, lo, hi, cr, cnt, nl, nh, n3);
+                        cnt += __shfl_xor_sync(kAll, cnt, 1, 4);
+                        cnt += __shfl_xor_sync(kAll, cnt, 2, 4);
+                        if (sub == r) {
+                            const uint64_t mid = ((uint64_t)s1[k] << kShift4) + ((d0 >> (16 * cr)) & 0xFFFFull);
+                            res[0] = upper ? mid + cnt : mid - cnt;
+                        }
+                    }
+                }
+            }
+            const bool range_bad = qv[k] > a.n;
+            if (!kQuad) {
+                const int c = cv[k];
+                const bool sym_bad = (unsigned)c > 1u;
+                uint64_t out = c == 1 ? res[0] : qv[k] - res[0];
+                if (range_bad || sym_bad) out = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, out);
+                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            } else if (KIND == kQuad4) {
+                if (range_bad) res[0] = res[1] = res[2] = res[3] = ~0ull;
+                if (live[k]) {
+                    uint64_t* o = a.out + 4 * i;
+                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o), "l"(res[0]), "l"(res[1]) : "memory");
+                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o + 2), "l"(res[2]), "l"(res[3])
+                                 : "memory");
+                    bad_flags |= range_bad ? kStatusRange : 0u;
+                }
+            } else {
+                const bool sym_bad = (unsigned)cv[k] > 3u;
+                uint64_t out = res[0];
+                if (range_bad || sym_bad) out = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, out);
+                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            }
+        }
+    }
+    if (bad_flags) atomicOr(a.status, bad_flags);
+}
+
 // ---------------------------------------------------------------- launch table
 using KernelFn = void (*)(RankArgs);
 
@@ -309,7 +447,26 @@ KernelFn pick_sector(int k) {
     }
 }
 
-KernelFn pick_kind(int kind, int k, int load, bool sector) {
+template <int KIND>
+KernelFn pick_line(int k) {
+    switch (k) {
+        case 1: return rank_line_kernel<1, KIND>;
+        case 2: return rank_line_kernel<2, KIND>;
+        default: return nullptr;
+    }
+}
+
+KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false) {
+    if (line128) {
+        switch (kind) {
+            case kBiScalar: return pick_line<kBiScalar>(k);
+            case kBiVec: return pick_line<kBiVec>(k);
+            case kQuadScalar: return pick_line<kQuadScalar>(k);
+            case kQuadVec: return pick_line<kQuadVec>(k);
+            case kQuad4: return pick_line<kQuad4>(k);
+            default: return nullptr;
+        }
+    }
     if (sector) {
         switch (kind) {
             case kBiScalar: return pick_sector<kBiScalar>(k);
@@ -386,7 +543,8 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     if (idx->sigma == 2) kind = cvec ? kBiVec : kBiScalar;
     else kind = rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
     const qr_tuning_t& t = idx->tune;
-    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR);
+    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR,
+                            idx->layout == QR_LAYOUT_LINE128);
     if (!fn) return fail(QR_EINVAL, "no rank kernel for this tuning");
     RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status};
     const uint64_t tiles = (m + (uint64_t)t.block_threads * t.queries_per_thread - 1) /

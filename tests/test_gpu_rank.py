@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
 B2S, S2S, B4S, S4S = 480, 480 * 128, 192, 192 * 256
-LAYOUTS = [0, 1]   # QR_LAYOUT_PAPER (BiRank16 / QuadRank16), QR_LAYOUT_SECTOR
+B2L, S2L, B4L, S4L = 1008, 1008 * 32, 480, 480 * 64
+LAYOUTS = [0, 1, 2]   # QR_LAYOUT_PAPER (BiRank16 / QuadRank16), QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,7 +86,8 @@ def test_multi_superblock_dna_every_q(kind, layout):
 
 
 @pytest.mark.parametrize("n", [0, 1, 63, 64, 119, 120, 121, 239, 240, 241, 255, 256, 359, 360, 361, 479, 480,
-                               481, 495, 496, 497, 991, 992, 993, S2S - 1, S2S, S2S + 1, S2 - 1, S2, S2 + 1,
+                               481, 495, 496, 497, 503, 504, 505, 991, 992, 993, 1007, 1008, 1009, 2016,
+                               S2L - 1, S2L, S2L + 1, S2S - 1, S2S, S2S + 1, S2 - 1, S2, S2 + 1,
                                2 * S2, 2 * S2 + 240])
 def test_edge_lengths_bits(n):
     for layout in LAYOUTS:
@@ -93,7 +95,8 @@ def test_edge_lengths_bits(n):
 
 
 @pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 47, 48, 49, 95, 96, 97, 127, 128, 143, 144, 145, 191, 192, 193,
-                               223, 224, 225, 447, 448, S4S - 1, S4S, S4S + 1, S4 - 1, S4, S4 + 1, 2 * S4 + 96])
+                               223, 224, 225, 239, 240, 241, 447, 448, 449, 479, 480, 481, S4L - 1, S4L, S4L + 1,
+                               S4S - 1, S4S, S4S + 1, S4 - 1, S4, S4 + 1, 2 * S4 + 96])
 def test_edge_lengths_dna(n):
     for layout in LAYOUTS:
         check_dna(synth.dna_uniform(n + 5, n), n, layout=layout)
@@ -242,10 +245,12 @@ def test_out_of_range_and_bad_symbols():
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
-@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1)])
+@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1), (0, 2)])
 @pytest.mark.parametrize("threads", [64, 256, 512])
 def test_every_tuning(k, load, layout, threads):
     from paper_2602_04103_gb300 import capi
+    if layout == 2 and k > 2:
+        pytest.skip("the 128-byte line layout takes 1 or 2 queries per thread")
     n, n4 = 3 * S2 + 77, 3 * S4 + 99
     words, w4 = synth.bits(17, n, 0.5), synth.dna_uniform(18, n4)
     q = synth.queries(19, n, 100_003)
@@ -400,3 +405,92 @@ def test_autotune_and_build_tuned():
     s4 = torch.empty((q4.size, 4), dtype=torch.int64, device="cuda")
     idx4, lay4 = capi.qr_build_tuned(dev_u64(w4), n4, 4, dq4, s4, rank4=True, max_overhead=0.40)
     assert np.array_equal(rank4(idx4, q4), oracle.rank4(w4, n4, q4)[0])
+
+
+def test_line128_layout_matches_definitions():
+    # sigma 2: delta to data offset 504 of a 1008-bit block, 32 lines per superblock
+    n = 3 * S2L + 777
+    words = synth.bits(88, n, 0.45)
+    idx = build(words, n, 2, 2)
+    from paper_2602_04103_gb300 import capi
+    info = capi.qr_info(idx)
+    assert info["line_bytes"] == 128 and info["block_chars"] == 1008 and info["super_blocks"] == 32
+    lines = np.empty(info["bytes_blocks"] // 8, dtype=np.uint64)
+    sup = np.empty(info["bytes_super"] // 4, dtype=np.uint32)
+    capi.qr_copy_layout(idx, lines, sup)
+    lines = lines.reshape(-1, 16)
+    nb = n // B2L + 1
+    js = np.arange(nb, dtype=np.uint64)
+    starts = np.minimum(np.arange(info["nsuper"], dtype=np.uint64) * np.uint64(S2L), np.uint64(n))
+    assert np.array_equal(sup.astype(np.uint64), oracle.rank(words, n, 2, starts, 1)[0] >> np.uint64(11))
+    mids = np.minimum(js * np.uint64(B2L) + np.uint64(504), np.uint64(n))
+    want = oracle.rank(words, n, 2, mids, 1)[0] - (sup.astype(np.uint64)[js >> np.uint64(5)] << np.uint64(11))
+    assert np.array_equal(lines[:, 0] & np.uint64(0xFFFF), want)
+    tb = np.unpackbits(words.view(np.uint8), bitorder="little")
+    lb = np.unpackbits(lines.view(np.uint8), bitorder="little").reshape(nb, 1024)
+    for j in [0, 1, 31, 32, nb - 1]:
+        lo, hi = j * B2L, min(j * B2L + B2L, n)
+        assert np.array_equal(lb[j, 16:16 + hi - lo], tb[lo:hi])
+    # sigma 4: chars 64g.. in words 2+2g (~low) / 3+2g (~high), tail 448..479 in word 1
+    n4 = 2 * S4L + 333
+    w4 = synth.dna_uniform(89, n4)
+    idx4 = build(w4, n4, 4, 2)
+    info4 = capi.qr_info(idx4)
+    l4 = np.empty(info4["bytes_blocks"] // 8, dtype=np.uint64)
+    s4 = np.empty(info4["bytes_super"] // 4, dtype=np.uint32)
+    capi.qr_copy_layout(idx4, l4, s4)
+    l4 = l4.reshape(-1, 16)
+    s4 = s4.reshape(-1, 4).astype(np.uint64)
+    nb4 = info4["nblocks"]
+    js = np.arange(nb4, dtype=np.uint64)
+    mids = np.minimum(js * np.uint64(B4L) + np.uint64(240), np.uint64(n4))
+    r4 = oracle.rank4(w4, n4, mids)[0]
+    r4[:, 0] += (js * np.uint64(B4L) + np.uint64(240)) - mids     # padding chars are A
+    got = np.stack([(l4[:, 0] >> np.uint64(16 * c)) & np.uint64(0xFFFF) for c in range(4)], axis=1)
+    assert np.array_equal(got, r4 - (s4[js >> np.uint64(6)] << np.uint64(13)))
+    codes = synth.unpack2(w4, n4)
+    for j in [0, 63, 64, nb4 - 1]:
+        for d in range(480):
+            i = j * B4L + d
+            if d < 448:
+                g, b = d // 64, d % 64
+                lo = (~int(l4[j, 2 + 2 * g]) >> b) & 1
+                hi = (~int(l4[j, 3 + 2 * g]) >> b) & 1
+            else:
+                b = d - 448
+                lo = (~int(l4[j, 1]) >> b) & 1
+                hi = (~int(l4[j, 1]) >> (32 + b)) & 1
+            assert lo | (hi << 1) == (int(codes[i]) if i < n4 else 0), (j, d)
+
+
+def test_line128_max_deltas_and_overheads():
+    # sigma 2: 2047 + 31 * 1008 + 504 = 33799; sigma 4: 8191 + 63 * 480 + 240 = 38671
+    n = 2 * S2L + 3000
+    bits = np.zeros(n, dtype=np.uint8)
+    bits[:2047] = 1
+    bits[S2L:2 * S2L] = 1
+    idx = check_bits(synth.pack_bits(bits), n, layout=2)
+    from paper_2602_04103_gb300 import capi
+    info = capi.qr_info(idx)
+    lines = np.empty(info["bytes_blocks"] // 8, dtype=np.uint64)
+    capi.qr_copy_layout(idx, lines, None)
+    assert int((lines.reshape(-1, 16)[:, 0] & np.uint64(0xFFFF)).max()) == 33799
+    n4 = 2 * S4L + 5000
+    codes = np.zeros(n4, dtype=np.uint8)
+    codes[:8191] = 3
+    codes[S4L:2 * S4L] = 3
+    idx4 = check_dna(synth.pack2(codes), n4, q=np.concatenate([np.arange(0, n4 + 1, 5), [n4]]).astype(np.uint64),
+                     layout=2)
+    info4 = capi.qr_info(idx4)
+    l4 = np.empty(info4["bytes_blocks"] // 8, dtype=np.uint64)
+    capi.qr_copy_layout(idx4, l4, None)
+    assert int((l4.reshape(-1, 16)[:, 0] >> np.uint64(48)).max()) == 38671
+    # overheads at large n (closed forms): 1.69% and 6.88%
+    n2 = 1 << 34
+    nb = n2 // 1008 + 1
+    assert abs(((128 * nb + 4 * ((nb + 31) // 32)) * 8 / n2 - 1) * 100 - 1.69) < 0.005
+    n4b = 1 << 32
+    nb4 = n4b // 480 + 1
+    assert abs(((128 * nb4 + 16 * ((nb4 + 63) // 64)) * 8 / (2 * n4b) - 1) * 100 - 6.88) < 0.01
+    with pytest.raises(capi.QRError):
+        capi.qr_set_tuning(idx, 4, 256, 0, 0)

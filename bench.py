@@ -347,6 +347,55 @@ def run_extras(args, idx, layout, tuning, dq, out, stream, peak):
     return res
 
 
+def run_layouts(args, stream):
+    """The space-time front: every layout of BiRank (n = 2^34) and QuadRank
+    (n = 2^32, rank with random symbols and rank_4), each autotuned on the
+    first 2^24 queries, timed on the full 2^28."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    m = 1 << args.log_m
+    names = {0: "paper (BiRank16 / QuadRank16)", 1: "sector (BiRank16x2 / 4-delta sectors)", 2: "128-byte lines"}
+    res = {"birank": {}, "quadrank": {}}
+    text, q = workloads.birank_inputs(args.log_n, args.log_m)
+    dq, o = dev_u64(q), None
+    o = torch.empty_like(dq)
+    dt = dev_u64(text)
+    del text
+    for layout in (0, 1, 2):
+        idx = capi.qr_build(dt, 1 << args.log_n, 2, layout=layout)
+        t = capi.qr_autotune(idx, dq[: 1 << 24], o, c=1)
+        ms = best_ms(lambda: capi.qr_rank(idx, dq, 1, o), stream)
+        info = capi.qr_info(idx)
+        res["birank"][names[layout]] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "tuning": t,
+                                        "overhead_pct": round(100 * ((info["bytes_blocks"] + info["bytes_super"]) * 8
+                                                                     / (1 << args.log_n) - 1), 3)}
+        idx.free()
+    del dt, dq, o
+    torch.cuda.empty_cache()
+    t4, q4, c4 = workloads.quadrank_inputs(args.log_n4, args.log_m)
+    dq, dc = dev_u64(q4), torch.from_numpy(c4).cuda()
+    o = torch.empty_like(dq)
+    o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
+    d4 = dev_u64(t4)
+    del t4
+    for layout in (0, 1, 2):
+        idx = capi.qr_build(d4, 1 << args.log_n4, 4, layout=layout)
+        t1 = capi.qr_autotune(idx, dq[: 1 << 24], o, c=dc[: 1 << 24])
+        ms1 = best_ms(lambda: capi.qr_rank_c(idx, dq, dc, o), stream)
+        t4r = capi.qr_autotune(idx, dq[: 1 << 24], o4, rank4=True)
+        ms4 = best_ms(lambda: capi.qr_rank4(idx, dq, o4), stream)
+        info = capi.qr_info(idx)
+        res["quadrank"][names[layout]] = {
+            "rank_Gq_s": round(m / (ms1 * 1e-3) / 1e9, 3), "rank4_Gq_s": round(m / (ms4 * 1e-3) / 1e9, 3),
+            "overhead_pct": round(100 * ((info["bytes_blocks"] + info["bytes_super"]) * 8
+                                         / (2 * (1 << args.log_n4)) - 1), 3)}
+        idx.free()
+    del d4, dq, dc, o, o4
+    torch.cuda.empty_cache()
+    log("[bench] layouts: " + json.dumps(res))
+    return {"layouts": res}
+
+
 def run_extras_other(args, stream, peak):
     import torch
     from paper_2602_04103_gb300 import capi, workloads
@@ -369,6 +418,7 @@ def run_extras_other(args, stream, peak):
         del dq, o
         torch.cuda.empty_cache()
     res.update(run_quadrank(args, stream, peak))
+    res.update(run_layouts(args, stream))
     res.update(run_fm(args, stream))
     res.update(run_serving(args))
     return res
@@ -572,7 +622,7 @@ def main():
     ap.add_argument("--serve-log-n", type=int, default=28)
     ap.add_argument("--serve-stream-calls", action="store_true",
                     help="also run the batching server without CUDA graphs")
-    ap.add_argument("--only", choices=["fm", "quadrank", "serving", "probe"], default=None,
+    ap.add_argument("--only", choices=["fm", "quadrank", "serving", "probe", "layouts"], default=None,
                     help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
@@ -583,6 +633,8 @@ def main():
             res = run_fm(args, stream)
         elif args.only == "serving":
             res = run_serving(args)
+        elif args.only == "layouts":
+            res = run_layouts(args, stream)
         elif args.only == "probe":
             res = {"random_32B_requests_G_per_s": round(probe_ceiling(stream), 3),
                    "probe": "qr_probe_gather: 2^26 random 32-byte loads over a 4 GiB buffer, 4 in flight per thread"}

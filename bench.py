@@ -344,6 +344,20 @@ def run_extras(args, idx, layout, tuning, dq, out, stream, peak):
                                     "algorithmic_bytes_per_query": round(bpq, 2),
                                     "roofline_frac": round(gq * bpq / peak, 4), "layout": layout}
     log(f"[bench] sorted: {gq:.2f} Gq/s")
+    # latency mode: dependent queries (each position from the previous answer)
+    if layout in (0, 1):
+        n = 1 << args.log_n
+        q0 = dq[: 1 << 20]
+        o2 = torch.empty((q0.numel(), 2), dtype=torch.int64, device="cuda")
+        steps1 = 2000
+        ms1 = best_ms(lambda: capi.qr_rank_chain(idx, q0[:1], steps1, 1, o2), stream)
+        stepsN = 64
+        msN = best_ms(lambda: capi.qr_rank_chain(idx, q0, stepsN, 1, o2), stream)
+        res["birank_dependent_queries"] = {
+            "one_chain_ns_per_query": round(ms1 * 1e6 / steps1, 1),
+            "chains_2^20_Gq_s": round(q0.numel() * stepsN / (msN * 1e-3) / 1e9, 3),
+            "note": "qr_rank_chain: each query position is derived from the previous answer"}
+        log(f"[bench] dependent: {res['birank_dependent_queries']}")
     return res
 
 

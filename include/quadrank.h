@@ -161,6 +161,30 @@ int qr_rank_c(const qr_index* idx, const uint64_t* q, const uint8_t* c, uint64_t
 int qr_rank4(const qr_index* idx, const uint64_t* q, uint64_t m, uint64_t* out4, void* stream);
 
 /*
+ * qr_prefix_rank -- out[k] = rank(q[k], 0) + ... + rank(q[k], c): the number
+ * of characters at most c before q[k] (sigma 4 only), the operation the paper
+ * names for a bidirectional FM-index (Sec. 6, future work); computed from the
+ * same line as rank_4.  c in 0..3; q > n gives UINT64_MAX and QR_ERANGE.
+ * Errors: QR_EINVAL (sigma != 4, c out of range, NULL buffers with m > 0).
+ */
+int qr_prefix_rank(const qr_index* idx, const uint64_t* q, uint64_t m, int c, uint64_t* out, void* stream);
+
+/*
+ * qr_rank_chain -- dependent queries (the paper's latency measurement, Sec.
+ * 5.1: each query depends on the result of the previous one).  Chain k starts
+ * at q0[k] and takes `steps` queries:
+ *   r_t = rank(q_t, c),  q_{t+1} = floor(x (n + 1) / 2^64)  with
+ *   x = (q_t + r_t) * 0x9E3779B97F4A7C15 mod 2^64,
+ * so a chain has one line in flight at a time; chains run in parallel, one
+ * per thread.  out2[2k] = q_{steps-1} (the last position queried), out2[2k+1] =
+ * r_{steps-1}.  A start q0[k] > n gives two UINT64_MAX and QR_ERANGE.
+ * Layouts: QR_LAYOUT_PAPER and QR_LAYOUT_SECTOR (QR_EINVAL for others).
+ * Errors: QR_EINVAL (steps = 0, c out of range, NULL buffers), QR_ECUDA.
+ */
+int qr_rank_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out2,
+                  void* stream);
+
+/*
  * qr_rank_host / qr_rank4_host -- the same queries with HOST buffers: the
  * call streams q to the device in chunks, runs the kernel and copies the
  * results back, overlapping the three on internal streams, and returns when

@@ -60,6 +60,7 @@ def _load():
         lib.or_count_sa.argtypes = [_P, u64, _P, _P, _P, u64, _P]
         lib.or_count_brute_batch.argtypes = [_P, u64, _P, _P, u64, _P]
         lib.or_revcomp.argtypes = [_P, u64, _P]
+        lib.or_rank_chain.argtypes = [_P, u64, C.c_int, _P, u64, u64, C.c_int, _P]
         lib.or_fm_steps.restype = u64
         lib.or_fm_steps.argtypes = [_P, u64, _P, _P, _P, u64, u64, _P]
         _lib = lib
@@ -110,6 +111,22 @@ def rank4(text: np.ndarray, n: int, q: np.ndarray) -> tuple[np.ndarray, int]:
     text, q = _u64(text), _u64(q)
     out = np.empty((q.size, 4), dtype=np.uint64)
     rc = _load().or_rank_sweep(_p(text), n, 4, _p(q), q.size, 2, 0, None, _p(out))
+    return out, rc
+
+
+def prefix_rank(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: int) -> tuple[np.ndarray, int]:
+    """#{i < q[k] : t_i <= c} for every k by one sweep; returns (out, rc)."""
+    text, q = _u64(text), _u64(q)
+    out = np.empty(q.size, dtype=np.uint64)
+    rc = _load().or_rank_sweep(_p(text), n, sigma, _p(q), q.size, 3, c, None, _p(out))
+    return out, rc
+
+
+def rank_chain(text: np.ndarray, n: int, sigma: int, q0: np.ndarray, steps: int, c: int) -> tuple[np.ndarray, int]:
+    """Dependent query chains: (out[chains, 2] = last position, last rank; rc)."""
+    text, q0 = _u64(text), _u64(q0)
+    out = np.empty((q0.size, 2), dtype=np.uint64)
+    rc = _load().or_rank_chain(_p(text), n, sigma, _p(q0), q0.size, steps, c, _p(out))
     return out, rc
 
 

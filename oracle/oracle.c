@@ -65,12 +65,13 @@ static int cmp_qpair(const void* a, const void* b) {
  * mode 0: out[k] = rank(q[k], c)              (scalar c; c_arr == NULL)
  * mode 1: out[k] = rank(q[k], c_arr[k])
  * mode 2: out[4k + c] = rank(q[k], c), c = 0..sigma-1   (rank_4 for sigma = 4)
+ * mode 3: out[k] = #{ i < q[k] : t_i <= c }            (prefix_rank, Sec. 6)
  * Queries with q > n get UINT64_MAX and the call returns OR_ERANGE.
  */
 int or_rank_sweep(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q, uint64_t m,
                   int mode, int c, const uint8_t* c_arr, uint64_t* out) {
     if (sigma != 2 && sigma != 4) return OR_EINVAL;
-    if (mode == 0 && (c < 0 || c >= sigma)) return OR_EINVAL;
+    if ((mode == 0 || mode == 3) && (c < 0 || c >= sigma)) return OR_EINVAL;
     if (mode == 2 && sigma != 4) return OR_EINVAL;
     qpair* ord = (qpair*)malloc((m ? m : 1) * sizeof(qpair));
     if (!ord) return OR_ENOMEM;
@@ -99,7 +100,11 @@ int or_rank_sweep(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q
             }
         }
         if (mode == 0) out[idx] = cnt[c];
-        else if (mode == 1) {
+        else if (mode == 3) {
+            uint64_t r = 0;
+            for (int s = 0; s <= c; s++) r += cnt[s];
+            out[idx] = r;
+        } else if (mode == 1) {
             int cc = c_arr[idx];
             if (cc >= sigma) { out[idx] = UINT64_MAX; rc = OR_EINVAL; }
             else out[idx] = cnt[cc];
@@ -108,6 +113,42 @@ int or_rank_sweep(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q
         }
     }
     free(ord);
+    return rc;
+}
+
+/*
+ * Dependent query chains (latency mode, Sec. 5.1): chain k starts at q0[k];
+ * r_t = rank(q_t, c) and q_{t+1} = floor(x (n + 1) / 2^64) with
+ * x = (q_t + r_t) * 0x9E3779B97F4A7C15 mod 2^64.  rank is read from a table
+ * of prefix counts built by one pass over the text.  out[2k] = last position,
+ * out[2k+1] = last rank.
+ */
+int or_rank_chain(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q0, uint64_t nchains,
+                  uint64_t steps, int c, uint64_t* out) {
+    if ((sigma != 2 && sigma != 4) || c < 0 || c >= sigma || steps == 0) return OR_EINVAL;
+    uint64_t* pref = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+    if (!pref) return OR_ENOMEM;
+    pref[0] = 0;
+    for (uint64_t i = 0; i < n; i++) pref[i + 1] = pref[i] + (text_char(text, sigma, i) == (uint64_t)c);
+    int rc = OR_OK;
+    for (uint64_t k = 0; k < nchains; k++) {
+        uint64_t q = q0[k], r = 0;
+        if (q > n) {
+            out[2 * k] = out[2 * k + 1] = UINT64_MAX;
+            rc = OR_ERANGE;
+            continue;
+        }
+        for (uint64_t t = 0; t < steps; t++) {
+            r = pref[q];
+            if (t + 1 < steps) {
+                const uint64_t x = (q + r) * 0x9E3779B97F4A7C15ull;
+                q = (uint64_t)(((unsigned __int128)x * (n + 1)) >> 64);
+            }
+        }
+        out[2 * k] = q;
+        out[2 * k + 1] = r;
+    }
+    free(pref);
     return rc;
 }
 

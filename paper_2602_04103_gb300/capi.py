@@ -58,6 +58,8 @@ _sig("qr_build_ex", [vp, u64, i32, i32, i32, vp, C.POINTER(vp)])
 _sig("qr_rank", [vp, vp, u64, i32, vp, vp])
 _sig("qr_rank_c", [vp, vp, vp, u64, vp, vp])
 _sig("qr_rank4", [vp, vp, u64, vp, vp])
+_sig("qr_prefix_rank", [vp, vp, u64, i32, vp, vp])
+_sig("qr_rank_chain", [vp, vp, u64, u64, i32, vp, vp])
 _sig("qr_rank_host", [vp, vp, vp, u64, i32, vp, vp])
 _sig("qr_rank4_host", [vp, vp, u64, vp, vp])
 _sig("qr_info", [vp, C.POINTER(qr_info_t)])
@@ -137,6 +139,15 @@ def qr_rank_c(idx: QRIndex, q, c, out, stream=None) -> None:
 
 def qr_rank4(idx: QRIndex, q, out4, stream=None) -> None:
     _check(lib.qr_rank4(idx, ptr(q), numel(q), ptr(out4), stream_ptr(stream)), "qr_rank4")
+
+
+def qr_prefix_rank(idx: QRIndex, q, c: int, out, stream=None) -> None:
+    _check(lib.qr_prefix_rank(idx, ptr(q), numel(q), c, ptr(out), stream_ptr(stream)), "qr_prefix_rank")
+
+
+def qr_rank_chain(idx: QRIndex, q0, steps: int, c: int, out2, stream=None) -> None:
+    """Dependent query chains (out2: 2 x chains: last position, last rank)."""
+    _check(lib.qr_rank_chain(idx, ptr(q0), numel(q0), steps, c, ptr(out2), stream_ptr(stream)), "qr_rank_chain")
 
 
 def qr_rank_host(idx: QRIndex, q_host, c, out_host, stream=None) -> None:

@@ -170,6 +170,25 @@ int qr_rank4(const qr_index* idx, const uint64_t* q, uint64_t m, uint64_t* out4,
     return launch_rank(idx, q, nullptr, 0, m, out4, 1, (cudaStream_t)stream);
 }
 
+int qr_prefix_rank(const qr_index* idx, const uint64_t* q, uint64_t m, int c, uint64_t* out, void* stream) {
+    int rc = check_query(idx, q, out, m, "qr_prefix_rank");
+    if (rc) return rc;
+    if (idx->sigma != 4) return fail(QR_EINVAL, "qr_prefix_rank: needs a sigma 4 index");
+    if (c < 0 || c > 3) return fail(QR_EINVAL, "qr_prefix_rank: symbol out of range");
+    return launch_rank(idx, q, nullptr, c, m, out, 2, (cudaStream_t)stream);
+}
+
+int qr_rank_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out2,
+                  void* stream) {
+    int rc = check_query(idx, q0, out2, nchains, "qr_rank_chain");
+    if (rc) return rc;
+    if (steps == 0) return fail(QR_EINVAL, "qr_rank_chain: steps must be >= 1");
+    if (c < 0 || c >= idx->sigma) return fail(QR_EINVAL, "qr_rank_chain: symbol out of range");
+    if (idx->layout != QR_LAYOUT_PAPER && idx->layout != QR_LAYOUT_SECTOR)
+        return fail(QR_EINVAL, "qr_rank_chain: paper or sector layout only");
+    return launch_chain(idx, q0, nchains, steps, c, out2, (cudaStream_t)stream);
+}
+
 // Host-buffer pipeline: chunks go round-robin to kPipe internal streams;
 // each chunk is copied in, ranked and copied out on its stream, so the copies
 // of some chunks overlap the kernels and copy-outs of others (the copy

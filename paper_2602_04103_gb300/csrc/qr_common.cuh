@@ -382,9 +382,12 @@ uint64_t super_lines(int sigma, int layout);
 uint64_t line_bytes(int layout);
 // Build the layout into an already sized index from a device text.
 int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
-// Launch the rank kernels (no argument checks beyond the mode).
+// Launch the rank kernels (no argument checks beyond the mode); rank4 = 0:
+// rank(q, c), 1: rank_4, 2: prefix_rank(q, c).
 int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                 int rank4, cudaStream_t s);
+int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out,
+                 cudaStream_t s);
 int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
                  int k, int threads, cudaStream_t s);
 }  // namespace qr

@@ -17,7 +17,11 @@
 namespace qr {
 namespace {
 
-enum Kind { kBiScalar = 0, kBiVec = 1, kQuadScalar = 2, kQuadVec = 3, kQuad4 = 4 };
+enum Kind { kBiScalar = 0, kBiVec = 1, kQuadScalar = 2, kQuadVec = 3, kQuad4 = 4, kQuadPrefix = 5 };
+
+// rank_4 and prefix_rank both need all four counts of the query's line
+template <int KIND>
+constexpr bool all4() { return KIND == kQuad4 || KIND == kQuadPrefix; }
 
 struct RankArgs {
     const uint4* __restrict__ lines;
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
                 j = div224(qq);
                 pos[k] = (uint32_t)(qq - j * kB4) + 32;
                 upper = pos[k] >= 128;
-                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
+                if (all4<KIND>()) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
                 else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + (cv[k] & 3));
             }
             const uint4* L = a.lines + 4 * j;
@@ -159,7 +163,19 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
                 uint64_t x[4];
                 if (upper) { x[0] = lo64(va[k]); x[1] = hi64(va[k]); x[2] = lo64(vb[k]); x[3] = hi64(vb[k]); }
                 else { x[0] = w0; x[1] = w1; x[2] = lo64(va[k]); x[3] = hi64(va[k]); }
-                if (KIND == kQuad4) {
+                if (KIND == kQuadPrefix) {
+                    uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
+                    uint64_t r[4];
+                    quad_finish4(s, w0, w1, x, pos[k], r);
+                    uint64_t sum = 0;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) sum += c <= a.c ? r[c] : 0;
+                    if (range_bad) sum = ~0ull;
+                    if (live[k]) {
+                        st_stream_u64(a.out + i, sum);
+                        bad_flags |= range_bad ? kStatusRange : 0u;
+                    }
+                } else if (KIND == kQuad4) {
                     uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
                     uint64_t r[4];
                     quad_finish4(s, w0, w1, x, pos[k], r);
@@ -226,7 +242,7 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
                 const uint32_t d = (uint32_t)(qq - j * kB4s);
                 h = d >= kHalf4s;
                 r[k] = d - h * (uint32_t)kHalf4s;
-                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
+                if (all4<KIND>()) s4[k] = __ldg((const uint4*)a.supers + (j >> 8));
                 else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + (cv[k] & 3));
             }
             W[k] = ld_line32(a.lines + 4 * j + 2 * h);
@@ -244,6 +260,18 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
                 if (live[k]) {
                     st_stream_u64(a.out + i, res);
                     bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                }
+            } else if (KIND == kQuadPrefix) {
+                const uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
+                uint64_t res[4];
+                quad_sector_finish4(s, W[k], r[k], res);
+                uint64_t sum = 0;
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum += c <= a.c ? res[c] : 0;
+                if (range_bad) sum = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, sum);
+                    bad_flags |= range_bad ? kStatusRange : 0u;
                 }
             } else if (KIND == kQuad4) {
                 const uint32_t s[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
@@ -312,7 +340,7 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
             } else {
                 j = div480(qq);
                 pos[k] = (uint32_t)(qq - j * kB4L);
-                if (KIND == kQuad4) s4[k] = __ldg((const uint4*)a.supers + (j >> 6));
+                if (all4<KIND>()) s4[k] = __ldg((const uint4*)a.supers + (j >> 6));
                 else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 6) + (cv[k] & 3));
             }
             const unsigned long long L = (unsigned long long)(a.lines + 8 * j);
@@ -346,7 +374,7 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
                     const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr;
                     const int32_t hi = upper ? (int32_t)pr : (int32_t)kMid4L;
                     const unsigned long long d0 = __shfl_sync(kAll, (unsigned long long)W[k][r].a, 0, 4);
-                    if (KIND == kQuad4) {
+                    if (all4<KIND>()) {
                         uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
                         line128_count4(W[k][r], sub, lo, hi, -1, cnt, nl, nh, n3);
                         nl += __shfl_xor_sync(kAll, nl, 1, 4);
@@ -387,6 +415,15 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
                     st_stream_u64(a.out + i, out);
                     bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
                 }
+            } else if (KIND == kQuadPrefix) {
+                uint64_t sum = 0;
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum += c <= a.c ? res[c] : 0;
+                if (range_bad) sum = ~0ull;
+                if (live[k]) {
+                    st_stream_u64(a.out + i, sum);
+                    bad_flags |= range_bad ? kStatusRange : 0u;
+                }
             } else if (KIND == kQuad4) {
                 if (range_bad) res[0] = res[1] = res[2] = res[3] = ~0ull;
                 if (live[k]) {
@@ -408,6 +445,70 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
         }
     }
     if (bad_flags) atomicOr(a.status, bad_flags);
+}
+
+// Dependent queries (latency mode): every thread follows one chain, each
+// query position derived from the previous answer, so only one line per chain
+// is ever in flight.  Paper and sector layouts; lines read as 32-byte sectors.
+__device__ __forceinline__ uint64_t chain_next(uint64_t q, uint64_t r, uint64_t n) {
+    return mulhi64((q + r) * 0x9E3779B97F4A7C15ull, n + 1);
+}
+
+template <bool QUAD, bool SECTOR>
+__device__ __forceinline__ uint64_t rank_one(const RankArgs& a, uint64_t q, int c) {
+    if (SECTOR) {
+        if (!QUAD) {
+            const uint64_t j = div480(q);
+            const uint32_t p = (uint32_t)(q - j * kB2s), h = p >= kHalf2s;
+            const uint32_t s = __ldg((const uint32_t*)a.supers + (j >> 7));
+            const u64x4 W = ld_line32(a.lines + 4 * j + 2 * h);
+            const uint64_t r1 = birank_sector_finish(s, W, p - h * (uint32_t)kHalf2s);
+            return c == 1 ? r1 : q - r1;
+        }
+        const uint64_t j = div192(q);
+        const uint32_t d = (uint32_t)(q - j * kB4s), h = d >= kHalf4s;
+        const uint32_t s = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + c);
+        const u64x4 W = ld_line32(a.lines + 4 * j + 2 * h);
+        return quad_sector_finish1(s, W, d - h * (uint32_t)kHalf4s, c);
+    }
+    const uint64_t j = QUAD ? div224(q) : div496(q);
+    const uint32_t pos = QUAD ? (uint32_t)(q - j * kB4) + 32 : (uint32_t)(q - j * kB2);
+    const bool upper = QUAD ? pos >= 128 : pos >= kMid2;
+    const uint4* L = a.lines + 4 * j;
+    const u64x4 S0 = ld_line32(L);
+    uint64_t x[4] = {S0.a, S0.b, S0.c, S0.d};
+    if (upper) {
+        const u64x4 S1 = ld_line32(L + 2);
+        x[0] = S1.a; x[1] = S1.b; x[2] = S1.c; x[3] = S1.d;
+    }
+    if (!QUAD) {
+        const uint32_t s = __ldg((const uint32_t*)a.supers + (j >> 7));
+        const uint64_t r1 = birank_finish(s, S0.a, x, pos);
+        return c == 1 ? r1 : q - r1;
+    }
+    const uint32_t s = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + c);
+    return quad_finish1(s, quad_delta(S0.a, S0.b, c), x, pos, c);
+}
+
+// a.q = chain starts (a.m chains), a.out[2k] = final position, a.out[2k+1] =
+// last rank; a.c = symbol; steps per chain in `steps`.
+template <bool QUAD, bool SECTOR>
+__global__ void __launch_bounds__(256) rank_chain_kernel(RankArgs a, uint64_t steps) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t q = a.q[k], r = 0;
+        if (q > a.n) {
+            a.out[2 * k] = ~0ull;
+            a.out[2 * k + 1] = ~0ull;
+            atomicOr(a.status, kStatusRange);
+            continue;
+        }
+        for (uint64_t t = 0; t < steps; t++) {
+            r = rank_one<QUAD, SECTOR>(a, q, a.c);
+            if (t + 1 < steps) q = chain_next(q, r, a.n);
+        }
+        a.out[2 * k] = q;
+        a.out[2 * k + 1] = r;
+    }
 }
 
 // ---------------------------------------------------------------- launch table
@@ -464,6 +565,7 @@ KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false)
             case kQuadScalar: return pick_line<kQuadScalar>(k);
             case kQuadVec: return pick_line<kQuadVec>(k);
             case kQuad4: return pick_line<kQuad4>(k);
+            case kQuadPrefix: return pick_line<kQuadPrefix>(k);
             default: return nullptr;
         }
     }
@@ -474,6 +576,7 @@ KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false)
             case kQuadScalar: return pick_sector<kQuadScalar>(k);
             case kQuadVec: return pick_sector<kQuadVec>(k);
             case kQuad4: return pick_sector<kQuad4>(k);
+            case kQuadPrefix: return pick_sector<kQuadPrefix>(k);
             default: return nullptr;
         }
     }
@@ -483,6 +586,7 @@ KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false)
         case kQuadScalar: return pick<kQuadScalar>(k, load);
         case kQuadVec: return pick<kQuadVec>(k, load);
         case kQuad4: return pick<kQuad4>(k, load);
+        case kQuadPrefix: return pick<kQuadPrefix>(k, load);
         default: return nullptr;
     }
 }
@@ -541,7 +645,7 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     if (m == 0) return QR_OK;
     int kind;
     if (idx->sigma == 2) kind = cvec ? kBiVec : kBiScalar;
-    else kind = rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
+    else kind = rank4 == 2 ? kQuadPrefix : rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
     const qr_tuning_t& t = idx->tune;
     KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR,
                             idx->layout == QR_LAYOUT_LINE128);
@@ -552,6 +656,21 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     uint64_t grid = t.grid_blocks > 0 ? (uint64_t)t.grid_blocks : resident_grid(fn, t.block_threads);
     if (grid > tiles) grid = tiles;
     fn<<<(unsigned)grid, t.block_threads, 0, s>>>(a);
+    QR_CUDA_TRY(cudaGetLastError());
+    return QR_OK;
+}
+
+int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out,
+                 cudaStream_t s) {
+    if (nchains == 0) return QR_OK;
+    RankArgs a{idx->lines, idx->supers, idx->n, q0, nullptr, c, nchains, out, idx->status};
+    const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR;
+    void (*fn)(RankArgs, uint64_t) = quad ? (sector ? rank_chain_kernel<true, true> : rank_chain_kernel<true, false>)
+                                          : (sector ? rank_chain_kernel<false, true> : rank_chain_kernel<false, false>);
+    uint64_t grid = (nchains + 255) / 256;
+    const uint64_t cap = (uint64_t)device_props().sms * 8;
+    if (grid > cap) grid = cap;
+    fn<<<(unsigned)grid, 256, 0, s>>>(a, steps);
     QR_CUDA_TRY(cudaGetLastError());
     return QR_OK;
 }

@@ -494,3 +494,46 @@ def test_line128_max_deltas_and_overheads():
     assert abs(((128 * nb4 + 16 * ((nb4 + 63) // 64)) * 8 / (2 * n4b) - 1) * 100 - 6.88) < 0.01
     with pytest.raises(capi.QRError):
         capi.qr_set_tuning(idx, 4, 256, 0, 0)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_prefix_rank(layout):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S4 + 321
+    w4 = synth.dna_gc_runs(71, n, 0.4, 0.05, 10, 1000)
+    idx = build(w4, n, 4, layout)
+    q = np.concatenate([synth.queries(72, n, 200_000), [0, n, n + 1]]).astype(np.uint64)
+    dq = dev_u64(q)
+    out = torch.empty_like(dq)
+    for c in range(4):
+        capi.qr_prefix_rank(idx, dq, c, out)
+        want, rc = oracle.prefix_rank(w4, n, 4, q, c)
+        assert rc == oracle.OR_ERANGE and np.array_equal(host_u64(out), want), c
+    assert capi.qr_status(idx) == capi.QR_ERANGE
+    with pytest.raises(capi.QRError):
+        capi.qr_prefix_rank(idx, dq, 4, out)
+    with pytest.raises(capi.QRError):
+        capi.qr_prefix_rank(build(synth.bits(1, 100, 0.5), 100, 2), dq, 0, out)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("sigma", [2, 4])
+def test_rank_chain(layout, sigma):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 4 * S2 + 99 if sigma == 2 else 4 * S4 + 99
+    words = synth.bits(91, n, 0.5) if sigma == 2 else synth.dna_uniform(92, n)
+    idx = build(words, n, sigma, layout)
+    q0 = np.concatenate([synth.queries(93, n, 5000), [0, n, n + 1]]).astype(np.uint64)
+    out = torch.empty((q0.size, 2), dtype=torch.int64, device="cuda")
+    for c in range(sigma):
+        capi.qr_rank_chain(idx, dev_u64(q0), 50, c, out)
+        want, rc = oracle.rank_chain(words, n, sigma, q0, 50, c)
+        assert rc == oracle.OR_ERANGE
+        assert np.array_equal(host_u64(out).reshape(-1, 2), want), c
+    assert capi.qr_status(idx) == capi.QR_ERANGE
+    with pytest.raises(capi.QRError):
+        capi.qr_rank_chain(idx, dev_u64(q0), 0, 0, out)
+    with pytest.raises(capi.QRError):
+        capi.qr_rank_chain(build(words, n, sigma, 2), dev_u64(q0), 5, 0, out)

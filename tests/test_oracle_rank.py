@@ -158,3 +158,42 @@ def test_sweep_matches_naive_unsorted_duplicates():
     got, rc = oracle.rank(words, n, 2, q, 1)
     assert rc == 0
     assert got.tolist() == [oracle.rank_naive(words, n, 2, int(x), 1) for x in q]
+
+
+def test_prefix_rank_pins(golden):
+    # GATTACA by hand: chars <= C (A or C) before q = rankA + rankC from the fixture
+    g = golden("rank_dna_gattaca.txt")
+    codes = np.array([DNA[ch] for ch in g["text"]], dtype=np.uint8)
+    words = synth.pack2(codes)
+    q = np.arange(8, dtype=np.uint64)
+    want = [int(a) + int(b) for a, b in zip(g["rankA"].split(), g["rankC"].split())]
+    got, rc = oracle.prefix_rank(words, 7, 4, q, 1)
+    assert rc == 0 and got.tolist() == want
+    # numpy: cumulative count of codes <= c; c = 3 gives q
+    rng = np.random.default_rng(77)
+    codes = rng.integers(0, 4, 5003).astype(np.uint8)
+    words = synth.pack2(codes)
+    q = np.arange(5004, dtype=np.uint64)
+    for c in range(4):
+        pref = np.concatenate([[0], np.cumsum(codes <= c)]).astype(np.uint64)
+        assert np.array_equal(oracle.prefix_rank(words, 5003, 4, q, c)[0], pref)
+    assert np.array_equal(oracle.prefix_rank(words, 5003, 4, q, 3)[0], q)
+
+
+def test_rank_chain_pins():
+    # every step of a chain: rank by the definition loop, the next position by the chain rule
+    n = 3001
+    words = synth.bits(81, n, 0.4)
+    q0 = np.array([0, 5, n, 1234], dtype=np.uint64)
+    steps = 7
+    got, rc = oracle.rank_chain(words, n, 2, q0, steps, 1)
+    assert rc == 0
+    for k, q in enumerate(q0.tolist()):
+        r = 0
+        for t in range(steps):
+            r = oracle.rank_naive(words, n, 2, q, 1)
+            if t + 1 < steps:
+                q = ((((q + r) * 0x9E3779B97F4A7C15) % 2 ** 64) * (n + 1)) >> 64
+        assert got[k].tolist() == [q, r]
+    bad, rc = oracle.rank_chain(words, n, 2, np.array([n + 1], dtype=np.uint64), 3, 1)
+    assert rc == oracle.OR_ERANGE and bad[0, 0] == oracle.U64_MAX

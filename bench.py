@@ -195,14 +195,20 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
 
 
 # ---------------------------------------------------------------- our arm
-def probe_ceiling(stream):
-    """Random 32-byte loads over a 4 GiB buffer: the GPU's random request rate."""
+def probe_ceiling(stream, quad128: bool = False):
+    """Random 32-byte loads over a 4 GiB buffer: the GPU's random request rate.
+    quad128: random 128-byte records, each read by the four lanes of a quad in
+    one instruction (the access of the 128-byte line layout)."""
     import torch
     from paper_2602_04103_gb300 import capi
     nbytes, m = 4 << 30, 1 << 26
     buf = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
     out = torch.empty(m, dtype=torch.int64, device="cuda")
-    ms = best_ms(lambda: capi.qr_probe_gather(buf, nbytes // 32, 32, m, 99, out, 4, 256, load_bytes=32), stream)
+    if quad128:
+        ms = min(best_ms(lambda: capi.qr_probe_gather(buf, nbytes // 128, 128, m, 99, out, k, 256, load_bytes=128),
+                         stream) for k in (1, 2))
+    else:
+        ms = best_ms(lambda: capi.qr_probe_gather(buf, nbytes // 32, 32, m, 99, out, 4, 256, load_bytes=32), stream)
     del buf, out
     torch.cuda.empty_cache()
     return m / (ms * 1e-3) / 1e9
@@ -222,8 +228,10 @@ def run_ours(args):
     t0 = time.time()
     text, q = workloads.birank_inputs(args.log_n, args.log_m, rank=rank)
     log(f"[bench] inputs n=2^{args.log_n} bits, m=2^{args.log_m} queries: {time.time() - t0:.1f}s")
-    ceiling = probe_ceiling(stream) if args.layout is None else float("nan")
-    log(f"[bench] random 32-byte request ceiling: {ceiling:.2f} G/s")
+    nan = float("nan")
+    ceil32 = probe_ceiling(stream) if args.layout is None else nan
+    ceil128 = probe_ceiling(stream, quad128=True) if args.layout is None else nan
+    log(f"[bench] random request ceilings: 32-byte {ceil32:.2f} G/s, 128-byte quad {ceil128:.2f} G/s")
     dq = dev_u64(q)
     d_text = dev_u64(text)
     t0 = time.time()
@@ -240,6 +248,7 @@ def run_ours(args):
     info = capi.qr_info(idx)
     log(f"[bench] tuned build: layout {layout}, {tuning} ({t_tune:.1f}s)")
     out = torch.empty_like(dq)
+    ceiling = ceil128 if layout == 2 else ceil32
 
     def step():
         capi.qr_rank(idx, dq, 1, out)
@@ -269,6 +278,7 @@ def run_ours(args):
                 "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
                 "random_requests_per_query": round(rpq, 3),
                 "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
+                "random_request_ceiling_kind": "128-byte quad-cooperative" if layout == 2 else "32-byte",
                 "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4) if ceiling == ceiling else None}
 
     # end to end through the public host-buffer API (H2D + kernels + D2H)
@@ -406,6 +416,8 @@ def run_layouts(args, stream):
         idx.free()
     del d4, dq, dc, o, o4
     torch.cuda.empty_cache()
+    res["random_request_ceilings_G_per_s"] = {"32-byte": round(probe_ceiling(stream), 3),
+                                              "128-byte quad": round(probe_ceiling(stream, quad128=True), 3)}
     log("[bench] layouts: " + json.dumps(res))
     return {"layouts": res}
 
@@ -651,7 +663,9 @@ def main():
             res = run_layouts(args, stream)
         elif args.only == "probe":
             res = {"random_32B_requests_G_per_s": round(probe_ceiling(stream), 3),
-                   "probe": "qr_probe_gather: 2^26 random 32-byte loads over a 4 GiB buffer, 4 in flight per thread"}
+                   "random_128B_quad_requests_G_per_s": round(probe_ceiling(stream, quad128=True), 3),
+                   "probe": "qr_probe_gather: 2^26 random 32-byte loads over a 4 GiB buffer, 4 in flight per "
+                            "thread; 2^26 random 128-byte records read quad-cooperatively, 1 or 2 per thread"}
         else:
             res = run_quadrank(args, stream, peaks()[0])
         print(json.dumps(res), flush=True)

@@ -256,7 +256,9 @@ int qr_free(qr_index* idx);
  * qr_probe_gather -- measurement aid: out[k] = XOR of the `bytes`-byte record
  * at a random record index of buf for m draws, read with load_bytes-byte (16
  * or 32) vector loads, with the same threads-and-loads-in-flight scheme as the
- * rank kernels.
+ * rank kernels.  load_bytes = 128 (records of 128 bytes only) reads each
+ * record as the 128-byte line layout's rank kernels read a line: the four
+ * lanes of a quad each load one 32-byte sector of it in the same instruction.
  * It gives the random-access ceiling of this GPU's memory for records of 32,
  * 64 or 128 bytes, the GPU counterpart of the paper's measured random-access
  * limit of RAM (Sec. 5.1, "Lower bounds": 2.5 ns per cache line in total).
@@ -264,7 +266,8 @@ int qr_free(qr_index* idx);
  *   seed   splitmix64 seed of the record indices (uniform in [0, nrec)).
  *   out    device array of m uint64 (one digest per draw, defeats dead-code
  *          elimination).
- * Errors: QR_EINVAL (bytes not 16/32/64/128, nrec = 0, no kernel for
+ * Errors: QR_EINVAL (bytes not 16/32/64/128, load_bytes not 16/32/128 or 128
+ * with bytes != 128, nrec = 0, no kernel for
  * (bytes, queries_per_thread) -- 128-byte records allow at most 4 in flight).
  */
 int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed,

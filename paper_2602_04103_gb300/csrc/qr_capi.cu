@@ -446,7 +446,8 @@ int qr_free(qr_index* idx) {
 int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed,
                     uint64_t* out, int queries_per_thread, int block_threads, void* stream) {
     if (bytes != 16 && bytes != 32 && bytes != 64 && bytes != 128) return fail(QR_EINVAL, "probe: bytes");
-    if (load_bytes != 16 && load_bytes != 32) return fail(QR_EINVAL, "probe: load_bytes");
+    if (load_bytes != 16 && load_bytes != 32 && !(load_bytes == 128 && bytes == 128))
+        return fail(QR_EINVAL, "probe: load_bytes");
     if (nrec == 0 || !buf || (m > 0 && !out)) return fail(QR_EINVAL, "probe: empty buffer");
     if (((uintptr_t)buf & 15) != 0) return fail(QR_EINVAL, "probe: buf must be 16-byte aligned");
     if (block_threads < 64 || block_threads > 1024 || (block_threads & 31)) return fail(QR_EINVAL, "probe: threads");

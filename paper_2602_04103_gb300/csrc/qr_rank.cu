@@ -301,11 +301,33 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
 }
 
 // 128-byte line layout (QR_LAYOUT_LINE128): the four lanes of a quad answer
-// their four queries together.  In round r every lane of the quad loads its
-// sector (32 bytes) of the line of lane r's query -- one instruction, one
-// request, one 128-byte fill per query -- and counts the bits (or chars) of
-// the query's range that fall in its sector; two shuffles sum the four
-// partial counts and lane r keeps the result.
+// their four queries together.  For each query r of the quad every lane loads
+// its sector (32 bytes) of query r's line -- four lanes, one instruction, one
+// request, one 128-byte fill per query -- and computes its signed part of the
+// answer: plus or minus the ones (chars) of the query's range in its sector,
+// plus the delta on the lane holding sector 0.  A reduce-scatter over the quad
+// (3 shuffles per value) leaves lane r with the sum for query r.
+__device__ __forceinline__ int32_t quad_reduce_scatter(const int32_t v[4], int sub) {
+    constexpr uint32_t kAll = 0xffffffffu;
+    const bool hi2 = sub & 2, hi1 = sub & 1;
+    // step 1 (lanes sub ^ 2): keep the half of indices that contains sub
+    const int32_t s0 = hi2 ? v[0] : v[2], s1 = hi2 ? v[1] : v[3];
+    const int32_t k0 = hi2 ? v[2] : v[0], k1 = hi2 ? v[3] : v[1];
+    const int32_t a0 = k0 + __shfl_xor_sync(kAll, s0, 2, 4);
+    const int32_t a1 = k1 + __shfl_xor_sync(kAll, s1, 2, 4);
+    // step 2 (lanes sub ^ 1): keep index sub
+    return (hi1 ? a1 : a0) + __shfl_xor_sync(kAll, hi1 ? a0 : a1, 1, 4);
+}
+__device__ __forceinline__ uint64_t quad_reduce_scatter64(const uint64_t v[4], int sub) {
+    constexpr uint32_t kAll = 0xffffffffu;
+    const bool hi2 = sub & 2, hi1 = sub & 1;
+    const uint64_t s0 = hi2 ? v[0] : v[2], s1 = hi2 ? v[1] : v[3];
+    const uint64_t k0 = hi2 ? v[2] : v[0], k1 = hi2 ? v[3] : v[1];
+    const uint64_t a0 = k0 + __shfl_xor_sync(kAll, (unsigned long long)s0, 2, 4);
+    const uint64_t a1 = k1 + __shfl_xor_sync(kAll, (unsigned long long)s1, 2, 4);
+    return (hi1 ? a1 : a0) + __shfl_xor_sync(kAll, (unsigned long long)(hi1 ? a0 : a1), 1, 4);
+}
+
 template <int K, int KIND>
 __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
     constexpr bool kQuad = KIND >= kQuadScalar;
@@ -353,56 +375,63 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            uint32_t pr[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) pr[r] = __shfl_sync(kAll, pos[k], r, 4);
             uint64_t res[4] = {0, 0, 0, 0};
+            if (!kQuad) {
+                int32_t part[4];
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const uint32_t pr = __shfl_sync(kAll, pos[k], r, 4);
-                if (!kQuad) {
-                    const bool upper = pr >= kMid2L;
-                    const int32_t lo = upper ? (int32_t)(16 + kMid2L) : (int32_t)(16 + pr);
-                    const int32_t hi = upper ? (int32_t)(16 + pr) : (int32_t)(16 + kMid2L);
-                    uint32_t t = line128_count2(W[k][r], sub, lo, hi);
-                    t += __shfl_xor_sync(kAll, t, 1, 4);
-                    t += __shfl_xor_sync(kAll, t, 2, 4);
-                    const uint64_t d = __shfl_sync(kAll, (unsigned long long)(W[k][r].a & 0xFFFFull), 0, 4);
-                    if (sub == r) {
-                        const uint64_t mid = ((uint64_t)s1[k] << kShift2) + d;
-                        res[0] = upper ? mid + t : mid - t;
-                    }
-                } else {
-                    const bool upper = pr >= kMid4L;
-                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr;
-                    const int32_t hi = upper ? (int32_t)pr : (int32_t)kMid4L;
-                    const unsigned long long d0 = __shfl_sync(kAll, (unsigned long long)W[k][r].a, 0, 4);
-                    if (all4<KIND>()) {
-                        uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
-                        line128_count4(W[k][r], sub, lo, hi, -1, cnt, nl, nh, n3);
-                        nl += __shfl_xor_sync(kAll, nl, 1, 4);
-                        nl += __shfl_xor_sync(kAll, nl, 2, 4);
-                        nh += __shfl_xor_sync(kAll, nh, 1, 4);
-                        nh += __shfl_xor_sync(kAll, nh, 2, 4);
-                        n3 += __shfl_xor_sync(kAll, n3, 1, 4);
-                        n3 += __shfl_xor_sync(kAll, n3, 2, 4);
-                        if (sub == r) {
-                            const uint32_t nm = (uint32_t)(hi - lo);
-                            const uint32_t nc[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+                for (int r = 0; r < 4; r++) {
+                    const bool upper = pr[r] >= kMid2L;
+                    const int32_t lo = upper ? (int32_t)(16 + kMid2L) : (int32_t)(16 + pr[r]);
+                    const int32_t hi = upper ? (int32_t)(16 + pr[r]) : (int32_t)(16 + kMid2L);
+                    const int32_t cnt = (int32_t)line128_count2(W[k][r], sub, lo, hi);
+                    part[r] = (upper ? cnt : -cnt) + (sub == 0 ? (int32_t)(W[k][r].a & 0xFFFFull) : 0);
+                }
+                // delta +- count of the own query: rank(q) - 2^11 s >= 0
+                res[0] = ((uint64_t)s1[k] << kShift2) + (uint64_t)(int64_t)quad_reduce_scatter(part, sub);
+            } else if (!all4<KIND>()) {
+                int32_t part[4];
 #pragma unroll
-                            for (int c = 0; c < 4; c++) {
-                                const uint64_t mid = ((uint64_t)(&s4[k].x)[c] << kShift4) + ((d0 >> (16 * c)) & 0xFFFFull);
-                                res[c] = upper ? mid + nc[c] : mid - nc[c];
-                            }
-                        }
-                    } else {
-                        const int cr = __shfl_sync(kAll, cv[k], r, 4) & 3;
-                        uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
-                        line128_count4(W[k][r], sub, lo, hi, cr, cnt, nl, nh, n3);
-                        cnt += __shfl_xor_sync(kAll, cnt, 1, 4);
-                        cnt += __shfl_xor_sync(kAll, cnt, 2, 4);
-                        if (sub == r) {
-                            const uint64_t mid = ((uint64_t)s1[k] << kShift4) + ((d0 >> (16 * cr)) & 0xFFFFull);
-                            res[0] = upper ? mid + cnt : mid - cnt;
-                        }
-                    }
+                for (int r = 0; r < 4; r++) {
+                    const int cr = __shfl_sync(kAll, cv[k], r, 4) & 3;
+                    const bool upper = pr[r] >= kMid4L;
+                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr[r];
+                    const int32_t hi = upper ? (int32_t)pr[r] : (int32_t)kMid4L;
+                    uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
+                    line128_count4(W[k][r], sub, lo, hi, cr, cnt, nl, nh, n3);
+                    part[r] = (upper ? (int32_t)cnt : -(int32_t)cnt) +
+                              (sub == 0 ? (int32_t)((W[k][r].a >> (16 * cr)) & 0xFFFFull) : 0);
+                }
+                res[0] = ((uint64_t)s1[k] << kShift4) + (uint64_t)(int64_t)quad_reduce_scatter(part, sub);
+            } else {
+                int32_t pl[4], ph[4], p3[4];
+                uint64_t pd[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const bool upper = pr[r] >= kMid4L;
+                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr[r];
+                    const int32_t hi = upper ? (int32_t)pr[r] : (int32_t)kMid4L;
+                    uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
+                    line128_count4(W[k][r], sub, lo, hi, -1, cnt, nl, nh, n3);
+                    pl[r] = (int32_t)nl;
+                    ph[r] = (int32_t)nh;
+                    p3[r] = (int32_t)n3;
+                    pd[r] = sub == 0 ? W[k][r].a : 0;  // the four deltas of line r
+                }
+                const uint32_t nl = (uint32_t)quad_reduce_scatter(pl, sub), nh = (uint32_t)quad_reduce_scatter(ph, sub);
+                const uint32_t n3 = (uint32_t)quad_reduce_scatter(p3, sub);
+                const uint64_t d0 = quad_reduce_scatter64(pd, sub);
+                const uint32_t pown = pos[k];
+                const bool upper = pown >= kMid4L;
+                const uint32_t nm = upper ? pown - (uint32_t)kMid4L : (uint32_t)kMid4L - pown;
+                const uint32_t nc[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+                const uint32_t sv[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const uint64_t mid = ((uint64_t)sv[c] << kShift4) + ((d0 >> (16 * c)) & 0xFFFFull);
+                    res[c] = upper ? mid + nc[c] : mid - nc[c];
                 }
             }
             const bool range_bad = qv[k] > a.n;
@@ -605,11 +634,18 @@ __device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-template <int K, int V, int W>  // V = 16-byte quarters per record, W = bytes per load (16 or 32)
+// V = 16-byte quarters per record, W = bytes per load: 16 or 32 (each lane
+// reads its own record), 128 (128-byte records read quad-cooperatively as the
+// 128-byte line rank kernels do: lane s of a quad loads sector s of the four
+// records of the quad in four instructions, then an XOR reduce-scatter gives
+// every lane the digest of its own record).
+template <int K, int V, int W>
 __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ buf, uint64_t nrec, uint64_t m,
                                                      uint64_t seed, uint64_t* __restrict__ out) {
+    constexpr uint32_t kAll = 0xffffffffu;
     const uint64_t tile = (uint64_t)blockDim.x * K;
-    constexpr int kLoads = W == 32 && V >= 2 ? V / 2 : V;
+    constexpr int kLoads = W == 128 ? 4 : W == 32 && V >= 2 ? V / 2 : V;
+    const int sub = threadIdx.x & 3;
     for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < m; t0 += (uint64_t)gridDim.x * tile) {
         uint64_t v[K][kLoads];
 #pragma unroll
@@ -618,7 +654,11 @@ __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ b
             const uint64_t r = mulhi64(probe_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull), nrec);
 #pragma unroll
             for (int u = 0; u < kLoads; u++) {
-                if (W == 32 && V >= 2) {
+                if (W == 128) {
+                    const uint64_t ru = __shfl_sync(kAll, (unsigned long long)r, u, 4);
+                    const u64x4 x = ld_line32(buf + ru * 8 + 2 * sub);
+                    v[k][u] = x.a ^ x.b ^ x.c ^ x.d;
+                } else if (W == 32 && V >= 2) {
                     const u64x4 x = ld_line32(buf + r * V + 2 * u);
                     v[k][u] = x.a ^ x.b ^ x.c ^ x.d;
                 } else {
@@ -631,8 +671,17 @@ __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ b
         for (int k = 0; k < K; k++) {
             const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
             uint64_t d = 0;
+            if (W == 128) {
+                const bool hi2 = sub & 2, hi1 = sub & 1;
+                const uint64_t a0 = (hi2 ? v[k][2] : v[k][0]) ^
+                                    __shfl_xor_sync(kAll, (unsigned long long)(hi2 ? v[k][0] : v[k][2]), 2, 4);
+                const uint64_t a1 = (hi2 ? v[k][3] : v[k][1]) ^
+                                    __shfl_xor_sync(kAll, (unsigned long long)(hi2 ? v[k][1] : v[k][3]), 2, 4);
+                d = (hi1 ? a1 : a0) ^ __shfl_xor_sync(kAll, (unsigned long long)(hi1 ? a0 : a1), 1, 4);
+            } else {
 #pragma unroll
-            for (int u = 0; u < kLoads; u++) d ^= v[k][u];
+                for (int u = 0; u < kLoads; u++) d ^= v[k][u];
+            }
             if (i < m) st_stream_u64(out + i, d);
         }
     }
@@ -681,7 +730,8 @@ int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint
     void (*fn)(const uint4*, uint64_t, uint64_t, uint64_t, uint64_t*) = nullptr;
 #define QR_PROBE_CASE(KK, VV)                                                            \
     if (k == KK && bytes == 16 * VV && load_bytes == 16) fn = probe_kernel<KK, VV, 16>; \
-    if (k == KK && bytes == 16 * VV && load_bytes == 32 && VV >= 2) fn = probe_kernel<KK, VV, 32>;
+    if (k == KK && bytes == 16 * VV && load_bytes == 32 && VV >= 2) fn = probe_kernel<KK, VV, 32>; \
+    if (k == KK && bytes == 128 && VV == 8 && load_bytes == 128) fn = probe_kernel<KK, 8, 128>;
     QR_PROBE_CASE(1, 1) QR_PROBE_CASE(1, 2) QR_PROBE_CASE(1, 4) QR_PROBE_CASE(1, 8)
     QR_PROBE_CASE(2, 1) QR_PROBE_CASE(2, 2) QR_PROBE_CASE(2, 4) QR_PROBE_CASE(2, 8)
     QR_PROBE_CASE(4, 1) QR_PROBE_CASE(4, 2) QR_PROBE_CASE(4, 4) QR_PROBE_CASE(4, 8)

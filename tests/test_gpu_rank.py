@@ -537,3 +537,34 @@ def test_rank_chain(layout, sigma):
         capi.qr_rank_chain(idx, dev_u64(q0), 0, 0, out)
     with pytest.raises(capi.QRError):
         capi.qr_rank_chain(build(words, n, sigma, 2), dev_u64(q0), 5, 0, out)
+
+
+@pytest.mark.parametrize("nbytes,load_bytes,k", [(32, 16, 4), (32, 32, 4), (64, 32, 2), (128, 32, 1),
+                                                 (128, 128, 1), (128, 128, 2)])
+def test_probe_gather_digests(nbytes, load_bytes, k):
+    """The measurement probe reads whole records: every digest is the XOR of
+    the 64-bit words of one record (also for the quad-cooperative 128-byte
+    reads), and a ragged last tile is written without running past m."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    nrec, m = 1000, 5003
+    words = synth.bits(synth.base_seed(60), nrec * nbytes * 8, 0.5)[: nrec * nbytes // 8]
+    buf = torch.from_numpy(words.view(np.int64)).cuda()
+    out = torch.full((m + 64,), -1, dtype=torch.int64, device="cuda")
+    capi.qr_probe_gather(buf, nrec, nbytes, m, 7, out, k, 256, load_bytes=load_bytes)
+    torch.cuda.synchronize()
+    rec = words.reshape(nrec, nbytes // 8)
+    digests = set(int(x) for x in np.bitwise_xor.reduce(rec, axis=1))
+    got = out.cpu().numpy().view(np.uint64)
+    assert all(int(x) in digests for x in got[:m])
+    assert (got[m:] == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    assert len(set(got[:m].tolist())) > nrec // 2      # many distinct records drawn
+
+
+def test_probe_gather_rejects_quad_mode_on_small_records():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    buf = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    with pytest.raises(RuntimeError):
+        capi.qr_probe_gather(buf, 128, 64, 16, 7, out, 1, 256, load_bytes=128)

@@ -45,7 +45,7 @@ __device__ __forceinline__ uint4 fm_ld(const uint4* p, uint64_t pol) {
 // rank(q, c) over the BWT with the sentinel row counted as code 0.
 template <bool KEEP = false>
 __device__ __forceinline__ uint64_t fm_rank_stored(const FmView& v, uint64_t q, int c, uint64_t pol = 0) {
-    const uint64_t j = div224(q);
+    const uint64_t j = div224_32((uint32_t)q);  // BWT rows < 2^32
     const uint32_t slot = (uint32_t)(q - j * kB4) + 32;
     const uint4* L = v.lines + 4 * j;
     const uint32_t* sp = (const uint32_t*)v.supers + 4 * (j >> 8) + c;
@@ -93,14 +93,14 @@ __device__ __forceinline__ FmLine fm_fetch(const uint4* L, bool upper, uint64_t 
 // count of c = 0 when it lies before the position.
 template <bool KEEP>
 __device__ __forceinline__ void fm_lf_pair(const FmView& v, uint64_t& lo, uint64_t& hi, int c, uint64_t pol) {
-    const uint64_t jl = div224(lo), jh = div224(hi);
-    const uint32_t sl = (uint32_t)(lo - jl * kB4) + 32, sh = (uint32_t)(hi - jh * kB4) + 32;
+    const uint32_t jl = div224_32((uint32_t)lo), jh = div224_32((uint32_t)hi);  // BWT rows < 2^32
+    const uint32_t sl = (uint32_t)lo - jl * (uint32_t)kB4 + 32, sh = (uint32_t)hi - jh * (uint32_t)kB4 + 32;
     const bool ul = sl >= 128, uh = sh >= 128;
     const uint32_t* sp = (const uint32_t*)v.supers + c;
     const uint32_t s_lo = KEEP ? ld_u32_hint(sp + 4 * (jl >> 8), pol) : __ldg(sp + 4 * (jl >> 8));
     const uint32_t s_hi = jl >> 8 == jh >> 8 ? s_lo : (KEEP ? ld_u32_hint(sp + 4 * (jh >> 8), pol) : __ldg(sp + 4 * (jh >> 8)));
-    const FmLine fl = fm_fetch<KEEP>(v.lines + 4 * jl, ul, pol);
-    const FmLine fh = (jl == jh && ul == uh) ? fl : fm_fetch<KEEP>(v.lines + 4 * jh, uh, pol);
+    const FmLine fl = fm_fetch<KEEP>(v.lines + 4 * (uint64_t)jl, ul, pol);
+    const FmLine fh = (jl == jh && ul == uh) ? fl : fm_fetch<KEEP>(v.lines + 4 * (uint64_t)jh, uh, pol);
     uint64_t rl = quad_finish1(s_lo, quad_delta(fl.d0, fl.d1, c), fl.x, sl, c);
     uint64_t rh = quad_finish1(s_hi, quad_delta(fh.d0, fh.d1, c), fh.x, sh, c);
     if (c == 0 && lo > v.dollar) rl -= 1;

@@ -98,6 +98,10 @@ __host__ __device__ __forceinline__ uint64_t div480(uint64_t q) { return mulhi64
 constexpr uint64_t kMagic63 = 0x8208208208208209ull;  // ceil(2^69 / 63)
 __host__ __device__ __forceinline__ uint64_t div1008(uint64_t q) { return mulhi64(q >> 4, kMagic63) >> 5; }
 __host__ __device__ __forceinline__ uint64_t div192(uint64_t q) { return mulhi64(q >> 6, kMagic3) >> 1; }
+// floor(q / 224) for q < 2^32 with one 32-bit high multiply: x = q >> 5 and
+// M = ceil(2^32 / 7) = (2^32 + 3) / 7 give x M / 2^32 = x / 7 + 3x / (7 2^32),
+// which floors to floor(x / 7) while 3x < 2^32 (here x < 2^27).
+__device__ __forceinline__ uint32_t div224_32(uint32_t q) { return __umulhi(q >> 5, 0x24924925u); }
 
 // ---------------------------------------------------------------- bit helpers
 __host__ __device__ __forceinline__ uint64_t low_mask(uint32_t nb) {  // nb in [0, 64]
@@ -107,6 +111,16 @@ __host__ __device__ __forceinline__ uint32_t clamp64(int32_t v) {
     return (uint32_t)(v < 0 ? 0 : (v > 64 ? 64 : v));
 }
 __device__ __forceinline__ uint32_t popc64(uint64_t x) { return (uint32_t)__popcll(x); }
+// Masks of 32-bit words.  low32(s) = the low s bits, s clamped to [0, 32]: the
+// clamping funnel shift stops at 32 and max() handles s < 0.  cmask32 is the
+// same for a compile-time s.  A range [X, M) or [M, X) with a fixed end M is
+// low(X) XOR low(M), one funnel shift per word instead of two masks.
+__device__ __forceinline__ uint32_t low32(int32_t s) {
+    return __funnelshift_lc(0xFFFFFFFFu, 0u, (uint32_t)max(s, 0));
+}
+__host__ __device__ constexpr uint32_t cmask32(int s) { return s <= 0 ? 0u : s >= 32 ? ~0u : (1u << s) - 1u; }
+__host__ __device__ __forceinline__ uint32_t lo32(uint64_t x) { return (uint32_t)x; }
+__host__ __device__ __forceinline__ uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
 
 // ---------------------------------------------------------------- memory
 // 16-byte loads of index lines: read-only path, no L1 allocation (a random
@@ -196,12 +210,11 @@ __device__ __forceinline__ uint64_t birank_finish(uint64_t s, uint64_t w0, const
     const bool upper = p >= kMid2;
     // number of counted bits measured from the start of the selected half
     const int32_t t = upper ? (int32_t)(p - kMid2) : (int32_t)(16 + p);
+    const uint32_t flip = upper ? 0u : ~0u;  // lower half: the bits at and above t
     uint32_t cnt = 0;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        uint64_t m = low_mask(clamp64(t - 64 * k));
-        cnt += popc64(x[k] & (upper ? m : ~m));
-    }
+    for (int k = 0; k < 4; k++)
+        cnt += __popc(lo32(x[k]) & (low32(t - 64 * k) ^ flip)) + __popc(hi32(x[k]) & (low32(t - 64 * k - 32) ^ flip));
     const uint64_t mid = (s << kShift2) + (w0 & 0xFFFFull);
     return upper ? mid + cnt : mid - cnt;
 }
@@ -217,21 +230,33 @@ __device__ __forceinline__ uint64_t quad_delta(uint64_t w0, uint64_t w1, int c) 
     uint64_t w = (c & 2) ? w1 : w0;
     return (w >> (16 * (c & 1))) & 0xFFFFull;
 }
-__device__ __forceinline__ void quad_masks(uint32_t slot, uint64_t m[2]) {
+// Slots 32 i .. 32 i + 31 of the needed half (i = 0..3) are the low (i even)
+// or high (i odd) 32 bits of words x[2 (i / 2)] (~low bits) and x[2 (i / 2) + 1]
+// (~high bits); m = the counted slots among them.
+struct QuadHalf32 {
+    uint32_t nl[4], nh[4], m[4];
+};
+__device__ __forceinline__ QuadHalf32 quad_half32(const uint64_t x[4], uint32_t slot) {
     const bool upper = slot >= 128;
     const int32_t t = upper ? (int32_t)(slot - 128) : (int32_t)slot;
+    const uint32_t flip = upper ? 0u : ~0u;
+    QuadHalf32 h;
 #pragma unroll
-    for (int g = 0; g < 2; g++) {
-        uint64_t lm = low_mask(clamp64(t - 64 * g));
-        m[g] = upper ? lm : ~lm;
+    for (int i = 0; i < 4; i++) {
+        const uint64_t L = x[2 * (i >> 1)], H = x[2 * (i >> 1) + 1];
+        h.nl[i] = (i & 1) ? hi32(L) : lo32(L);
+        h.nh[i] = (i & 1) ? hi32(H) : lo32(H);
+        h.m[i] = low32(t - 32 * i) ^ flip;
     }
+    return h;
 }
 __device__ __forceinline__ uint64_t quad_finish1(uint64_t s_c, uint64_t delta, const uint64_t x[4], uint32_t slot,
                                                  int c) {
-    uint64_t m[2];
-    quad_masks(slot, m);
-    const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
-    uint32_t cnt = popc64((x[0] ^ cl) & (x[1] ^ ch) & m[0]) + popc64((x[2] ^ cl) & (x[3] ^ ch) & m[1]);
+    const QuadHalf32 h = quad_half32(x, slot);
+    const uint32_t cl = 0u - (uint32_t)(c & 1), ch = 0u - (uint32_t)(c >> 1);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) cnt += __popc((h.nl[i] ^ cl) & (h.nh[i] ^ ch) & h.m[i]);
     const uint64_t mid = (s_c << kShift4) + delta;
     return slot >= 128 ? mid + cnt : mid - cnt;
 }
@@ -239,15 +264,14 @@ __device__ __forceinline__ uint64_t quad_finish1(uint64_t s_c, uint64_t delta, c
 // n2 = |H| - n3, n0 = |mask| - n1 - n2 - n3 (L, H = raw low/high bits).
 __device__ __forceinline__ void quad_finish4(const uint32_t s[4], uint64_t w0, uint64_t w1, const uint64_t x[4],
                                              uint32_t slot, uint64_t r[4]) {
-    uint64_t m[2];
-    quad_masks(slot, m);
+    const QuadHalf32 h = quad_half32(x, slot);
     uint32_t nl = 0, nh = 0, n3 = 0;
 #pragma unroll
-    for (int g = 0; g < 2; g++) {
-        uint64_t L = ~x[2 * g] & m[g], H = ~x[2 * g + 1] & m[g];
-        nl += popc64(L);
-        nh += popc64(H);
-        n3 += popc64(L & H);
+    for (int i = 0; i < 4; i++) {
+        const uint32_t L = ~h.nl[i] & h.m[i], H = ~h.nh[i] & h.m[i];
+        nl += __popc(L);
+        nh += __popc(H);
+        n3 += __popc(L & H);
     }
     const bool upper = slot >= 128;
     const uint32_t nm = upper ? slot - 128 : 128 - slot;
@@ -260,90 +284,61 @@ __device__ __forceinline__ void quad_finish4(const uint32_t s[4], uint64_t w0, u
 }
 
 // ---------------------------------------------------------------- sector layout queries
-// Mask of bits [a, b) inside 64-bit word k of a bit string (0 <= a <= b).
-__device__ __forceinline__ uint64_t range_mask(int32_t a, int32_t b, int k) {
-    return low_mask(clamp64(b - 64 * k)) & ~low_mask(clamp64(a - 64 * k));
-}
 // BiRank16x2 half-line: W = the 4 words of the query's 32-byte half, r = data
 // offset inside the half (0..239).  Data offset d sits at half bit 16 + d; the
-// delta counts the ones before data offset 120 of the half.
+// delta counts the ones before data offset 120 of the half (half bit 136).
+// Counted bits: low(16 + r) XOR low(136); the 16 delta bits lie under both.
 __device__ __forceinline__ uint64_t birank_sector_finish(uint64_t s, const u64x4& W, uint32_t r) {
-    const bool upper = r >= kMid2s;
-    const int32_t a = upper ? (int32_t)(16 + kMid2s) : (int32_t)(16 + r);
-    const int32_t b = upper ? (int32_t)(16 + r) : (int32_t)(16 + kMid2s);
-    const uint32_t cnt = popc64(W.a & range_mask(a, b, 0)) + popc64(W.b & range_mask(a, b, 1)) +
-                         popc64(W.c & range_mask(a, b, 2)) + popc64(W.d & range_mask(a, b, 3));
+    const int32_t x = 16 + (int32_t)r;
+    constexpr int kM = 16 + (int)kMid2s;
+    const uint32_t w[8] = {lo32(W.a), hi32(W.a), lo32(W.b), hi32(W.b), lo32(W.c), hi32(W.c), lo32(W.d), hi32(W.d)};
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) cnt += __popc(w[i] & (low32(x - 32 * i) ^ cmask32(kM - 32 * i)));
     const uint64_t mid = (s << kShift2) + (W.a & 0xFFFFull);
-    return upper ? mid + cnt : mid - cnt;
+    return r >= kMid2s ? mid + cnt : mid - cnt;
 }
-// QuadRank sector: chars [a, b) of the half, as masks of group A (chars 0..63,
-// words b/c) and group B (chars 64..95, low/high 32-bit halves of word d).
-__device__ __forceinline__ void quad_sector_range(uint32_t r, int32_t& a, int32_t& b) {
-    const bool upper = r >= kMid4s;
-    a = upper ? (int32_t)kMid4s : (int32_t)r;
-    b = upper ? (int32_t)r : (int32_t)kMid4s;
+// QuadRank sector half: chars 0..31 and 32..63 are the low and high 32 bits
+// of W.b (~low bits) and W.c (~high bits), chars 64..95 the low (~low bits)
+// and high (~high bits) 32 bits of W.d; the deltas count chars before char 48.
+struct QuadSector32 {
+    uint32_t nl[3], nh[3], m[3];
+};
+__device__ __forceinline__ QuadSector32 quad_sector32(const u64x4& W, uint32_t r) {
+    QuadSector32 h;
+    h.nl[0] = lo32(W.b); h.nh[0] = lo32(W.c);
+    h.nl[1] = hi32(W.b); h.nh[1] = hi32(W.c);
+    h.nl[2] = lo32(W.d); h.nh[2] = hi32(W.d);
+#pragma unroll
+    for (int i = 0; i < 3; i++) h.m[i] = low32((int32_t)r - 32 * i) ^ cmask32((int)kMid4s - 32 * i);
+    return h;
 }
 __device__ __forceinline__ uint64_t quad_sector_finish1(uint64_t s_c, const u64x4& W, uint32_t r, int c) {
-    int32_t a, b;
-    quad_sector_range(r, a, b);
-    const uint64_t mA = range_mask(a, b, 0), mB = range_mask(a, b, 1) & 0xFFFFFFFFull;
-    const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
-    const uint32_t cnt = popc64((W.b ^ cl) & (W.c ^ ch) & mA) + popc64((W.d ^ cl) & ((W.d >> 32) ^ ch) & mB);
+    const QuadSector32 h = quad_sector32(W, r);
+    const uint32_t cl = 0u - (uint32_t)(c & 1), ch = 0u - (uint32_t)(c >> 1);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) cnt += __popc((h.nl[i] ^ cl) & (h.nh[i] ^ ch) & h.m[i]);
     const uint64_t mid = (s_c << kShift4) + ((W.a >> (16 * c)) & 0xFFFFull);
     return r >= kMid4s ? mid + cnt : mid - cnt;
 }
 __device__ __forceinline__ void quad_sector_finish4(const uint32_t s[4], const u64x4& W, uint32_t r, uint64_t out[4]) {
-    int32_t a, b;
-    quad_sector_range(r, a, b);
-    const uint64_t mA = range_mask(a, b, 0), mB = range_mask(a, b, 1) & 0xFFFFFFFFull;
-    const uint64_t LA = ~W.b & mA, HA = ~W.c & mA, LB = ~W.d & mB, HB = (~W.d >> 32) & mB;
-    const uint32_t n3 = popc64(LA & HA) + popc64(LB & HB);
-    const uint32_t nl = popc64(LA) + popc64(LB), nh = popc64(HA) + popc64(HB);
-    const uint32_t nm = (uint32_t)(b - a);
-    const uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+    const QuadSector32 h = quad_sector32(W, r);
+    uint32_t nl = 0, nh = 0, n3 = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const uint32_t L = ~h.nl[i] & h.m[i], H = ~h.nh[i] & h.m[i];
+        nl += __popc(L);
+        nh += __popc(H);
+        n3 += __popc(L & H);
+    }
     const bool upper = r >= kMid4s;
+    const uint32_t nm = upper ? r - (uint32_t)kMid4s : (uint32_t)kMid4s - r;
+    const uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         const uint64_t mid = ((uint64_t)s[c] << kShift4) + ((W.a >> (16 * c)) & 0xFFFFull);
         out[c] = upper ? mid + n[c] : mid - n[c];
-    }
-}
-
-// ---------------------------------------------------------------- 128-byte line queries
-// The quad lane `sub` holds sector `sub` (words 4 sub .. 4 sub + 3) of the line.
-// sigma 2: the ones of line bits [a, b) that fall in this sector.
-__device__ __forceinline__ uint32_t line128_count2(const u64x4& W, int sub, int32_t a, int32_t b) {
-    const int32_t o = 256 * sub;
-    return popc64(W.a & range_mask(a - o, b - o, 0)) + popc64(W.b & range_mask(a - o, b - o, 1)) +
-           popc64(W.c & range_mask(a - o, b - o, 2)) + popc64(W.d & range_mask(a - o, b - o, 3));
-}
-// sigma 4: raw low/high bits of chars [a, b) in this sector: its 64-char
-// groups (sector 0: group 0 in words 2, 3 and the 32-char tail in word 1;
-// sector k >= 1: groups 2k - 1 and 2k).  Returns the match count for symbol c,
-// or (with c < 0) fills nl = |L|, nh = |H|, n3 = |L & H|.
-__device__ __forceinline__ void line128_group(uint64_t lo_n, uint64_t hi_n, uint64_t m, int c, uint32_t& cnt,
-                                              uint32_t& nl, uint32_t& nh, uint32_t& n3) {
-    if (c >= 0) {
-        const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
-        cnt += popc64((lo_n ^ cl) & (hi_n ^ ch) & m);
-    } else {
-        const uint64_t L = ~lo_n & m, H = ~hi_n & m;
-        nl += popc64(L);
-        nh += popc64(H);
-        n3 += popc64(L & H);
-    }
-}
-__device__ __forceinline__ void line128_count4(const u64x4& W, int sub, int32_t a, int32_t b, int c, uint32_t& cnt,
-                                               uint32_t& nl, uint32_t& nh, uint32_t& n3) {
-    if (sub == 0) {
-        // tail: chars 448..479 in word 1 (low half ~low bits, high half ~high bits)
-        const uint64_t mt = range_mask(a - 448, b - 448, 0) & 0xFFFFFFFFull;
-        line128_group(W.b & 0xFFFFFFFFull, W.b >> 32, mt, c, cnt, nl, nh, n3);
-        line128_group(W.c, W.d, range_mask(a, b, 0), c, cnt, nl, nh, n3);          // group 0
-    } else {
-        const int g0 = 2 * sub - 1;                                                 // groups g0, g0 + 1
-        line128_group(W.a, W.b, range_mask(a - 64 * g0, b - 64 * g0, 0), c, cnt, nl, nh, n3);
-        line128_group(W.c, W.d, range_mask(a - 64 * g0 - 64, b - 64 * g0 - 64, 0), c, cnt, nl, nh, n3);
     }
 }
 

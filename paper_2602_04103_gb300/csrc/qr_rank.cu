@@ -13,27 +13,10 @@
 #include <cuda_runtime.h>
 
 #include "qr_common.cuh"
+#include "qr_rank.cuh"
 
 namespace qr {
 namespace {
-
-enum Kind { kBiScalar = 0, kBiVec = 1, kQuadScalar = 2, kQuadVec = 3, kQuad4 = 4, kQuadPrefix = 5 };
-
-// rank_4 and prefix_rank both need all four counts of the query's line
-template <int KIND>
-constexpr bool all4() { return KIND == kQuad4 || KIND == kQuadPrefix; }
-
-struct RankArgs {
-    const uint4* __restrict__ lines;
-    const void* __restrict__ supers;
-    uint64_t n;
-    const uint64_t* __restrict__ q;
-    const uint8_t* __restrict__ cvec;
-    int c;
-    uint64_t m;
-    uint64_t* __restrict__ out;
-    uint32_t* status;
-};
 
 template <int K, int LOAD, int KIND>
 __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
@@ -300,182 +283,6 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
     if (bad_flags) atomicOr(a.status, bad_flags);
 }
 
-// 128-byte line layout (QR_LAYOUT_LINE128): the four lanes of a quad answer
-// their four queries together.  For each query r of the quad every lane loads
-// its sector (32 bytes) of query r's line -- four lanes, one instruction, one
-// request, one 128-byte fill per query -- and computes its signed part of the
-// answer: plus or minus the ones (chars) of the query's range in its sector,
-// plus the delta on the lane holding sector 0.  A reduce-scatter over the quad
-// (3 shuffles per value) leaves lane r with the sum for query r.
-__device__ __forceinline__ int32_t quad_reduce_scatter(const int32_t v[4], int sub) {
-    constexpr uint32_t kAll = 0xffffffffu;
-    const bool hi2 = sub & 2, hi1 = sub & 1;
-    // step 1 (lanes sub ^ 2): keep the half of indices that contains sub
-    const int32_t s0 = hi2 ? v[0] : v[2], s1 = hi2 ? v[1] : v[3];
-    const int32_t k0 = hi2 ? v[2] : v[0], k1 = hi2 ? v[3] : v[1];
-    const int32_t a0 = k0 + __shfl_xor_sync(kAll, s0, 2, 4);
-    const int32_t a1 = k1 + __shfl_xor_sync(kAll, s1, 2, 4);
-    // step 2 (lanes sub ^ 1): keep index sub
-    return (hi1 ? a1 : a0) + __shfl_xor_sync(kAll, hi1 ? a0 : a1, 1, 4);
-}
-__device__ __forceinline__ uint64_t quad_reduce_scatter64(const uint64_t v[4], int sub) {
-    constexpr uint32_t kAll = 0xffffffffu;
-    const bool hi2 = sub & 2, hi1 = sub & 1;
-    const uint64_t s0 = hi2 ? v[0] : v[2], s1 = hi2 ? v[1] : v[3];
-    const uint64_t k0 = hi2 ? v[2] : v[0], k1 = hi2 ? v[3] : v[1];
-    const uint64_t a0 = k0 + __shfl_xor_sync(kAll, (unsigned long long)s0, 2, 4);
-    const uint64_t a1 = k1 + __shfl_xor_sync(kAll, (unsigned long long)s1, 2, 4);
-    return (hi1 ? a1 : a0) + __shfl_xor_sync(kAll, (unsigned long long)(hi1 ? a0 : a1), 1, 4);
-}
-
-template <int K, int KIND>
-__global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
-    constexpr bool kQuad = KIND >= kQuadScalar;
-    constexpr uint32_t kAll = 0xffffffffu;
-    const int sub = threadIdx.x & 3;
-    const uint64_t tile = (uint64_t)blockDim.x * K;
-    uint32_t bad_flags = 0;
-    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < a.m; t0 += (uint64_t)gridDim.x * tile) {
-        uint64_t qv[K];
-        int cv[K];
-        bool live[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
-            live[k] = i < a.m;
-            qv[k] = live[k] ? ld_stream_u64(a.q + i) : 0;
-            if (KIND == kBiVec || KIND == kQuadVec) cv[k] = live[k] ? (int)ld_stream_u8(a.cvec + i) : 0;
-            else cv[k] = a.c;
-        }
-        uint32_t pos[K];
-        uint32_t s1[K];
-        uint4 s4[K];
-        u64x4 W[K][4];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const uint64_t qq = qv[k] <= a.n ? qv[k] : 0;
-            uint64_t j;
-            if (!kQuad) {
-                j = div1008(qq);
-                pos[k] = (uint32_t)(qq - j * kB2L);
-                s1[k] = __ldg((const uint32_t*)a.supers + (j >> 5));
-            } else {
-                j = div480(qq);
-                pos[k] = (uint32_t)(qq - j * kB4L);
-                if (all4<KIND>()) s4[k] = __ldg((const uint4*)a.supers + (j >> 6));
-                else s1[k] = __ldg((const uint32_t*)a.supers + 4 * (j >> 6) + (cv[k] & 3));
-            }
-            const unsigned long long L = (unsigned long long)(a.lines + 8 * j);
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const uint4* Lr = (const uint4*)__shfl_sync(kAll, L, r, 4);
-                W[k][r] = ld_line32(Lr + 2 * sub);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const uint64_t i = t0 + threadIdx.x + (uint64_t)k * blockDim.x;
-            uint32_t pr[4];
-#pragma unroll
-            for (int r = 0; r < 4; r++) pr[r] = __shfl_sync(kAll, pos[k], r, 4);
-            uint64_t res[4] = {0, 0, 0, 0};
-            if (!kQuad) {
-                int32_t part[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const bool upper = pr[r] >= kMid2L;
-                    const int32_t lo = upper ? (int32_t)(16 + kMid2L) : (int32_t)(16 + pr[r]);
-                    const int32_t hi = upper ? (int32_t)(16 + pr[r]) : (int32_t)(16 + kMid2L);
-                    const int32_t cnt = (int32_t)line128_count2(W[k][r], sub, lo, hi);
-                    part[r] = (upper ? cnt : -cnt) + (sub == 0 ? (int32_t)(W[k][r].a & 0xFFFFull) : 0);
-                }
-                // delta +- count of the own query: rank(q) - 2^11 s >= 0
-                res[0] = ((uint64_t)s1[k] << kShift2) + (uint64_t)(int64_t)quad_reduce_scatter(part, sub);
-            } else if (!all4<KIND>()) {
-                int32_t part[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const int cr = __shfl_sync(kAll, cv[k], r, 4) & 3;
-                    const bool upper = pr[r] >= kMid4L;
-                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr[r];
-                    const int32_t hi = upper ? (int32_t)pr[r] : (int32_t)kMid4L;
-                    uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
-                    line128_count4(W[k][r], sub, lo, hi, cr, cnt, nl, nh, n3);
-                    part[r] = (upper ? (int32_t)cnt : -(int32_t)cnt) +
-                              (sub == 0 ? (int32_t)((W[k][r].a >> (16 * cr)) & 0xFFFFull) : 0);
-                }
-                res[0] = ((uint64_t)s1[k] << kShift4) + (uint64_t)(int64_t)quad_reduce_scatter(part, sub);
-            } else {
-                int32_t pl[4], ph[4], p3[4];
-                uint64_t pd[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const bool upper = pr[r] >= kMid4L;
-                    const int32_t lo = upper ? (int32_t)kMid4L : (int32_t)pr[r];
-                    const int32_t hi = upper ? (int32_t)pr[r] : (int32_t)kMid4L;
-                    uint32_t cnt = 0, nl = 0, nh = 0, n3 = 0;
-                    line128_count4(W[k][r], sub, lo, hi, -1, cnt, nl, nh, n3);
-                    pl[r] = (int32_t)nl;
-                    ph[r] = (int32_t)nh;
-                    p3[r] = (int32_t)n3;
-                    pd[r] = sub == 0 ? W[k][r].a : 0;  // the four deltas of line r
-                }
-                const uint32_t nl = (uint32_t)quad_reduce_scatter(pl, sub), nh = (uint32_t)quad_reduce_scatter(ph, sub);
-                const uint32_t n3 = (uint32_t)quad_reduce_scatter(p3, sub);
-                const uint64_t d0 = quad_reduce_scatter64(pd, sub);
-                const uint32_t pown = pos[k];
-                const bool upper = pown >= kMid4L;
-                const uint32_t nm = upper ? pown - (uint32_t)kMid4L : (uint32_t)kMid4L - pown;
-                const uint32_t nc[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
-                const uint32_t sv[4] = {s4[k].x, s4[k].y, s4[k].z, s4[k].w};
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const uint64_t mid = ((uint64_t)sv[c] << kShift4) + ((d0 >> (16 * c)) & 0xFFFFull);
-                    res[c] = upper ? mid + nc[c] : mid - nc[c];
-                }
-            }
-            const bool range_bad = qv[k] > a.n;
-            if (!kQuad) {
-                const int c = cv[k];
-                const bool sym_bad = (unsigned)c > 1u;
-                uint64_t out = c == 1 ? res[0] : qv[k] - res[0];
-                if (range_bad || sym_bad) out = ~0ull;
-                if (live[k]) {
-                    st_stream_u64(a.out + i, out);
-                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                }
-            } else if (KIND == kQuadPrefix) {
-                uint64_t sum = 0;
-#pragma unroll
-                for (int c = 0; c < 4; c++) sum += c <= a.c ? res[c] : 0;
-                if (range_bad) sum = ~0ull;
-                if (live[k]) {
-                    st_stream_u64(a.out + i, sum);
-                    bad_flags |= range_bad ? kStatusRange : 0u;
-                }
-            } else if (KIND == kQuad4) {
-                if (range_bad) res[0] = res[1] = res[2] = res[3] = ~0ull;
-                if (live[k]) {
-                    uint64_t* o = a.out + 4 * i;
-                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o), "l"(res[0]), "l"(res[1]) : "memory");
-                    asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(o + 2), "l"(res[2]), "l"(res[3])
-                                 : "memory");
-                    bad_flags |= range_bad ? kStatusRange : 0u;
-                }
-            } else {
-                const bool sym_bad = (unsigned)cv[k] > 3u;
-                uint64_t out = res[0];
-                if (range_bad || sym_bad) out = ~0ull;
-                if (live[k]) {
-                    st_stream_u64(a.out + i, out);
-                    bad_flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                }
-            }
-        }
-    }
-    if (bad_flags) atomicOr(a.status, bad_flags);
-}
-
 // Dependent queries (latency mode): every thread follows one chain, each
 // query position derived from the previous answer, so only one line per chain
 // is ever in flight.  Paper and sector layouts; lines read as 32-byte sectors.
@@ -541,8 +348,6 @@ __global__ void __launch_bounds__(256) rank_chain_kernel(RankArgs a, uint64_t st
 }
 
 // ---------------------------------------------------------------- launch table
-using KernelFn = void (*)(RankArgs);
-
 template <int K, int KIND>
 KernelFn pick_load(int load) {
     switch (load) {
@@ -577,27 +382,8 @@ KernelFn pick_sector(int k) {
     }
 }
 
-template <int KIND>
-KernelFn pick_line(int k) {
-    switch (k) {
-        case 1: return rank_line_kernel<1, KIND>;
-        case 2: return rank_line_kernel<2, KIND>;
-        default: return nullptr;
-    }
-}
-
 KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false) {
-    if (line128) {
-        switch (kind) {
-            case kBiScalar: return pick_line<kBiScalar>(k);
-            case kBiVec: return pick_line<kBiVec>(k);
-            case kQuadScalar: return pick_line<kQuadScalar>(k);
-            case kQuadVec: return pick_line<kQuadVec>(k);
-            case kQuad4: return pick_line<kQuad4>(k);
-            case kQuadPrefix: return pick_line<kQuadPrefix>(k);
-            default: return nullptr;
-        }
-    }
+    if (line128) return pick_line_kind(kind, k);
     if (sector) {
         switch (kind) {
             case kBiScalar: return pick_sector<kBiScalar>(k);

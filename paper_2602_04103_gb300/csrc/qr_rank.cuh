@@ -1,0 +1,34 @@
+// Declarations shared by the batched rank kernels of the three layouts
+// (qr_rank.cu: paper and sector layouts, chains, probe; qr_rank_line.cu:
+// 128-byte line layout).
+#pragma once
+
+#include "qr_common.cuh"
+
+namespace qr {
+
+enum Kind { kBiScalar = 0, kBiVec = 1, kQuadScalar = 2, kQuadVec = 3, kQuad4 = 4, kQuadPrefix = 5 };
+
+// rank_4 and prefix_rank both need all four counts of the query's line
+template <int KIND>
+__host__ __device__ constexpr bool all4() { return KIND == kQuad4 || KIND == kQuadPrefix; }
+
+struct RankArgs {
+    const uint4* __restrict__ lines;
+    const void* __restrict__ supers;
+    uint64_t n;
+    const uint64_t* __restrict__ q;
+    const uint8_t* __restrict__ cvec;
+    int c;
+    uint64_t m;
+    uint64_t* __restrict__ out;
+    uint32_t* status;
+};
+
+using KernelFn = void (*)(RankArgs);
+
+// Kernel of the 128-byte line layout for a query kind and K queries per
+// thread (K = 1 or 2; nullptr otherwise).
+KernelFn pick_line_kind(int kind, int k);
+
+}  // namespace qr

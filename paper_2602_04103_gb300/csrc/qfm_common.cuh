@@ -87,26 +87,50 @@ __device__ __forceinline__ FmLine fm_fetch(const uint4* L, bool upper, uint64_t 
     return f;
 }
 
+// C[c] by selects: indexing the kernel-parameter array with a run-time c
+// would copy the whole argument block to local memory.
+__device__ __forceinline__ uint64_t fm_C(const FmView& v, int c) {
+    return c == 0 ? v.C[0] : c == 1 ? v.C[1] : c == 2 ? v.C[2] : v.C[3];
+}
+
+// rank(q, c) of one interval end from its fetched words, in 32-bit
+// arithmetic (BWT rows < 2^32): 2^13 s + delta +- the masked count.
+__device__ __forceinline__ uint32_t fm_finish32(uint32_t s, const FmLine& f, uint32_t slot, int c) {
+    const uint32_t dw = (c & 2) ? lo32(f.d1) : lo32(f.d0);
+    const uint32_t delta = (dw >> (16 * (c & 1))) & 0xFFFFu;
+    const QuadHalf32 h = quad_half32(f.x, slot);
+    const uint32_t cl = 0u - (uint32_t)(c & 1), ch = 0u - (uint32_t)(c >> 1);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) cnt += __popc((h.nl[i] ^ cl) & (h.nh[i] ^ ch) & h.m[i]);
+    const uint32_t mid = (s << kShift4) + delta;
+    return slot >= 128 ? mid + cnt : mid - cnt;
+}
+
 // LF of both interval ends for symbol c.  When lo and hi fall in the same
 // half-line (the interval is narrow, the usual case after a few steps) the
 // words are fetched once.  The $ row (stored as code 0) is removed from the
 // count of c = 0 when it lies before the position.
 template <bool KEEP>
-__device__ __forceinline__ void fm_lf_pair(const FmView& v, uint64_t& lo, uint64_t& hi, int c, uint64_t pol) {
-    const uint32_t jl = div224_32((uint32_t)lo), jh = div224_32((uint32_t)hi);  // BWT rows < 2^32
-    const uint32_t sl = (uint32_t)lo - jl * (uint32_t)kB4 + 32, sh = (uint32_t)hi - jh * (uint32_t)kB4 + 32;
+__device__ __forceinline__ void fm_lf_pair(const FmView& v, uint32_t& lo, uint32_t& hi, int c, uint64_t pol) {
+    const uint32_t jl = div224_32(lo), jh = div224_32(hi);
+    const uint32_t sl = lo - jl * (uint32_t)kB4 + 32, sh = hi - jh * (uint32_t)kB4 + 32;
     const bool ul = sl >= 128, uh = sh >= 128;
     const uint32_t* sp = (const uint32_t*)v.supers + c;
     const uint32_t s_lo = KEEP ? ld_u32_hint(sp + 4 * (jl >> 8), pol) : __ldg(sp + 4 * (jl >> 8));
     const uint32_t s_hi = jl >> 8 == jh >> 8 ? s_lo : (KEEP ? ld_u32_hint(sp + 4 * (jh >> 8), pol) : __ldg(sp + 4 * (jh >> 8)));
     const FmLine fl = fm_fetch<KEEP>(v.lines + 4 * (uint64_t)jl, ul, pol);
     const FmLine fh = (jl == jh && ul == uh) ? fl : fm_fetch<KEEP>(v.lines + 4 * (uint64_t)jh, uh, pol);
-    uint64_t rl = quad_finish1(s_lo, quad_delta(fl.d0, fl.d1, c), fl.x, sl, c);
-    uint64_t rh = quad_finish1(s_hi, quad_delta(fh.d0, fh.d1, c), fh.x, sh, c);
-    if (c == 0 && lo > v.dollar) rl -= 1;
-    if (c == 0 && hi > v.dollar) rh -= 1;
-    lo = v.C[c] + rl;
-    hi = v.C[c] + rh;
+    uint32_t rl = fm_finish32(s_lo, fl, sl, c);
+    uint32_t rh = fm_finish32(s_hi, fh, sh, c);
+    if (c == 0) {
+        const uint32_t d = (uint32_t)v.dollar;
+        rl -= lo > d ? 1u : 0u;
+        rh -= hi > d ? 1u : 0u;
+    }
+    const uint32_t Cc = (uint32_t)fm_C(v, c);
+    lo = Cc + rl;
+    hi = Cc + rh;
 }
 
 // LF step of one interval end: C[c] + rank(q, c), where the $ row (stored as
@@ -115,7 +139,7 @@ template <bool KEEP = false>
 __device__ __forceinline__ uint64_t fm_lf(const FmView& v, uint64_t q, int c, uint64_t pol = 0) {
     uint64_t r = fm_rank_stored<KEEP>(v, q, c, pol);
     if (c == 0 && q > v.dollar) r -= 1;
-    return v.C[c] + r;
+    return fm_C(v, c) + r;
 }
 
 int fm_view(const qfm_index* idx, FmView* v);

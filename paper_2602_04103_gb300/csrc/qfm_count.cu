@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
     uint64_t pool_next = 0, pool_end = 0;
     bool drained = false;  // the queue has no ids left for this warp
     bool active = false;
-    uint64_t id = 0, lo = 0, hi = 0, start = 0, len = 0;
+    uint64_t id = 0, start = 0, len = 0;
+    uint32_t lo = 0, hi = 0;  // BWT rows < 2^32
     int64_t i = -1;
     bool rc = false;
     uint32_t bad = 0;
@@ -127,10 +128,13 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                     start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
                     const uint64_t end = kKeep ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
                     len = end - start;
-                    if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo, hi, i)) {
+                    uint64_t lo0 = 0, hi0 = 0;
+                    if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo0, hi0, i)) {
                         a.out[id] = 0;  // malformed: offsets out of order or a byte > 3
                         bad |= kStatusBadSym;
                     } else {
+                        lo = (uint32_t)lo0;
+                        hi = (uint32_t)hi0;
                         active = true;
                     }
                 }
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                 }
             }
             if (active && (i < 0 || lo >= hi)) {
-                st_stream_u64(a.out + id, hi > lo ? hi - lo : 0);
+                st_stream_u64(a.out + id, hi > lo ? (uint64_t)(hi - lo) : 0);
                 active = false;
             }
         }

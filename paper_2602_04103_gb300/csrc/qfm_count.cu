@@ -2,9 +2,9 @@
 //
 // qfm_count: one persistent launch.  Every warp takes pattern ids from a
 // device work queue (an atomic counter) in chunks of 64 (32 for small
-// batches), keeps one search
-// per lane, and refills a lane as soon as its search ends, so the lanes of a
-// warp stay busy despite uneven pattern lengths and early mismatches.  This is
+// batches), keeps one search per lane, and refills its idle lanes in groups
+// of at least 8, so the lanes of a warp stay busy despite uneven pattern
+// lengths and early mismatches.  This is
 // the GPU form of the paper's query_batch: a batch of active searches where
 // finished ones are swapped out and the rest take one rank + LF step per pass.
 //
@@ -20,6 +20,12 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kChunkMax = 64;  // pattern ids taken from the queue at once per warp
+// A warp refills its lanes once at least this many are idle (or all are): the
+// refill path costs the whole warp the same instructions for 1 lane as for 8,
+// and a lane finishes a search about every 26 steps, so refilling per finished
+// lane would run it on almost every step.  Measured on the 10^7-pattern
+// workload: 1 -> 2.70, 4 -> 3.13, 8 -> 3.27, 16 -> 2.96 G patterns/s.
+constexpr uint32_t kRefillMin = 8;
 
 struct CountArgs {
     FmView v;
@@ -59,32 +65,44 @@ __device__ __forceinline__ bool fm_start(const FmView& v, const uint8_t* __restr
     return true;
 }
 
-// A lane reads its pattern backwards through a 16-byte register window: one
-// aligned vector load per 16 characters instead of one byte load per step.
-// The window is only loaded when the whole aligned chunk lies inside the
-// pattern buffer [pat, pat + total); otherwise the byte is loaded alone.
+// A lane reads its pattern through a 16-byte register window: one aligned
+// vector load per 16 characters instead of one byte load per step.  `cur` is
+// the byte offset (from pat) of the next char, moving by `dir` per step (-1
+// for a pattern, +1 for its reverse complement); `k` is cur's index in the
+// window, kNoWindow when cur is outside it.  The window is only loaded when
+// the whole aligned chunk lies inside the pattern buffer [pat, pat + total);
+// otherwise the byte is loaded alone.
+constexpr int32_t kNoWindow = 1 << 20;  // stays outside [0, 16) under +-1 steps
+
 struct PatWindow {
     uint4 w;
     uint64_t lo = 0;      // byte offset (from pat) of the window start
     bool valid = false;
+    int32_t k = kNoWindow;
 };
+
+// Index of byte offset p in the current window (at the start of a search).
+__device__ __forceinline__ int32_t window_index(const PatWindow& win, uint64_t p) {
+    return win.valid && p >= win.lo && p - win.lo < 16 ? (int32_t)(p - win.lo) : kNoWindow;
+}
 
 template <bool STREAM>
 __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uint64_t total, uint64_t p, PatWindow& win,
                                             uint64_t pol_first) {
-    if (!win.valid || p < win.lo || p - win.lo >= 16) {
+    if ((uint32_t)win.k >= 16u) {
         const uint64_t a = p - (((uintptr_t)(pat + p)) & 15);  // aligned chunk start, as an offset
         if (a <= p && a + 16 <= total) {
             win.w = STREAM ? ld_line16_hint((const uint4*)(pat + a), pol_first) : __ldg((const uint4*)(pat + a));
             win.lo = a;
             win.valid = true;
+            win.k = (int32_t)(p - a);
         } else {
             return pat[p];
         }
     }
-    const uint32_t k = (uint32_t)(p - win.lo);
+    const uint32_t k = (uint32_t)win.k;
     const uint32_t word = k < 8 ? (k < 4 ? win.w.x : win.w.y) : (k < 12 ? win.w.z : win.w.w);
-    return (int)((word >> (8 * (k & 3))) & 0xFF);
+    return (int)__byte_perm(word, 0u, 0x4440u | (k & 3));
 }
 
 template <int POLICY, int STRANDS>
@@ -102,15 +120,16 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
     uint64_t pool_next = 0, pool_end = 0;
     bool drained = false;  // the queue has no ids left for this warp
     bool active = false;
-    uint64_t id = 0, start = 0, len = 0;
-    uint32_t lo = 0, hi = 0;  // BWT rows < 2^32
+    uint64_t id = 0, cur = 0;  // cur: byte offset of the next char to read
+    uint32_t lo = 0, hi = 0;   // BWT rows < 2^32
     int64_t i = -1;
     bool rc = false;
+    int dir = -1;
     uint32_t bad = 0;
     while (true) {
         // ---- refill lanes whose search ended
         const unsigned need = __ballot_sync(0xffffffffu, !active);
-        if (need && !drained) {
+        if (need && !drained && (__popc(need) >= kRefillMin || need == 0xffffffffu)) {
             const uint32_t cnt = __popc(need);
             const uint32_t r = __popc(need & lt_mask);
             const uint64_t avail = pool_end - pool_next;
@@ -125,9 +144,9 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                 if (id < work) {
                     rc = kBoth && id >= a.m;
                     const uint64_t pid = rc ? id - a.m : id;
-                    start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
+                    const uint64_t start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
                     const uint64_t end = kKeep ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
-                    len = end - start;
+                    const uint64_t len = end - start;
                     uint64_t lo0 = 0, hi0 = 0;
                     if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo0, hi0, i)) {
                         a.out[id] = 0;  // malformed: offsets out of order or a byte > 3
@@ -135,6 +154,10 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                     } else {
                         lo = (uint32_t)lo0;
                         hi = (uint32_t)hi0;
+                        // char i of the searched string: p[i], or 3 - p[len-1-i] for the reverse complement
+                        cur = rc ? start + (len - 1 - (uint64_t)i) : start + (uint64_t)i;
+                        dir = rc ? 1 : -1;
+                        win.k = window_index(win, cur);
                         active = true;
                     }
                 }
@@ -154,9 +177,9 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
         // ---- one LF step for every active lane
         if (active) {
             if (i >= 0 && lo < hi) {
-                // char i of the searched string: p[i], or 3 - p[len-1-i] for the reverse complement
-                const uint64_t pos = rc ? start + (len - 1 - (uint64_t)i) : start + (uint64_t)i;
-                const int raw = pattern_char<kKeep>(a.pat, total, pos, win, pol_first);
+                const int raw = pattern_char<kKeep>(a.pat, total, cur, win, pol_first);
+                cur += dir;
+                win.k += dir;
                 const int c = rc && raw <= 3 ? 3 - raw : raw;
                 if (c > 3) {
                     a.out[id] = 0;

@@ -182,11 +182,12 @@ def bytes_per_query(sigma: int, layout: int, load_mode: int, rank4: bool = False
 
 
 def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
-    """Random 32-byte DRAM requests of one uniform query (superblock entries
-    are L2-resident): the sector layout reads one sector; the paper layout
-    reads one sector below the block middle and two above it (both with
-    whole-line load modes 0 and 2)."""
-    if layout in (1, 2):
+    """Random DRAM requests of one uniform query (superblock entries are
+    L2-resident): the sector and 128-byte line layouts issue one request per
+    query, and so does the paper layout's pair-cooperative load mode 4 (the two
+    lanes' halves of a line in one instruction); load modes 1 and 3 read one
+    sector below the block middle and two above it, modes 0 and 2 two."""
+    if layout in (1, 2) or load_mode == 4:
         return 1.0
     if load_mode in (0, 2):
         return 2.0

@@ -47,4 +47,5 @@ def test_bytes_and_requests_per_query():
     assert bench.requests_per_query(2, 1, 0) == 1.0 and bench.requests_per_query(2, 2, 0) == 1.0
     assert bench.bytes_per_query(2, 2, 0) == 144
     assert bench.requests_per_query(2, 0, 2) == 2.0
+    assert bench.requests_per_query(2, 0, 4) == 1.0 and bench.requests_per_query(4, 0, 4) == 1.0
     assert abs(bench.requests_per_query(2, 0, 3) - (240 / 496 + 2 * 256 / 496)) < 1e-12

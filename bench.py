@@ -356,20 +356,23 @@ def run_extras(args, idx, layout, tuning, dq, out, stream, peak):
                                     "roofline_frac": round(gq * bpq / peak, 4), "layout": layout}
     log(f"[bench] sorted: {gq:.2f} Gq/s")
     # latency mode: dependent queries (each position from the previous answer)
-    if layout in (0, 1):
-        n = 1 << args.log_n
-        q0 = dq[: 1 << 20]
-        o2 = torch.empty((q0.numel(), 2), dtype=torch.int64, device="cuda")
-        steps1 = 2000
-        ms1 = best_ms(lambda: capi.qr_rank_chain(idx, q0[:1], steps1, 1, o2), stream)
-        stepsN = 64
-        msN = best_ms(lambda: capi.qr_rank_chain(idx, q0, stepsN, 1, o2), stream)
-        res["birank_dependent_queries"] = {
-            "one_chain_ns_per_query": round(ms1 * 1e6 / steps1, 1),
-            "chains_2^20_Gq_s": round(q0.numel() * stepsN / (msN * 1e-3) / 1e9, 3),
-            "note": "qr_rank_chain: each query position is derived from the previous answer"}
-        log(f"[bench] dependent: {res['birank_dependent_queries']}")
+    res["birank_dependent_queries"] = dict(dependent_queries(idx, dq, stream), layout=layout,
+                                           note="qr_rank_chain: each query position is derived from the previous answer")
+    log(f"[bench] dependent: {res['birank_dependent_queries']}")
     return res
+
+
+def dependent_queries(idx, dq, stream):
+    """One chain of 2000 dependent queries (latency) and 2^20 chains of 64."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    q0 = dq[: 1 << 20]
+    o2 = torch.empty((q0.numel(), 2), dtype=torch.int64, device="cuda")
+    steps1, stepsN = 2000, 64
+    ms1 = best_ms(lambda: capi.qr_rank_chain(idx, q0[:1], steps1, 1, o2), stream)
+    msN = best_ms(lambda: capi.qr_rank_chain(idx, q0, stepsN, 1, o2), stream)
+    return {"one_chain_ns_per_query": round(ms1 * 1e6 / steps1, 1),
+            "chains_2^20_Gq_s": round(q0.numel() * stepsN / (msN * 1e-3) / 1e9, 3)}
 
 
 def run_layouts(args, stream):
@@ -393,7 +396,8 @@ def run_layouts(args, stream):
         info = capi.qr_info(idx)
         res["birank"][names[layout]] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "tuning": t,
                                         "overhead_pct": round(100 * ((info["bytes_blocks"] + info["bytes_super"]) * 8
-                                                                     / (1 << args.log_n) - 1), 3)}
+                                                                     / (1 << args.log_n) - 1), 3),
+                                        "dependent": dependent_queries(idx, dq, stream)}
         idx.free()
     del dt, dq, o
     torch.cuda.empty_cache()

@@ -176,9 +176,9 @@ int qr_prefix_rank(const qr_index* idx, const uint64_t* q, uint64_t m, int c, ui
  *   r_t = rank(q_t, c),  q_{t+1} = floor(x (n + 1) / 2^64)  with
  *   x = (q_t + r_t) * 0x9E3779B97F4A7C15 mod 2^64,
  * so a chain has one line in flight at a time; chains run in parallel, one
- * per thread.  out2[2k] = q_{steps-1} (the last position queried), out2[2k+1] =
+ * per thread, and every layout reads one line (one request) per query.
+ * out2[2k] = q_{steps-1} (the last position queried), out2[2k+1] =
  * r_{steps-1}.  A start q0[k] > n gives two UINT64_MAX and QR_ERANGE.
- * Layouts: QR_LAYOUT_PAPER and QR_LAYOUT_SECTOR (QR_EINVAL for others).
  * Errors: QR_EINVAL (steps = 0, c out of range, NULL buffers), QR_ECUDA.
  */
 int qr_rank_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out2,

@@ -184,8 +184,6 @@ int qr_rank_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uin
     if (rc) return rc;
     if (steps == 0) return fail(QR_EINVAL, "qr_rank_chain: steps must be >= 1");
     if (c < 0 || c >= idx->sigma) return fail(QR_EINVAL, "qr_rank_chain: symbol out of range");
-    if (idx->layout != QR_LAYOUT_PAPER && idx->layout != QR_LAYOUT_SECTOR)
-        return fail(QR_EINVAL, "qr_rank_chain: paper or sector layout only");
     return launch_chain(idx, q0, nchains, steps, c, out2, (cudaStream_t)stream);
 }
 

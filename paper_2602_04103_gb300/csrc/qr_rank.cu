@@ -285,11 +285,10 @@ __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
 
 // Dependent queries (latency mode): every thread follows one chain, each
 // query position derived from the previous answer, so only one line per chain
-// is ever in flight.  Paper and sector layouts; lines read as 32-byte sectors.
-__device__ __forceinline__ uint64_t chain_next(uint64_t q, uint64_t r, uint64_t n) {
-    return mulhi64((q + r) * 0x9E3779B97F4A7C15ull, n + 1);
-}
-
+// is ever in flight.  Whole warps run the chains of 32 consecutive starts, so
+// that on the paper layout the two lanes of a pair can load the two sectors
+// of both their lines in two instructions: one request (one line fill) per
+// query, as in load mode 4.  The sector layout needs one sector per query.
 template <bool QUAD, bool SECTOR>
 __device__ __forceinline__ uint64_t rank_one(const RankArgs& a, uint64_t q, int c) {
     if (SECTOR) {
@@ -307,43 +306,56 @@ __device__ __forceinline__ uint64_t rank_one(const RankArgs& a, uint64_t q, int 
         const u64x4 W = ld_line32(a.lines + 4 * j + 2 * h);
         return quad_sector_finish1(s, W, d - h * (uint32_t)kHalf4s, c);
     }
+    constexpr uint32_t kAll = 0xffffffffu;
     const uint64_t j = QUAD ? div224(q) : div496(q);
     const uint32_t pos = QUAD ? (uint32_t)(q - j * kB4) + 32 : (uint32_t)(q - j * kB2);
     const bool upper = QUAD ? pos >= 128 : pos >= kMid2;
+    const uint32_t s = QUAD ? __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + c)
+                            : __ldg((const uint32_t*)a.supers + (j >> 7));
     const uint4* L = a.lines + 4 * j;
-    const u64x4 S0 = ld_line32(L);
-    uint64_t x[4] = {S0.a, S0.b, S0.c, S0.d};
-    if (upper) {
-        const u64x4 S1 = ld_line32(L + 2);
-        x[0] = S1.a; x[1] = S1.b; x[2] = S1.c; x[3] = S1.d;
-    }
+    const bool odd = threadIdx.x & 1;
+    const uint4* P = (const uint4*)__shfl_xor_sync(kAll, (unsigned long long)L, 1);
+    const u64x4 r1 = ld_line32((odd ? P : L) + 2 * odd);  // even: own sector 0; odd: partner's sector 1
+    const u64x4 r2 = ld_line32((odd ? L : P) + 2 * odd);  // even: partner's sector 0; odd: own sector 1
+    const u64x4 send = odd ? r1 : r2;
+    u64x4 recv;
+    recv.a = __shfl_xor_sync(kAll, send.a, 1);
+    recv.b = __shfl_xor_sync(kAll, send.b, 1);
+    recv.c = __shfl_xor_sync(kAll, send.c, 1);
+    recv.d = __shfl_xor_sync(kAll, send.d, 1);
+    const u64x4 S0 = odd ? recv : r1, S1 = odd ? r2 : recv;
+    const u64x4 H = upper ? S1 : S0;
+    const uint64_t x[4] = {H.a, H.b, H.c, H.d};
     if (!QUAD) {
-        const uint32_t s = __ldg((const uint32_t*)a.supers + (j >> 7));
-        const uint64_t r1 = birank_finish(s, S0.a, x, pos);
-        return c == 1 ? r1 : q - r1;
+        const uint64_t r = birank_finish(s, S0.a, x, pos);
+        return c == 1 ? r : q - r;
     }
-    const uint32_t s = __ldg((const uint32_t*)a.supers + 4 * (j >> 8) + c);
     return quad_finish1(s, quad_delta(S0.a, S0.b, c), x, pos, c);
 }
 
 // a.q = chain starts (a.m chains), a.out[2k] = final position, a.out[2k+1] =
-// last rank; a.c = symbol; steps per chain in `steps`.
+// last rank; a.c = symbol; steps per chain in `steps`.  A start > n runs a
+// chain from 0 (its lanes still take part in the pair loads) and reports
+// UINT64_MAX.
 template <bool QUAD, bool SECTOR>
 __global__ void __launch_bounds__(256) rank_chain_kernel(RankArgs a, uint64_t steps) {
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < a.m; k += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t q = a.q[k], r = 0;
-        if (q > a.n) {
-            a.out[2 * k] = ~0ull;
-            a.out[2 * k + 1] = ~0ull;
-            atomicOr(a.status, kStatusRange);
-            continue;
-        }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); base < a.m; base += stride) {
+        const uint64_t k = base + lane;
+        const bool live = k < a.m;
+        uint64_t q = live ? a.q[k] : 0, r = 0;
+        const bool bad = q > a.n;
+        if (bad) q = 0;
         for (uint64_t t = 0; t < steps; t++) {
             r = rank_one<QUAD, SECTOR>(a, q, a.c);
             if (t + 1 < steps) q = chain_next(q, r, a.n);
         }
-        a.out[2 * k] = q;
-        a.out[2 * k + 1] = r;
+        if (live) {
+            a.out[2 * k] = bad ? ~0ull : q;
+            a.out[2 * k + 1] = bad ? ~0ull : r;
+            if (bad) atomicOr(a.status, kStatusRange);
+        }
     }
 }
 
@@ -500,8 +512,10 @@ int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint
     if (nchains == 0) return QR_OK;
     RankArgs a{idx->lines, idx->supers, idx->n, q0, nullptr, c, nchains, out, idx->status};
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR;
-    void (*fn)(RankArgs, uint64_t) = quad ? (sector ? rank_chain_kernel<true, true> : rank_chain_kernel<true, false>)
-                                          : (sector ? rank_chain_kernel<false, true> : rank_chain_kernel<false, false>);
+    ChainFn fn = idx->layout == QR_LAYOUT_LINE128
+                     ? pick_chain_line(quad)
+                     : quad ? (sector ? rank_chain_kernel<true, true> : rank_chain_kernel<true, false>)
+                            : (sector ? rank_chain_kernel<false, true> : rank_chain_kernel<false, false>);
     uint64_t grid = (nchains + 255) / 256;
     const uint64_t cap = (uint64_t)device_props().sms * 8;
     if (grid > cap) grid = cap;

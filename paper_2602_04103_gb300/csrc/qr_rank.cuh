@@ -31,4 +31,16 @@ using KernelFn = void (*)(RankArgs);
 // thread (K = 1 or 2; nullptr otherwise).
 KernelFn pick_line_kind(int kind, int k);
 
+// Dependent queries: the next position of a chain from the last position and
+// its rank, uniform in [0, n]: floor(x (n + 1) / 2^64) with
+// x = (q + r) * 0x9E3779B97F4A7C15 mod 2^64.
+__device__ __forceinline__ uint64_t chain_next(uint64_t q, uint64_t r, uint64_t n) {
+    return mulhi64((q + r) * 0x9E3779B97F4A7C15ull, n + 1);
+}
+
+// Chain kernel of the 128-byte line layout; a.q = starts, a.m = chains,
+// a.out = 2 values per chain (see qr_rank_chain).  Launched with whole warps.
+using ChainFn = void (*)(RankArgs, uint64_t);
+ChainFn pick_chain_line(bool quad);
+
 }  // namespace qr

@@ -263,6 +263,71 @@ __global__ void __launch_bounds__(512) rank_line_kernel(RankArgs a) {
     if (bad_flags) atomicOr(a.status, bad_flags);
 }
 
+// Dependent queries on 128-byte lines: the quad's four chains take their
+// steps together, each step reading the four lines quad-cooperatively.
+template <bool QUAD>
+__device__ __forceinline__ uint64_t rank_line_one(const RankArgs& a, const BiLane& bl, const QuadLane& ql, int sub,
+                                                  uint64_t q, int c) {
+    uint64_t j;
+    uint32_t pos, s;
+    if (!QUAD) {
+        j = div1008(q);
+        pos = (uint32_t)(q - j * kB2L);
+        s = __ldg((const uint32_t*)a.supers + (j >> 5));
+    } else {
+        j = div480(q);
+        pos = (uint32_t)(q - j * kB4L);
+        s = __ldg((const uint32_t*)a.supers + 4 * (j >> 6) + c);
+    }
+    const unsigned long long L = (unsigned long long)(a.lines + 8 * j);
+    u64x4 W[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) W[r] = ld_line32((const uint4*)__shfl_sync(kAll, L, r, 4) + 2 * sub);
+    int32_t part[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const uint32_t pr = __shfl_sync(kAll, pos, r, 4);
+        if (!QUAD) {
+            const int32_t cnt = (int32_t)bi_part(bl, W[r], 16 + (int32_t)pr);
+            part[r] = (pr >= kMid2L ? cnt : -cnt) + (sub == 0 ? (int32_t)(W[r].a & 0xFFFFull) : 0);
+        } else {
+            const int32_t cnt = (int32_t)quad_part1(ql, W[r], (int32_t)pr, c);
+            part[r] = (pr >= kMid4L ? cnt : -cnt) + (sub == 0 ? (int32_t)((W[r].a >> (16 * c)) & 0xFFFFull) : 0);
+        }
+    }
+    const int64_t sum = quad_reduce_scatter(part, sub);
+    if (!QUAD) {
+        const uint64_t r1 = ((uint64_t)s << kShift2) + (uint64_t)sum;
+        return c == 1 ? r1 : q - r1;
+    }
+    return ((uint64_t)s << kShift4) + (uint64_t)sum;
+}
+
+template <bool QUAD>
+__global__ void __launch_bounds__(256) rank_chain_line_kernel(RankArgs a, uint64_t steps) {
+    const int sub = threadIdx.x & 3;
+    const BiLane bl = bi_lane(sub);
+    const QuadLane ql = quad_lane(sub);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); base < a.m; base += stride) {
+        const uint64_t k = base + lane;
+        const bool live = k < a.m;
+        uint64_t q = live ? a.q[k] : 0, r = 0;
+        const bool bad = q > a.n;
+        if (bad) q = 0;
+        for (uint64_t t = 0; t < steps; t++) {
+            r = rank_line_one<QUAD>(a, bl, ql, sub, q, a.c);
+            if (t + 1 < steps) q = chain_next(q, r, a.n);
+        }
+        if (live) {
+            a.out[2 * k] = bad ? ~0ull : q;
+            a.out[2 * k + 1] = bad ? ~0ull : r;
+            if (bad) atomicOr(a.status, kStatusRange);
+        }
+    }
+}
+
 template <int KIND>
 KernelFn pick_line(int k) {
     switch (k) {
@@ -273,6 +338,8 @@ KernelFn pick_line(int k) {
 }
 
 }  // namespace
+
+ChainFn pick_chain_line(bool quad) { return quad ? rank_chain_line_kernel<true> : rank_chain_line_kernel<false>; }
 
 KernelFn pick_line_kind(int kind, int k) {
     switch (kind) {

@@ -517,7 +517,7 @@ def test_prefix_rank(layout):
         capi.qr_prefix_rank(build(synth.bits(1, 100, 0.5), 100, 2), dq, 0, out)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("sigma", [2, 4])
 def test_rank_chain(layout, sigma):
     import torch
@@ -535,8 +535,11 @@ def test_rank_chain(layout, sigma):
     assert capi.qr_status(idx) == capi.QR_ERANGE
     with pytest.raises(capi.QRError):
         capi.qr_rank_chain(idx, dev_u64(q0), 0, 0, out)
-    with pytest.raises(capi.QRError):
-        capi.qr_rank_chain(build(words, n, sigma, 2), dev_u64(q0), 5, 0, out)
+    # one chain alone (a warp with a single live lane) and a single step
+    one = torch.empty((1, 2), dtype=torch.int64, device="cuda")
+    capi.qr_rank_chain(idx, dev_u64(q0[:1]), 1, sigma - 1, one)
+    want, _ = oracle.rank_chain(words, n, sigma, q0[:1], 1, sigma - 1)
+    assert np.array_equal(host_u64(one).reshape(-1, 2), want)
 
 
 @pytest.mark.parametrize("nbytes,load_bytes,k", [(32, 16, 4), (32, 32, 4), (64, 32, 2), (128, 32, 1),

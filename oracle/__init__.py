@@ -1,8 +1,9 @@
 """ORACLE -- test infrastructure, not part of the product.
 
 ctypes wrapper over ``oracle.c``: plain CPU definitions of rank, rank_4, the
-suffix array / BWT of T$ and pattern occurrence counts (QuadRank paper,
-Sec. 1 rank definition, Sec. 4 rank_4, App. D count-only FM-index).
+suffix array / BWT of T$, pattern occurrence counts and positions (QuadRank
+paper, Sec. 1 rank definition, Sec. 4 rank_4, App. D count-only FM-index,
+Sec. 6 locate).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path
@@ -60,6 +61,8 @@ def _load():
         lib.or_count_sa.argtypes = [_P, u64, _P, _P, _P, u64, _P]
         lib.or_count_brute_batch.argtypes = [_P, u64, _P, _P, u64, _P]
         lib.or_revcomp.argtypes = [_P, u64, _P]
+        lib.or_locate_brute.argtypes = [_P, u64, _P, _P, u64, _P, _P]
+        lib.or_locate_sa.argtypes = [_P, u64, _P, _P, _P, u64, _P, _P]
         lib.or_rank_chain.argtypes = [_P, u64, C.c_int, _P, u64, u64, C.c_int, _P]
         lib.or_fm_steps.restype = u64
         lib.or_fm_steps.argtypes = [_P, u64, _P, _P, _P, u64, u64, _P]
@@ -173,6 +176,32 @@ def count_sa(codes: np.ndarray, sa: np.ndarray, pats: np.ndarray, offsets: np.nd
     out = np.empty(m, dtype=np.uint64)
     _load().or_count_sa(_p(codes), codes.size, _p(sa), _p(pats) if pats.size else None, _p(offsets), m, _p(out))
     return out
+
+
+def locate_brute(codes: np.ndarray, pats: np.ndarray, offsets: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(occ[m+1], positions): every start position of each pattern, increasing."""
+    codes, pats, offsets = _u8(codes), _u8(pats), _u64(offsets)
+    m = offsets.size - 1
+    occ = np.empty(m + 1, dtype=np.uint64)
+    lib = _load()
+    pp = _p(pats) if pats.size else None
+    lib.or_locate_brute(_p(codes), codes.size, pp, _p(offsets), m, _p(occ), None)
+    pos = np.empty(max(int(occ[m]), 1), dtype=np.uint64)
+    lib.or_locate_brute(_p(codes), codes.size, pp, _p(offsets), m, _p(occ), _p(pos))
+    return occ, pos[: int(occ[m])]
+
+
+def locate_sa(codes: np.ndarray, sa: np.ndarray, pats: np.ndarray, offsets: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(occ[m+1], positions): each pattern's positions in suffix-array row order."""
+    codes, sa, pats, offsets = _u8(codes), _u64(sa), _u8(pats), _u64(offsets)
+    m = offsets.size - 1
+    occ = np.empty(m + 1, dtype=np.uint64)
+    lib = _load()
+    pp = _p(pats) if pats.size else None
+    lib.or_locate_sa(_p(codes), codes.size, _p(sa), pp, _p(offsets), m, _p(occ), None)
+    pos = np.empty(max(int(occ[m]), 1), dtype=np.uint64)
+    lib.or_locate_sa(_p(codes), codes.size, _p(sa), pp, _p(offsets), m, _p(occ), _p(pos))
+    return occ, pos[: int(occ[m])]
 
 
 def fm_steps(codes: np.ndarray, sa: np.ndarray, pats: np.ndarray, offsets: np.ndarray,

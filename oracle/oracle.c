@@ -14,6 +14,10 @@
  *   count(P)   = number of positions i with T[i .. i+|P|) = P, the quantity a
  *                count-only FM-index returns (App. D); equivalently the size
  *                of the suffix-array interval of suffixes of T$ prefixed by P.
+ *   locate(P)  = those positions i themselves (the locate query the paper
+ *                names as an extension of its FM-index, Sec. 6); listed in
+ *                increasing order, or in suffix-array order (the order of the
+ *                rows of P's interval).
  * The suffix array is the textbook one: all suffixes of T$ sorted, with the
  * sentinel $ smaller than every symbol (App. D stores one sentinel).
  *
@@ -250,6 +254,45 @@ int or_count_sa(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint
         or_sa_interval(codes, n, sa, pats + offsets[k], offsets[k + 1] - offsets[k], &lo, &hi);
         out[k] = hi - lo;
     }
+    return OR_OK;
+}
+
+/* locate for m patterns by direct comparison: occ[k] = index of pattern k's
+ * first position in pos (occ[m] = total), positions in increasing order.  With
+ * pos == NULL only occ is filled. */
+int or_locate_brute(const uint8_t* codes, uint64_t n, const uint8_t* pats, const uint64_t* offsets, uint64_t m,
+                    uint64_t* occ, uint64_t* pos) {
+    uint64_t e = 0;
+    for (uint64_t k = 0; k < m; k++) {
+        const uint8_t* p = pats + offsets[k];
+        const uint64_t len = offsets[k + 1] - offsets[k];
+        occ[k] = e;
+        for (uint64_t i = 0; i + len <= n; i++) {  /* the empty pattern: every i in 0..n */
+            if (len == 0 || memcmp(codes + i, p, len) == 0) {
+                if (pos) pos[e] = i;
+                e++;
+            }
+        }
+    }
+    occ[m] = e;
+    return OR_OK;
+}
+
+/* locate for m patterns via the suffix array: the positions sa[lo .. hi) of
+ * each pattern's interval, in row order. */
+int or_locate_sa(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uint8_t* pats,
+                 const uint64_t* offsets, uint64_t m, uint64_t* occ, uint64_t* pos) {
+    uint64_t e = 0;
+    for (uint64_t k = 0; k < m; k++) {
+        uint64_t lo, hi;
+        or_sa_interval(codes, n, sa, pats + offsets[k], offsets[k + 1] - offsets[k], &lo, &hi);
+        occ[k] = e;
+        for (uint64_t r = lo; r < hi; r++) {
+            if (pos) pos[e] = sa[r];
+            e++;
+        }
+    }
+    occ[m] = e;
     return OR_OK;
 }
 

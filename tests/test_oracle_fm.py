@@ -172,3 +172,64 @@ def test_revcomp_pins():
             st = int(rng.integers(0, t.size - L))
             q = t[st:st + L]
             assert oracle.count_brute(t, oracle.revcomp(q)) == oracle.count_brute(t_rc, q)
+
+
+def test_locate_golden(golden):
+    g = golden("fm_gattaca.txt")
+    t = enc(g["text"])
+    sa = oracle.suffix_array(t)
+    for line in g["locate"]:
+        f = line.split()
+        p = "" if f[0] == "EMPTY" else f[0]
+        want = [int(x) for x in f[1:]]
+        pats, off = enc(p), np.array([0, len(p)], dtype=np.uint64)
+        occ, pos = oracle.locate_sa(t, sa, pats, off)
+        assert pos.tolist() == want and occ.tolist() == [0, len(want)]
+        occ, pos = oracle.locate_brute(t, pats, off)
+        assert pos.tolist() == sorted(want)
+
+
+def test_locate_matches_regex_and_suffix_order():
+    rng = np.random.default_rng(31)
+    t = synth.fm_text(41, 3000, repeat_cover=0.3, len_min=50, len_max=300, sub_rate=0.02)
+    s = dec(t)
+    sa = oracle.suffix_array(t)
+    plist = [b""]
+    for L in [1, 2, 3, 5, 8, 13, 40]:
+        for _ in range(12):
+            if rng.random() < 0.7:
+                st = int(rng.integers(0, t.size - L))
+                plist.append(t[st:st + L].tobytes())
+            else:
+                plist.append(rng.integers(0, 4, L).astype(np.uint8).tobytes())
+    off = np.concatenate([[0], np.cumsum([len(p) for p in plist])]).astype(np.uint64)
+    pats = np.frombuffer(b"".join(plist), dtype=np.uint8)
+    occ_b, pos_b = oracle.locate_brute(t, pats, off)
+    occ_s, pos_s = oracle.locate_sa(t, sa, pats, off)
+    assert np.array_equal(occ_b, occ_s)
+    assert np.array_equal(np.diff(occ_b), oracle.count_brute_batch(t, pats, off))
+    for k, p in enumerate(plist):
+        a, b = int(occ_b[k]), int(occ_b[k + 1])
+        want = list(range(t.size + 1)) if not p else [mt.start() for mt in re.finditer("(?=" + dec(p) + ")", s)]
+        assert pos_b[a:b].tolist() == want
+        # suffix-array order: the suffixes at consecutive positions increase ('$' < 'A' in ASCII)
+        got = pos_s[a:b].tolist()
+        assert sorted(got) == want
+        suf = [s[i:] + "$" for i in got]
+        assert suf == sorted(suf)
+
+
+def test_locate_closed_forms():
+    n = 200
+    a = np.zeros(n, dtype=np.uint8)                       # A^n: A^k starts at 0..n-k
+    sa = oracle.suffix_array(a)
+    for k in [1, 5, 200, 201]:
+        pats, off = np.zeros(k, np.uint8), np.array([0, k], np.uint64)
+        want = list(range(n - k + 1)) if k <= n else []
+        assert oracle.locate_brute(a, pats, off)[1].tolist() == want
+        # rows of A^k are the suffixes A^j$ for j >= k, shortest first: positions n-k, n-k-1, ..., 0
+        assert oracle.locate_sa(a, sa, pats, off)[1].tolist() == want[::-1]
+    r = 50
+    per = np.tile(np.arange(4, dtype=np.uint8), r)       # (ACGT)^r: CG starts at 1, 5, 9, ...
+    occ, pos = oracle.locate_brute(per, enc("CG"), np.array([0, 2], np.uint64))
+    assert pos.tolist() == list(range(1, 4 * r, 4))

@@ -27,6 +27,9 @@ typedef struct {
     uint64_t bytes_table;  /* bytes of the 8-mer table                        */
     int32_t kmer;          /* prefix-table length (8)                          */
     int32_t has_sa;        /* 1 if the suffix array was kept (QFM_KEEP_SA)     */
+    int32_t sa_sample;     /* suffix-array sampling factor for locate (0: none) */
+    int32_t reserved;
+    uint64_t bytes_locate; /* bytes of the locate structures (marks + samples) */
 } qfm_info_t;
 
 #define QFM_KEEP_SA 1      /* qfm_build flag: keep the suffix array for export */
@@ -45,6 +48,49 @@ typedef struct {
  * Errors: QR_EINVAL (n, null, a byte > 3), QR_ENOMEM, QR_ECUDA.
  */
 int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, void* stream, qfm_index** out);
+
+/*
+ * qfm_build_ex -- qfm_build that also prepares locate queries when
+ * sa_sample > 0.  The paper names locate as the natural extension of its
+ * FM-index (Sec. 6) without a method; its comparison indexes sample the
+ * suffix array (App. D results, "suffix-array sampling factor").  Here the
+ * rows whose suffix starts at a multiple of sa_sample are marked in a
+ * BiRank16 index over the n + 1 rows (Sec. 3), and the sampled positions
+ * divided by sa_sample are stored in row order: (n + 1) / 8 * 1.033 +
+ * 4 (n / sa_sample + 1) bytes on top of the count index.  A locate then takes
+ * at most sa_sample - 1 LF steps per occurrence.
+ *   sa_sample  0 (count only) or >= 1.  Other arguments as qfm_build.
+ * Errors: as qfm_build.
+ */
+int qfm_build_ex(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, uint32_t sa_sample, void* stream,
+                 qfm_index** out);
+
+/*
+ * qfm_locate -- the text positions of every occurrence of m patterns.
+ * Paper: Sec. 6 (locate, future work); the search is App. D's backward search
+ * (the persistent count kernel, which also records each pattern's
+ * suffix-array interval [lo, hi)); each row of an interval is then walked by
+ * LF steps to a sampled row: SA[r] = sa_sample * sample + steps.
+ *   patterns, offsets  as qfm_count.
+ *   occ        device array of m + 1 uint64: occ[k] = index in `positions` of
+ *              pattern k's first occurrence, occ[m] = total (the exclusive
+ *              scan of the counts).
+ *   positions  device array of `capacity` uint64, or NULL to only compute occ
+ *              and *total.  positions[occ[k] .. occ[k+1]) are pattern k's
+ *              occurrences in suffix-array row order (the order of the
+ *              suffixes starting there; sort them for text order).
+ *   total      host pointer: receives the number of occurrences.
+ * The call synchronises the stream once (to read the total) and returns with
+ * the locate kernel queued on it.  Patterns with a byte > 3 or out-of-order
+ * offsets have no occurrences and set QR_EBADSYM in the status; the empty
+ * pattern occurs at 0..n.  Scratch: 16 m + 16 bytes from the stream-ordered
+ * pool of the stream.
+ * Errors: QR_EINVAL (NULL arguments, index built without a sampling factor),
+ * QR_ERANGE (positions given and total > capacity: occ and *total are valid,
+ * positions untouched), QR_ENOMEM, QR_ECUDA.
+ */
+int qfm_locate(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, uint64_t* occ,
+               uint64_t* positions, uint64_t capacity, uint64_t* total, void* stream);
 
 /*
  * qfm_count -- out[k] = number of occurrences of pattern k in T, for k < m,

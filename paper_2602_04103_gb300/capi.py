@@ -234,10 +234,13 @@ def qr_probe_gather(buf, nrec: int, nbytes: int, m: int, seed: int, out, queries
 # ---------------------------------------------------------------- QuadFm (include/quadfm.h)
 class qfm_info_t(C.Structure):
     _fields_ = [("n", u64), ("dollar_row", u64), ("C", u64 * 5), ("bytes_rank", u64), ("bytes_table", u64),
-                ("kmer", C.c_int32), ("has_sa", C.c_int32)]
+                ("kmer", C.c_int32), ("has_sa", C.c_int32), ("sa_sample", C.c_int32), ("reserved", C.c_int32),
+                ("bytes_locate", u64)]
 
 
 _sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
+_sig("qfm_build_ex", [vp, u64, i32, i32, C.c_uint32, vp, C.POINTER(vp)])
+_sig("qfm_locate", [vp, vp, vp, u64, vp, vp, u64, C.POINTER(u64), vp])
 _sig("qfm_count", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_ex", [vp, vp, vp, u64, vp, i32, vp])
 _sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
@@ -259,12 +262,24 @@ class QFMIndex(QRIndex):
             self.handle = None
 
 
-def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None) -> QFMIndex:
+def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None, sa_sample: int = 0) -> QFMIndex:
     on_dev = int(hasattr(codes, "is_cuda") and codes.is_cuda)
     n = numel(codes) if n is None else n
     h = vp()
-    _check(lib.qfm_build(ptr(codes), n, on_dev, flags, stream_ptr(stream), C.byref(h)), "qfm_build")
+    _check(lib.qfm_build_ex(ptr(codes), n, on_dev, flags, sa_sample, stream_ptr(stream), C.byref(h)), "qfm_build")
     return QFMIndex(h.value)
+
+
+def qfm_locate(idx: QFMIndex, patterns, offsets, occ, positions=None, stream=None) -> int:
+    """occ (m + 1 device uint64) and, with `positions`, every occurrence's text
+    position; returns the total.  QRError with code QR_ERANGE when `positions`
+    is too small (occ is valid then)."""
+    m = numel(offsets) - 1
+    total = u64(0)
+    cap = numel(positions) if positions is not None else 0
+    _check(lib.qfm_locate(idx, ptr(patterns), ptr(offsets), m, ptr(occ), ptr(positions), cap, C.byref(total),
+                          stream_ptr(stream)), "qfm_locate")
+    return int(total.value)
 
 
 def qfm_count(idx: QFMIndex, patterns, offsets, out, stream=None) -> None:

@@ -4,8 +4,7 @@
 
 namespace qr {
 int build_fm(qfm_index* idx, const uint8_t* d_t, uint64_t n, cudaStream_t s);
-int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s, int strands);
+int build_locate(qfm_index* idx, uint32_t sa_sample, cudaStream_t s);
 int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                           cudaStream_t s);
 
@@ -28,6 +27,8 @@ void free_fm(qfm_index* idx) {
     if (idx->table) cudaFree(idx->table);
     if (idx->sa) cudaFree(idx->sa);
     if (idx->status) cudaFree(idx->status);
+    if (idx->marks) qr_free(idx->marks);
+    if (idx->samples) cudaFree(idx->samples);
     delete idx;
 }
 }  // namespace
@@ -38,6 +39,11 @@ using namespace qr;
 extern "C" {
 
 int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, void* stream, qfm_index** out) {
+    return qfm_build_ex(codes, n, codes_on_device, flags, 0, stream, out);
+}
+
+int qfm_build_ex(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, uint32_t sa_sample, void* stream,
+                 qfm_index** out) {
     if (!out) return fail(QR_EINVAL, "qfm_build: out is NULL");
     *out = nullptr;
     if (n == 0 || n >= 0xFFFFFFFFull - 1) return fail(QR_EINVAL, "qfm_build: need 1 <= n < 2^32 - 1");
@@ -63,6 +69,7 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
         return cuda_fail(e, "qfm_build: allocation");
     }
     int rc = build_fm(idx, d_t, n, s);
+    if (rc == QR_OK && sa_sample > 0) rc = build_locate(idx, sa_sample, s);
     if (tmp) cudaFreeAsync(tmp, s);
     cudaError_t se = cudaStreamSynchronize(s);
     if (rc == QR_OK && se != cudaSuccess) rc = cuda_fail(se, "qfm_build: synchronize");
@@ -122,6 +129,9 @@ int qfm_info(const qfm_index* idx, qfm_info_t* info) {
     info->bytes_table = kQfmTable * 16;
     info->kmer = kQfmK;
     info->has_sa = idx->sa != nullptr;
+    info->sa_sample = (int32_t)idx->sa_sample;
+    info->reserved = 0;
+    info->bytes_locate = idx->marks ? 64 * idx->marks->nblocks + 4 * idx->marks->nsuper + 4 * idx->nsamples : 0;
     return QR_OK;
 }
 

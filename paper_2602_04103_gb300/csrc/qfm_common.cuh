@@ -18,6 +18,13 @@ struct qfm_index {
     uint32_t* status = nullptr;
     int device = 0;
     int policy = 1;            // kFmPolicy* of the persistent count kernel
+    // locate (built when a sampling factor is given): rows whose suffix
+    // starts at a multiple of sa_sample are marked in a BiRank16 index over
+    // the n + 1 rows; samples[rank1(marks, row)] = SA[row] / sa_sample.
+    uint32_t sa_sample = 0;
+    qr_index* marks = nullptr;
+    uint32_t* samples = nullptr;
+    uint64_t nsamples = 0;
 };
 
 namespace qr {
@@ -142,6 +149,50 @@ __device__ __forceinline__ uint64_t fm_lf(const FmView& v, uint64_t q, int c, ui
     return fm_C(v, c) + r;
 }
 
+// BWT char of row r and LF(r) = C[c] + rank(r, c) - [c = 0 and r > dollar],
+// both from the half-line that holds r (its slot lies in the counted half).
+// The $ row is never passed (it is marked for locate: its suffix starts at 0).
+__device__ __forceinline__ uint32_t fm_lf_row(const FmView& v, uint32_t r) {
+    const uint32_t j = div224_32(r);
+    const uint32_t slot = r - j * (uint32_t)kB4 + 32;
+    const bool upper = slot >= 128;
+    const uint4 s4 = __ldg(v.supers + (j >> 8));
+    const FmLine f = fm_fetch<false>(v.lines + 4 * (uint64_t)j, upper, 0);
+    const uint32_t t = slot - (upper ? 128u : 0u), g = t >> 6, b = t & 63;
+    const uint64_t nl = g ? f.x[2] : f.x[0], nh = g ? f.x[3] : f.x[1];
+    const int c = (int)(((~nl >> b) & 1) | (((~nh >> b) & 1) << 1));
+    const uint32_t sc = c == 0 ? s4.x : c == 1 ? s4.y : c == 2 ? s4.z : s4.w;
+    uint32_t rk = fm_finish32(sc, f, slot, c);
+    if (c == 0 && r > (uint32_t)v.dollar) rk -= 1;
+    return (uint32_t)fm_C(v, c) + rk;
+}
+
+// rank1(q) over a BiRank16 index in the paper layout (64-byte lines).
+__device__ __forceinline__ uint64_t birank_rank_paper(const uint4* __restrict__ lines, const uint32_t* __restrict__ supers,
+                                                      uint64_t q) {
+    const uint64_t j = div496(q);
+    const uint32_t p = (uint32_t)(q - j * kB2);
+    const bool upper = p >= kMid2;
+    const uint4* L = lines + 4 * j;
+    const u64x4 S = ld_line32(L + (upper ? 2 : 0));
+    const uint64_t w0 = upper ? __ldg((const unsigned long long*)L) : S.a;
+    const uint64_t x[4] = {S.a, S.b, S.c, S.d};
+    return birank_finish(__ldg(supers + (j >> 7)), w0, x, p);
+}
+
+// Bit q of the bit string held in a BiRank16 paper-layout index.
+__device__ __forceinline__ bool birank_bit_paper(const uint4* __restrict__ lines, uint64_t q) {
+    const uint64_t j = div496(q);
+    const uint32_t b = (uint32_t)(q - j * kB2) + 16;  // line bit of data offset q - jB
+    const uint64_t w = __ldg((const unsigned long long*)lines + 8 * j + (b >> 6));
+    return (w >> (b & 63)) & 1;
+}
+
 int fm_view(const qfm_index* idx, FmView* v);
+
+// The persistent count launch (qfm_count.cu): counts of m patterns (2 m with
+// strands = 2) into out; with lohi, also each search's final interval.
+int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
+                 unsigned long long* queue, cudaStream_t s, int strands, uint64_t* lohi = nullptr);
 
 }  // namespace qr

@@ -37,6 +37,7 @@ struct CountArgs {
     uint32_t* status;
     uint32_t chunk;  // ids per queue grab: 64, or 32 when the batch is too small to fill the grid
     uint32_t strands;  // 1: patterns as given; 2: also their reverse complements (ids m..2m-1)
+    uint64_t* lohi;    // optional: the final interval [lo, hi) of search id at lohi[2 id], lohi[2 id + 1]
 };
 
 // Start a search: the interval of the last 8 chars from the table (or the full
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                     uint64_t lo0 = 0, hi0 = 0;
                     if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo0, hi0, i)) {
                         a.out[id] = 0;  // malformed: offsets out of order or a byte > 3
+                        if (a.lohi) a.lohi[2 * id] = a.lohi[2 * id + 1] = 0;
                         bad |= kStatusBadSym;
                     } else {
                         lo = (uint32_t)lo0;
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                 const int c = rc && raw <= 3 ? 3 - raw : raw;
                 if (c > 3) {
                     a.out[id] = 0;
+                    if (a.lohi) a.lohi[2 * id] = a.lohi[2 * id + 1] = 0;
                     bad |= kStatusBadSym;
                     active = false;
                 } else {
@@ -192,6 +195,10 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
             }
             if (active && (i < 0 || lo >= hi)) {
                 st_stream_u64(a.out + id, hi > lo ? (uint64_t)(hi - lo) : 0);
+                if (a.lohi) {
+                    a.lohi[2 * id] = lo;
+                    a.lohi[2 * id + 1] = hi > lo ? hi : lo;
+                }
                 active = false;
             }
         }
@@ -266,9 +273,10 @@ unsigned persistent_grid(int policy, int strands = 1) {
 }  // namespace
 
 int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s, int strands) {
+                 unsigned long long* queue, cudaStream_t s, int strands, uint64_t* lohi) {
     CountArgs a;
     a.strands = strands == 2 ? 2 : 1;
+    a.lohi = lohi;
     fm_view(idx, &a.v);
     a.pat = pat;
     a.off = off;
@@ -306,6 +314,7 @@ int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off,
     a->queue = queue;
     a->status = idx->status;
     a->strands = 1;
+    a->lohi = nullptr;
     uint64_t grid = persistent_grid(idx->policy);
     a->chunk = m >= grid * (kThreads / 32) * kChunkMax * 2 ? kChunkMax : 32;
     const uint64_t warps_needed = (m + a->chunk - 1) / a->chunk;
@@ -332,6 +341,7 @@ int launch_count_stepwise(qfm_index* idx, const uint8_t* pat, const uint64_t* of
     a.out = out;
     a.queue = nullptr;
     a.status = idx->status;
+    a.lohi = nullptr;
     StepState* st = nullptr;
     unsigned long long* mx = nullptr;
     QR_CUDA_TRY(cudaMallocAsync((void**)&st, m * sizeof(StepState), s));

@@ -25,8 +25,6 @@
 #include "quadfm.h"
 
 namespace qr {
-int launch_count(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
-                 unsigned long long* queue, cudaStream_t s, int strands);
 int count_kernel_params(qfm_index* idx, const uint8_t* pat, const uint64_t* off, uint64_t m, uint64_t* out,
                         unsigned long long* queue, void* args, size_t args_bytes, cudaKernelNodeParams* p,
                         void** param_slot);

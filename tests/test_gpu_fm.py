@@ -167,3 +167,95 @@ def test_counts_both_strands():
     assert capi.qfm_status(idx) == 0
     with pytest.raises(capi.QRError):
         capi.qfm_count_ex(idx, dev_u8(pats), dev_u64(off), out, 4)
+
+
+def locate(idx, pats, off):
+    """(occ, positions) from qfm_locate: a size query first, then the walk."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    m = off.size - 1
+    occ = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    dp = dev_u8(pats if pats.size else np.zeros(1, np.uint8))
+    doff = dev_u64(off)
+    total = capi.qfm_locate(idx, dp, doff, occ)
+    pos = torch.empty(max(total, 1), dtype=torch.int64, device="cuda")
+    assert capi.qfm_locate(idx, dp, doff, occ, pos) == total
+    return host_u64(occ), host_u64(pos)[:total]
+
+
+def plist_batch(t, rng, lengths, per_len, sampled_frac=0.7, extra=()):
+    plist = [np.frombuffer(p, np.uint8) for p in extra]
+    for L in lengths:
+        for _ in range(per_len):
+            if rng.random() < sampled_frac and L <= t.size:
+                st = int(rng.integers(0, t.size - L + 1))
+                plist.append(t[st:st + L])
+            else:
+                plist.append(rng.integers(0, 4, L).astype(np.uint8))
+    off = np.concatenate([[0], np.cumsum([p.size for p in plist])]).astype(np.uint64)
+    pats = np.concatenate(plist).astype(np.uint8) if off[-1] else np.zeros(0, np.uint8)
+    return pats, off
+
+
+@pytest.mark.parametrize("sample", [1, 3, 32])
+def test_locate_mid_size(sample):
+    """Every occurrence's position, in suffix-array row order, equals the
+    oracle's SA[lo .. hi) for each pattern (and, sorted, the brute-force scan)."""
+    from paper_2602_04103_gb300 import capi
+    t = synth.fm_text(71, 20000, repeat_cover=0.3, len_min=100, len_max=2000, sub_rate=0.02)
+    idx = capi.qfm_build(dev_u8(t), t.size, 0, sa_sample=sample)
+    info = capi.qfm_info(idx)
+    assert info["sa_sample"] == sample and info["bytes_locate"] > 0 and not info["has_sa"]
+    rng = np.random.default_rng(72)
+    pats, off = plist_batch(t, rng, [1, 2, 3, 5, 8, 9, 12, 20, 60], 25, extra=[b""])
+    occ, pos = locate(idx, pats, off)
+    sa = oracle.suffix_array(t)
+    want_occ, want_pos = oracle.locate_sa(t, sa, pats, off)
+    assert np.array_equal(occ, want_occ)
+    assert np.array_equal(pos, want_pos)
+    bocc, bpos = oracle.locate_brute(t, pats, off)
+    for k in range(off.size - 1):
+        a, b = int(occ[k]), int(occ[k + 1])
+        assert np.array_equal(np.sort(pos[a:b]), bpos[a:b]), k
+    assert capi.qfm_status(idx) == 0
+
+
+@pytest.mark.parametrize("sample", [1, 2, 5, 100])
+def test_locate_tiny_exhaustive(sample):
+    """Every pattern of length 1..4 over small texts, including a sampling
+    factor above the text length (only the whole-text suffix is sampled)."""
+    from paper_2602_04103_gb300 import capi
+    for n, seed in [(1, 1), (9, 2), (40, 3)]:
+        t = np.random.default_rng(seed).integers(0, 4, n).astype(np.uint8)
+        idx = capi.qfm_build(dev_u8(t), n, 0, sa_sample=sample)
+        plist = [np.array(p, np.uint8) for L in range(0, 5) for p in itertools.product(range(4), repeat=L)]
+        off = np.concatenate([[0], np.cumsum([p.size for p in plist])]).astype(np.uint64)
+        pats = np.concatenate(plist).astype(np.uint8)
+        occ, pos = locate(idx, pats, off)
+        want_occ, want_pos = oracle.locate_sa(t, oracle.suffix_array(t), pats, off)
+        assert np.array_equal(occ, want_occ) and np.array_equal(pos, want_pos), (n, sample)
+
+
+def test_locate_capacity_and_errors():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    t = synth.fm_text(73, 5000, repeat_cover=0.2, len_min=100, len_max=500, sub_rate=0.02)
+    idx = capi.qfm_build(dev_u8(t), t.size, 0, sa_sample=16)
+    pats, off = plist_batch(t, np.random.default_rng(74), [1, 4], 10, sampled_frac=1.0)
+    bad = np.concatenate([pats, [7, 0, 1]]).astype(np.uint8)      # one pattern with a byte > 3
+    boff = np.concatenate([off, [off[-1] + 3]]).astype(np.uint64)
+    occ = torch.empty(boff.size, dtype=torch.int64, device="cuda")
+    total = capi.qfm_locate(idx, dev_u8(bad), dev_u64(boff), occ)
+    assert total == int(oracle.locate_brute(t, pats, off)[0][-1])
+    assert host_u64(occ)[-1] == host_u64(occ)[-2] == total         # the malformed pattern has none
+    assert capi.qfm_status(idx) == capi.QR_EBADSYM
+    small = torch.empty(total - 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(capi.QRError) as ei:
+        capi.qfm_locate(idx, dev_u8(bad), dev_u64(boff), occ, small)
+    assert ei.value.code == capi.QR_ERANGE
+    assert host_u64(occ)[-1] == total                              # occ is valid after QR_ERANGE
+    plain = capi.qfm_build(dev_u8(t), t.size, 0)                   # built without a sampling factor
+    with pytest.raises(capi.QRError):
+        capi.qfm_locate(plain, dev_u8(pats), dev_u64(off), occ)
+    empty_occ = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    assert capi.qfm_locate(idx, dev_u8(pats), dev_u64(off[:1]), empty_occ) == 0 and host_u64(empty_occ)[0] == 0

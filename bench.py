@@ -529,6 +529,25 @@ def run_fm(args, stream):
         res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_config4.json)"
     log(f"[bench] qfm: persistent {m / ms_p / 1e3:.1f} M/s, stepwise {m / ms_s / 1e3:.1f} M/s")
     fidx.free()
+    # locate: the same text indexed with suffix-array sampling factor 32; every
+    # occurrence of all 10^7 patterns (count with intervals, scan, LF walks)
+    sample = 32
+    lidx = capi.qfm_build(dt, text.size, 0, sa_sample=sample)
+    linfo = capi.qfm_info(lidx)
+    occ = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    total = capi.qfm_locate(lidx, dp, doff, occ)
+    pos = torch.empty(max(total, 1), dtype=torch.int64, device="cuda")
+    ms_l = best_ms(lambda: capi.qfm_locate(lidx, dp, doff, occ, pos), stream)
+    assert torch.equal(occ[1:] - occ[:-1], ref)
+    assert capi.qfm_status(lidx) == 0
+    res["qfm_locate"] = {"patterns_per_s": round(m / (ms_l * 1e-3)), "occurrences": total,
+                         "occurrences_per_s": round(total / (ms_l * 1e-3)), "ms": round(ms_l, 3),
+                         "ms_beyond_count": round(ms_l - ms_p, 3), "sa_sample": sample,
+                         "bytes_locate": linfo["bytes_locate"],
+                         "note": "whole qfm_locate call: count with intervals, scan, total read-back, one "
+                                 "thread per occurrence walking at most 31 LF steps"}
+    log(f"[bench] qfm locate: {total} occurrences in {ms_l:.3f} ms")
+    lidx.free()
     return res
 
 

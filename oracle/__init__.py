@@ -1,9 +1,10 @@
 """ORACLE -- test infrastructure, not part of the product.
 
 ctypes wrapper over ``oracle.c``: plain CPU definitions of rank, rank_4, the
-suffix array / BWT of T$, pattern occurrence counts and positions (QuadRank
-paper, Sec. 1 rank definition, Sec. 4 rank_4, App. D count-only FM-index,
-Sec. 6 locate).
+suffix array / BWT of T$, pattern occurrence counts (exact and with up to k
+substitutions) and positions (QuadRank paper, Sec. 1 rank definition and
+approximate matching, Sec. 4 rank_4, App. D count-only FM-index, Sec. 6
+locate).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path
@@ -62,6 +63,9 @@ def _load():
         lib.or_count_brute_batch.argtypes = [_P, u64, _P, _P, u64, _P]
         lib.or_revcomp.argtypes = [_P, u64, _P]
         lib.or_locate_brute.argtypes = [_P, u64, _P, _P, u64, _P, _P]
+        lib.or_count_approx.restype = u64
+        lib.or_count_approx.argtypes = [_P, u64, _P, u64, C.c_uint32]
+        lib.or_count_approx_batch.argtypes = [_P, u64, _P, _P, u64, C.c_uint32, _P]
         lib.or_locate_sa.argtypes = [_P, u64, _P, _P, _P, u64, _P, _P]
         lib.or_rank_chain.argtypes = [_P, u64, C.c_int, _P, u64, u64, C.c_int, _P]
         lib.or_fm_steps.restype = u64
@@ -175,6 +179,20 @@ def count_sa(codes: np.ndarray, sa: np.ndarray, pats: np.ndarray, offsets: np.nd
     m = offsets.size - 1
     out = np.empty(m, dtype=np.uint64)
     _load().or_count_sa(_p(codes), codes.size, _p(sa), _p(pats) if pats.size else None, _p(offsets), m, _p(out))
+    return out
+
+
+def count_approx(codes: np.ndarray, p: np.ndarray, k: int) -> int:
+    """Positions where P matches with at most k substitutions."""
+    codes, p = _u8(codes), _u8(p)
+    return int(_load().or_count_approx(_p(codes), codes.size, _p(p) if p.size else None, p.size, k))
+
+
+def count_approx_batch(codes: np.ndarray, pats: np.ndarray, offsets: np.ndarray, k: int) -> np.ndarray:
+    codes, pats, offsets = _u8(codes), _u8(pats), _u64(offsets)
+    m = offsets.size - 1
+    out = np.empty(m, dtype=np.uint64)
+    _load().or_count_approx_batch(_p(codes), codes.size, _p(pats) if pats.size else None, _p(offsets), m, k, _p(out))
     return out
 
 

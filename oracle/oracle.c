@@ -14,6 +14,9 @@
  *   count(P)   = number of positions i with T[i .. i+|P|) = P, the quantity a
  *                count-only FM-index returns (App. D); equivalently the size
  *                of the suffix-array interval of suffixes of T$ prefixed by P.
+ *   count_k(P) = number of positions i with T[i .. i+|P|) differing from P in
+ *                at most k characters (approximate matching with
+ *                substitutions, the use of rank_4 the paper names, Sec. 1).
  *   locate(P)  = those positions i themselves (the locate query the paper
  *                names as an extension of its FM-index, Sec. 6); listed in
  *                increasing order, or in suffix-array order (the order of the
@@ -293,6 +296,27 @@ int or_locate_sa(const uint8_t* codes, uint64_t n, const uint64_t* sa, const uin
         }
     }
     occ[m] = e;
+    return OR_OK;
+}
+
+/* count_k(P) by comparing P with every length-|P| window of T (the empty
+ * pattern: every position 0..n, as count). */
+uint64_t or_count_approx(const uint8_t* codes, uint64_t n, const uint8_t* p, uint64_t len, uint32_t k) {
+    if (len == 0) return n + 1;
+    if (len > n) return 0;
+    uint64_t cnt = 0;
+    for (uint64_t i = 0; i + len <= n; i++) {
+        uint32_t d = 0;
+        for (uint64_t j = 0; j < len && d <= k; j++) d += codes[i + j] != p[j];
+        if (d <= k) cnt++;
+    }
+    return cnt;
+}
+
+int or_count_approx_batch(const uint8_t* codes, uint64_t n, const uint8_t* pats, const uint64_t* offsets,
+                          uint64_t m, uint32_t k, uint64_t* out) {
+    for (uint64_t j = 0; j < m; j++)
+        out[j] = or_count_approx(codes, n, pats + offsets[j], offsets[j + 1] - offsets[j], k);
     return OR_OK;
 }
 

@@ -233,3 +233,50 @@ def test_locate_closed_forms():
     per = np.tile(np.arange(4, dtype=np.uint8), r)       # (ACGT)^r: CG starts at 1, 5, 9, ...
     occ, pos = oracle.locate_brute(per, enc("CG"), np.array([0, 2], np.uint64))
     assert pos.tolist() == list(range(1, 4 * r, 4))
+
+
+def numpy_hamming_counts(t, p, k):
+    """Independent re-statement: sliding windows compared with numpy."""
+    L = p.size
+    if L == 0:
+        return t.size + 1
+    if L > t.size:
+        return 0
+    win = np.lib.stride_tricks.sliding_window_view(t, L)
+    return int(((win != p).sum(axis=1) <= k).sum())
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_count_approx_matches_numpy(k):
+    rng = np.random.default_rng(50 + k)
+    t = synth.fm_text(51, 3000, repeat_cover=0.3, len_min=50, len_max=300, sub_rate=0.02)
+    for L in [0, 1, 2, 4, 7, 12, 30]:
+        for _ in range(8):
+            if L and rng.random() < 0.6:
+                st = int(rng.integers(0, t.size - L))
+                p = t[st:st + L].copy()
+                for j in rng.integers(0, L, int(rng.integers(0, 3))):
+                    p[j] = (p[j] + 1 + rng.integers(0, 3)) % 4     # substitute 0..2 chars
+            else:
+                p = rng.integers(0, 4, L).astype(np.uint8)
+            assert oracle.count_approx(t, p, k) == numpy_hamming_counts(t, p, k), (L, k)
+
+
+def test_count_approx_special_cases():
+    rng = np.random.default_rng(60)
+    t = rng.integers(0, 4, 2000).astype(np.uint8)
+    for L in [1, 5, 11]:
+        p = t[100:100 + L]
+        assert oracle.count_approx(t, p, 0) == oracle.count_brute(t, p)      # k = 0 is exact count
+        assert oracle.count_approx(t, p, L) == t.size - L + 1               # k >= |P|: every window
+        cs = [oracle.count_approx(t, p, k) for k in range(4)]
+        assert cs == sorted(cs)                                            # monotone in k
+    n = 300
+    a = np.zeros(n, dtype=np.uint8)                                        # A^n
+    p = np.array([0] * 9 + [1], np.uint8)                                  # A^9 C: one substitution from every window
+    assert [oracle.count_approx(a, p, k) for k in range(3)] == [0, n - 9, n - 9]
+    p = np.array([2, 3, 1], np.uint8)                                      # GTC: three substitutions
+    assert [oracle.count_approx(a, p, k) for k in range(4)] == [0, 0, 0, n - 2]
+    pats = np.array([0, 0, 1, 2, 0, 3], np.uint8)                          # AA, empty, CG (2 substitutions), AT
+    off = np.array([0, 2, 2, 4, 6], np.uint64)
+    assert oracle.count_approx_batch(a, pats, off, 1).tolist() == [n - 1, n + 1, 0, n - 1]

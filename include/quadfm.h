@@ -50,6 +50,26 @@ typedef struct {
 int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, void* stream, qfm_index** out);
 
 /*
+ * qfm_count_approx -- out[k] = number of text positions where pattern k
+ * matches with at most max_mismatches substituted characters (Hamming
+ * distance), by backtracking backward search.  Paper: Sec. 1 (rank_4, all
+ * four ranks of a position at once, serves approximate pattern matching in an
+ * FM-index), Sec. 4 rank_4, App. D backward search.  Every node of the search
+ * extends its interval by all four characters from rank_4 of both ends; the
+ * prefix table is not used (a mismatch may fall in the last 8 characters).
+ * One persistent launch with a device work queue, as qfm_count.
+ *   max_mismatches  0..3 (0 gives the exact counts of qfm_count).
+ * The empty pattern counts n + 1.  A pattern holding a byte > 3 anywhere, or
+ * with out-of-order offsets, yields 0 and sets QR_EBADSYM.  The work grows
+ * with the number of strings within the distance that occur in T: about
+ * (3 |P|)^k nodes near the start of a search over a random text.
+ * Errors: QR_EINVAL (NULL with m > 0, max_mismatches out of range),
+ * QR_ENOMEM, QR_ECUDA.
+ */
+int qfm_count_approx(qfm_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t m, int max_mismatches,
+                     uint64_t* out, void* stream);
+
+/*
  * qfm_build_ex -- qfm_build that also prepares locate queries when
  * sa_sample > 0.  The paper names locate as the natural extension of its
  * FM-index (Sec. 6) without a method; its comparison indexes sample the

@@ -241,6 +241,7 @@ class qfm_info_t(C.Structure):
 _sig("qfm_build", [vp, u64, i32, i32, vp, C.POINTER(vp)])
 _sig("qfm_build_ex", [vp, u64, i32, i32, C.c_uint32, vp, C.POINTER(vp)])
 _sig("qfm_locate", [vp, vp, vp, u64, vp, vp, u64, C.POINTER(u64), vp])
+_sig("qfm_count_approx", [vp, vp, vp, u64, i32, vp, vp])
 _sig("qfm_count", [vp, vp, vp, u64, vp, vp])
 _sig("qfm_count_ex", [vp, vp, vp, u64, vp, i32, vp])
 _sig("qfm_count_stepwise", [vp, vp, vp, u64, vp, vp])
@@ -268,6 +269,13 @@ def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None, sa_sampl
     h = vp()
     _check(lib.qfm_build_ex(ptr(codes), n, on_dev, flags, sa_sample, stream_ptr(stream), C.byref(h)), "qfm_build")
     return QFMIndex(h.value)
+
+
+def qfm_count_approx(idx: QFMIndex, patterns, offsets, k: int, out, stream=None) -> None:
+    """out[j] = occurrences of pattern j with at most k substitutions (k <= 3)."""
+    m = numel(offsets) - 1
+    _check(lib.qfm_count_approx(idx, ptr(patterns), ptr(offsets), m, k, ptr(out), stream_ptr(stream)),
+           "qfm_count_approx")
 
 
 def qfm_locate(idx: QFMIndex, patterns, offsets, occ, positions=None, stream=None) -> int:

@@ -259,3 +259,57 @@ def test_locate_capacity_and_errors():
         capi.qfm_locate(plain, dev_u8(pats), dev_u64(off), occ)
     empty_occ = torch.full((1,), 7, dtype=torch.int64, device="cuda")
     assert capi.qfm_locate(idx, dev_u8(pats), dev_u64(off[:1]), empty_occ) == 0 and host_u64(empty_occ)[0] == 0
+
+
+def approx_counts(idx, pats, off, k):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    m = off.size - 1
+    out = torch.full((max(m, 1),), -1, dtype=torch.int64, device="cuda")
+    capi.qfm_count_approx(idx, dev_u8(pats if pats.size else np.zeros(1, np.uint8)), dev_u64(off), k, out)
+    return host_u64(out)[:m]
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_count_approx_mid_size(k):
+    """Counts with at most k substitutions equal the oracle's window scan;
+    k = 0 equals the exact counts."""
+    t = synth.fm_text(81, 5000, repeat_cover=0.3, len_min=100, len_max=800, sub_rate=0.02)
+    idx = build_fm(t, keep_sa=False)
+    rng = np.random.default_rng(82 + k)
+    lengths = [1, 2, 3, 6, 9, 14, 25] if k < 3 else [1, 2, 4, 7, 10]
+    pats, off = plist_batch(t, rng, lengths, 12, extra=[b""])
+    got = approx_counts(idx, pats, off, k)
+    assert np.array_equal(got, oracle.count_approx_batch(t, pats, off, k))
+    if k == 0:
+        assert np.array_equal(got, counts(idx, pats, off))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_count_approx_tiny_exhaustive(k):
+    for n, seed in [(1, 5), (12, 6), (50, 7)]:
+        t = np.random.default_rng(seed).integers(0, 4, n).astype(np.uint8)
+        idx = build_fm(t, keep_sa=False)
+        plist = [np.array(p, np.uint8) for L in range(0, 5) for p in itertools.product(range(4), repeat=L)]
+        off = np.concatenate([[0], np.cumsum([p.size for p in plist])]).astype(np.uint64)
+        pats = np.concatenate(plist).astype(np.uint8)
+        assert np.array_equal(approx_counts(idx, pats, off, k), oracle.count_approx_batch(t, pats, off, k)), n
+
+
+def test_count_approx_repetitive_and_errors():
+    from paper_2602_04103_gb300 import capi
+    t = np.array([0] * 200 + [1] + [0] * 99, np.uint8)          # A^200 C A^99
+    idx = build_fm(t, keep_sa=False)
+    plist = [np.zeros(10, np.uint8), np.array([0] * 9 + [1], np.uint8), np.array([2, 3, 1], np.uint8),
+             np.array([0, 1, 7], np.uint8)]                     # the last one is malformed
+    off = np.concatenate([[0], np.cumsum([p.size for p in plist])]).astype(np.uint64)
+    pats = np.concatenate(plist).astype(np.uint8)
+    for k in range(4):
+        got = approx_counts(idx, pats, off, k)
+        want = oracle.count_approx_batch(t, pats[:int(off[3])], off[:4], k)
+        assert np.array_equal(got[:3], want) and got[3] == 0, k
+    assert capi.qfm_status(idx) == capi.QR_EBADSYM
+    import torch
+    out = torch.empty(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(capi.QRError):
+        capi.qfm_count_approx(idx, dev_u8(pats), dev_u64(off), 4, out)

@@ -548,6 +548,22 @@ def run_fm(args, stream):
                                  "thread per occurrence walking at most 31 LF steps"}
     log(f"[bench] qfm locate: {total} occurrences in {ms_l:.3f} ms")
     lidx.free()
+    # approximate counts (at most k substitutions) on leading subsets of the
+    # same patterns: rank_4 of both interval ends at every search node
+    fidx = capi.qfm_build(dt, text.size)
+    res["qfm_count_approx"] = {}
+    for k, mk in [(0, 10 ** 6), (1, 10 ** 6), (2, 10 ** 5)]:
+        ok = doff[: mk + 1]
+        oa = torch.empty(mk, dtype=torch.int64, device="cuda")
+        ms_a = best_ms(lambda: capi.qfm_count_approx(fidx, dp, ok, k, oa), stream)
+        if k == 0:
+            assert torch.equal(oa, ref[:mk])
+        res["qfm_count_approx"][f"k={k}"] = {"patterns": mk, "patterns_per_s": round(mk / (ms_a * 1e-3)),
+                                             "ms": round(ms_a, 3),
+                                             "mean_count": round(float(oa.double().mean()), 3)}
+        log(f"[bench] qfm approx k={k}: {mk / ms_a / 1e3:.2f} M patterns/s")
+    assert capi.qfm_status(fidx) == 0
+    fidx.free()
     return res
 
 

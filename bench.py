@@ -195,6 +195,51 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
     return lower + 2 * (1 - lower)
 
 
+REGION_TILE, REGION_COUNT = 8192, 256
+REGION_PASSES = ("sort", "rank", "unsort")
+REGION_KERNELS = {"sort": "region_sort<VEC>", "rank": "region_rank<SECTOR,QUAD,VEC>", "unsort": "region_unsort"}
+
+
+def region_pass_bytes(m: int, index_bytes: int, per_query_c: bool = False) -> dict:
+    """Algorithmic DRAM bytes per query of each region-batching pass: the
+    query word (and symbol) read once, 8-byte work items written and read
+    back, the 4-byte segment entries (one per region and tile of 8192
+    queries), and the index read once per batch in the rank pass."""
+    seg = 4.0 * REGION_COUNT / REGION_TILE
+    sym = 1.0 if per_query_c else 0.0
+    return {"sort": 8 + sym + 8 + seg, "rank": 8 + 8 + seg + index_bytes / m, "unsort": 8 + 8}
+
+
+def region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream, per_query_c=False):
+    """Roofline of the dominant pass of a region-batched step, from CUDA
+    events the library records between its passes (median of 3 calls)."""
+    from paper_2602_04103_gb300 import capi
+    capi.qr_region_timing(idx, True)
+    runs = []
+    for _ in range(3):
+        step()
+        runs.append(capi.qr_region_timing(idx, True, read=True))
+    capi.qr_region_timing(idx, False)
+    pass_ms = {p: float(np.median([r[i] for r in runs])) for i, p in enumerate(REGION_PASSES)}
+    pbytes = region_pass_bytes(m, index_bytes, per_query_c)
+    dom = max(pass_ms, key=pass_ms.get)
+    achieved = pbytes[dom] * m / (pass_ms[dom] * 1e-3) / 1e9
+    tr = traffic_record(f"birank_region_{dom}")
+    step_bytes = sum(pbytes.values())
+    launches = len(REGION_PASSES)
+    return ({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+             "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
+             "peak_kind": f"of {peak_kind} (copy bandwidth)", "kernel": REGION_KERNELS[dom],
+             "algorithmic_bytes_per_query": round(pbytes[dom], 3), "queries_per_launch": m,
+             "passes_ms": {p: round(v, 4) for p, v in pass_ms.items()},
+             "passes_bytes_per_query": {p: round(v, 3) for p, v in pbytes.items()},
+             "passes_frac": {p: round(pbytes[p] * m / (pass_ms[p] * 1e-3) / 1e9 / peak, 4) for p in REGION_PASSES},
+             "step_bytes_per_query": round(step_bytes, 3),
+             "step_achieved_GB_s": round(step_bytes * m / (avg_ms * 1e-3) / 1e9, 1),
+             "step_frac": round(step_bytes * m / (avg_ms * 1e-3) / 1e9 / peak, 4),
+             "launches_per_step": launches}, launches)
+
+
 # ---------------------------------------------------------------- our arm
 def probe_ceiling(stream, quad128: bool = False):
     """Random 32-byte loads over a 4 GiB buffer: the GPU's random request rate.
@@ -250,6 +295,8 @@ def run_ours(args):
     log(f"[bench] tuned build: layout {layout}, {tuning} ({t_tune:.1f}s)")
     out = torch.empty_like(dq)
     ceiling = ceil128 if layout == 2 else ceil32
+    plan = capi.qr_rank_plan(idx, m)
+    log(f"[bench] batch path: {'region batching' if plan == capi.QR_BATCH_REGIONS else 'direct kernels'}")
 
     def step():
         capi.qr_rank(idx, dq, 1, out)
@@ -264,23 +311,41 @@ def run_ours(args):
     assert capi.qr_status(idx) == 0
     value = ws * m * args.steps / (total_ms * 1e-3) / 1e9
     avg_ms = float(np.mean(per))
-    bpq = bytes_per_query(2, layout, tuning["load_mode"])
-    rpq = requests_per_query(2, layout, tuning["load_mode"])
-    achieved = bpq * m / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    kname = {0: "birank_rank_paper", 1: "birank_rank_sector", 2: "birank_rank_line128"}[layout]
-    tr = traffic_record(kname)
-    gq_launch = m / (avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
-                "peak_kind": f"of {peak_kind} (copy bandwidth)",
-                "kernel": {0: "rank_kernel<K,LOAD,kBiScalar>", 1: "rank_sector_kernel<K,kBiScalar>",
-                           2: "rank_line_kernel<K,kBiScalar>"}[layout],
-                "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
-                "random_requests_per_query": round(rpq, 3),
-                "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
-                "random_request_ceiling_kind": "128-byte quad-cooperative" if layout == 2 else "32-byte",
-                "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4) if ceiling == ceiling else None}
+    index_bytes = info["bytes_blocks"] + info["bytes_super"]
+    rpq = requests_per_query(2, layout, tuning["load_mode"])
+    if plan == capi.QR_BATCH_REGIONS:
+        roofline, launches = region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream)
+        # the direct kernels on the same index and queries, for comparison
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
+        ms_d = best_ms(step, stream)
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_AUTO)
+        gq_d = m / (ms_d * 1e-3) / 1e9
+        roofline["direct_path"] = {
+            "Gq_s": round(gq_d, 3), "ms": round(ms_d, 3),
+            "algorithmic_bytes_per_query": bytes_per_query(2, layout, tuning["load_mode"]),
+            "random_requests_per_query": round(rpq, 3),
+            "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
+            "frac_of_random_request_ceiling": round(gq_d * rpq / ceiling, 4) if ceiling == ceiling else None}
+        log(f"[bench] direct kernels on the same batch: {gq_d:.2f} Gq/s")
+    else:
+        launches = 1
+        bpq = bytes_per_query(2, layout, tuning["load_mode"])
+        achieved = bpq * m / (avg_ms * 1e-3) / 1e9
+        kname = {0: "birank_rank_paper", 1: "birank_rank_sector", 2: "birank_rank_line128"}[layout]
+        tr = traffic_record(kname)
+        gq_launch = m / (avg_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
+                    "peak_kind": f"of {peak_kind} (copy bandwidth)",
+                    "kernel": {0: "rank_kernel<K,LOAD,kBiScalar>", 1: "rank_sector_kernel<K,kBiScalar>",
+                               2: "rank_line_kernel<K,kBiScalar>"}[layout],
+                    "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
+                    "random_requests_per_query": round(rpq, 3),
+                    "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
+                    "random_request_ceiling_kind": "128-byte quad-cooperative" if layout == 2 else "32-byte",
+                    "frac_of_random_request_ceiling": round(gq_launch * rpq / ceiling, 4) if ceiling == ceiling
+                    else None}
 
     # end to end through the public host-buffer API (H2D + kernels + D2H)
     qh = torch.from_numpy(q.view(np.int64)).pin_memory()
@@ -316,7 +381,10 @@ def run_ours(args):
                    "n_bits": n, "queries_per_gpu": m,
                    "layout": {0: "BiRank16 (3.28% overhead)", 1: "BiRank16x2 sector layout (6.72% overhead)",
                               2: "BiRank16 on 128-byte lines (1.69% overhead)"}[layout],
-                   "index_bytes": info["bytes_blocks"] + info["bytes_super"], "tuning": tuning,
+                   "index_bytes": index_bytes, "tuning": tuning,
+                   "batch_path": "region batching (tiles of 8192 queries sorted by 256 text regions, answered "
+                                 "region after region from L2, results put back in query order)"
+                   if plan == capi.QR_BATCH_REGIONS else "direct kernels (one line load per query)",
                    "tuned_build_s": round(t_tune, 2),
                    "l2": "inputs larger than L2 (2 GiB queries, 2.3 GB index; L2 129 MB)",
                    "parallelism": f"independent replica per GPU x{ws}"},
@@ -324,7 +392,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e_val, 3), "unit": "Gqueries/s", "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 8 * m,
                 "api": "qr_rank_host: pinned host q/out, chunks of 2^23 on four streams"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches,
         "gpu_launches_e2e_per_step": (m + CHUNK_HOST - 1) // CHUNK_HOST,
         "clocks": clk.summary(),
     }

@@ -224,6 +224,8 @@ int qr_set_tuning(qr_index* idx, const qr_tuning_t* t);
  *            production batch (same size class and distribution).
  *   mode     0: qr_rank with symbol c; 1: qr_rank_c with c_vec; 2: qr_rank4.
  *   out      device scratch output: m uint64 (4 m for mode 2).
+ * The candidates run the direct kernels (region batching, where the handle
+ * would use it, is switched off while they are timed).
  * Synchronises stream.  Errors: QR_EINVAL, QR_ECUDA.  This library's own
  * addition: the paper tunes by hand per CPU (Sec. 3.1 and 4.1 variants).
  */
@@ -232,9 +234,11 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
 
 /*
  * qr_build_tuned -- build the index in every layout whose space overhead is at
- * most max_overhead (fraction of the text size, e.g. 0.10), autotune each on
- * the given queries as qr_autotune does, and return the fastest; the others
- * are freed.  *layout_out (may be NULL) receives the chosen QR_LAYOUT_*.
+ * most max_overhead (fraction of the text size, e.g. 0.10), autotune each as
+ * qr_autotune does on the first min(m, 2^24) of the given queries, time each
+ * tuned index on all m queries (by the path qr_rank takes for a batch of m,
+ * region batching included) and return the fastest; the others are freed.
+ * *layout_out (may be NULL) receives the chosen QR_LAYOUT_*.
  * Overheads: sigma 2 paper 3.28%, sector 6.72%, 128-byte lines 1.69%; sigma 4
  * paper 14.40%, sector 33.46%, 128-byte lines 6.88%.
  * Errors: QR_EINVAL (no layout within max_overhead), as qr_build.
@@ -242,6 +246,73 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
 int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_device, double max_overhead,
                    const uint64_t* q, uint64_t m, int mode, int c, const uint8_t* c_vec, uint64_t* out, void* stream,
                    qr_index** idx_out, int* layout_out);
+
+/*
+ * Region batching -- how qr_rank and qr_rank_c answer a large batch.
+ * The paper answers each query from its own cache line and hides the
+ * latency of the line by prefetching while it works through a batch of
+ * independent queries (Sec. 3 "Prefetching", Sec. 5.1 for-loop and prefetch
+ * modes).  On GB300 a random 64-byte line costs a whole 128-byte DRAM fill,
+ * so a batch that holds several queries per line of the index is answered
+ * faster by moving the queries instead: the batch is cut into tiles of 8192
+ * queries, every tile is sorted by text region in shared memory (256
+ * regions, region = q >> shift), the sorted runs are answered region after
+ * region (the lines of the region in flight stay in L2, each line is read
+ * from DRAM about once per batch) and every tile's results are put back in
+ * query order.  Every result is computed by the same query arithmetic from
+ * the same line, so the outputs are those of the direct kernels, bit for
+ * bit.  This is this library's own addition; the paper has no counterpart.
+ *   QR_BATCH_AUTO     (default) region batching when the index is not
+ *                     L2-resident (more than half of L2), 2^20 <= m < 2^32 and
+ *                     the batch holds at least two queries per 128 bytes of
+ *                     index; the direct kernels otherwise.  When region
+ *                     batching is chosen, a probe kernel first counts the
+ *                     regions met by the leading 1024 queries of 64 tiles; a
+ *                     clustered batch (at most 4 regions per probe on
+ *                     average, e.g. sorted queries, whose neighbours share
+ *                     lines) is answered by the direct kernels instead.  The
+ *                     choice is made on the device: both paths are launched
+ *                     and the one not chosen returns at once.
+ *   QR_BATCH_DIRECT   always the direct kernels (one line load per query).
+ *   QR_BATCH_REGIONS  region batching for every m < 2^32.
+ * Scope: qr_rank and qr_rank_c on the paper and sector layouts; rank_4,
+ * prefix_rank, chains and the 128-byte line layout always run direct.
+ * Scratch: 8 bytes per query plus 4 bytes per (region, tile) pair (1/8
+ * byte per query), from a memory pool of the library that keeps the memory
+ * for later calls (released by qr_release_scratch).  When that memory cannot
+ * be had, the call runs the direct kernels instead.
+ * Status bits and sentinel outputs are those of the direct kernels.
+ */
+#define QR_BATCH_AUTO 0
+#define QR_BATCH_DIRECT 1
+#define QR_BATCH_REGIONS 2
+
+/* Set the batch mode of the handle (QR_BATCH_*).  Errors: QR_EINVAL. */
+int qr_set_batch_mode(qr_index* idx, int mode);
+
+/* *plan = the path a call of m queries would take on this handle:
+ * QR_BATCH_DIRECT or QR_BATCH_REGIONS (rank4: 0 rank / rank_c, 1 rank_4,
+ * 2 prefix_rank).  Under QR_BATCH_AUTO, QR_BATCH_REGIONS means region
+ * batching subject to the device-side probe for clustered batches.
+ * Errors: QR_EINVAL (NULL arguments, rank4 out of range). */
+int qr_rank_plan(const qr_index* idx, uint64_t m, int rank4, int* plan);
+
+/* Measurement aid: with enable != 0, region-batched calls on this handle
+ * record CUDA events between their three passes (sort, rank, unsort).  With
+ * ms3 != NULL the call first waits for the last such call and writes the
+ * three pass durations in milliseconds.  Not for concurrent calls on one
+ * handle.  Errors: QR_EINVAL (ms3 before timing was enabled), QR_ECUDA. */
+int qr_region_timing(qr_index* idx, int enable, float* ms3);
+
+/* Launch tuning of the rank pass of region batching: variant 0..3 picks
+ * the items in flight per lane, the resident blocks per SM, how far ahead
+ * work items are loaded, the sorted runs per warp-step and whether steps are
+ * handed out by a device queue.  Errors: QR_EINVAL. */
+int qr_set_region_tuning(qr_index* idx, int variant);
+
+/* Return the pooled scratch memory of region batching to the device (on every
+ * device the library has used).  Errors: QR_ECUDA. */
+int qr_release_scratch(void);
 
 /* Synchronise stream, return the OR of the status bits (QR_ERANGE, QR_EBADSYM,
  * QR_ETIMEOUT; each >= 4) set by queries since the last call, and clear them;

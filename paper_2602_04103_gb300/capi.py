@@ -73,6 +73,11 @@ _sig("qr_build_tuned", [vp, u64, i32, i32, C.c_double, vp, u64, i32, i32, vp, vp
 _sig("qr_status", [vp, vp])
 _sig("qr_free", [vp])
 _sig("qr_probe_gather", [vp, u64, i32, i32, u64, u64, vp, i32, i32, vp])
+_sig("qr_set_batch_mode", [vp, i32])
+_sig("qr_rank_plan", [vp, u64, i32, C.POINTER(C.c_int)])
+_sig("qr_region_timing", [vp, i32, C.POINTER(C.c_float)])
+_sig("qr_release_scratch", [])
+_sig("qr_set_region_tuning", [vp, i32])
 
 
 def _check(rc: int, where: str) -> None:
@@ -216,6 +221,35 @@ def qr_build_tuned(text, n: int, sigma: int, q, out, c=1, rank4=False, max_overh
     _check(lib.qr_build_tuned(ptr(text), n, sigma, on_dev, max_overhead, ptr(q), numel(q), mode, ci, cv, ptr(out),
                               stream_ptr(stream), C.byref(h), C.byref(lay)), "qr_build_tuned")
     return QRIndex(h.value), lay.value
+
+
+QR_BATCH_AUTO, QR_BATCH_DIRECT, QR_BATCH_REGIONS = 0, 1, 2
+
+
+def qr_set_batch_mode(idx: QRIndex, mode: int) -> None:
+    _check(lib.qr_set_batch_mode(idx, mode), "qr_set_batch_mode")
+
+
+def qr_rank_plan(idx: QRIndex, m: int, rank4: int = 0) -> int:
+    plan = C.c_int()
+    _check(lib.qr_rank_plan(idx, m, rank4, C.byref(plan)), "qr_rank_plan")
+    return plan.value
+
+
+def qr_region_timing(idx: QRIndex, enable: bool, read: bool = False) -> list[float] | None:
+    """Switch per-pass timing of region-batched calls; with read=True first return the
+    last such call's three pass times (sort, rank, unsort) in ms."""
+    ms = (C.c_float * 3)()
+    _check(lib.qr_region_timing(idx, int(enable), ms if read else None), "qr_region_timing")
+    return list(ms) if read else None
+
+
+def qr_set_region_tuning(idx: QRIndex, variant: int = 0) -> None:
+    _check(lib.qr_set_region_tuning(idx, variant), "qr_set_region_tuning")
+
+
+def qr_release_scratch() -> None:
+    _check(lib.qr_release_scratch(), "qr_release_scratch")
 
 
 def qr_status(idx: QRIndex, stream=None) -> int:

@@ -68,6 +68,8 @@ static void free_index(qr_index* idx) {
         if (s) cudaStreamDestroy(s);
     for (auto& e : idx->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : idx->region_ev)
+        if (e) cudaEventDestroy(e);
     delete idx;
 }
 
@@ -325,6 +327,9 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
     QR_CUDA_TRY(cudaEventCreate(&e1));
     const qr_tuning_t saved = idx->tune;
     qr_tuning_t win = saved;
+    // the candidates tune the direct kernels, so time those alone
+    const int saved_mode = idx->batch_mode;
+    idx->batch_mode = QR_BATCH_DIRECT;
     float win_ms = 1e30f;
     const int ks[] = {1, 2, 4, 8}, ths[] = {128, 256, 512};
     const int nload = idx->layout == QR_LAYOUT_PAPER ? 5 : 1;
@@ -354,10 +359,13 @@ int qr_autotune(qr_index* idx, const uint64_t* q, uint64_t m, int mode, int c, c
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    idx->batch_mode = saved_mode;
     idx->tune = rc == QR_OK ? win : saved;
     if (best) *best = idx->tune;
     return rc;
 }
+
+static constexpr uint64_t kTuneSample = 1ull << 24;  // queries timed per autotuning candidate
 
 static double layout_overhead(int sigma, int layout, uint64_t n) {
     const uint64_t B = block_chars(sigma, layout), per = super_lines(sigma, layout);
@@ -386,8 +394,10 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
             if (best) qr_free(best);
             return rc;
         }
+        // the direct kernels are tuned on a prefix of the batch; the layouts are
+        // then compared on the whole batch, by the path the handle takes for it
         qr_tuning_t t;
-        rc = qr_autotune(idx, q, m, mode, c, c_vec, out, stream, &t);
+        rc = qr_autotune(idx, q, m < kTuneSample ? m : kTuneSample, mode, c, c_vec, out, stream, &t);
         if (rc != QR_OK) {
             qr_free(idx);
             if (best) qr_free(best);
@@ -423,6 +433,51 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
     if (layout_out) *layout_out = best_layout;
     return QR_OK;
 }
+
+int qr_set_batch_mode(qr_index* idx, int mode) {
+    if (!idx) return fail(QR_EINVAL, "qr_set_batch_mode: NULL index");
+    if (mode != QR_BATCH_AUTO && mode != QR_BATCH_DIRECT && mode != QR_BATCH_REGIONS)
+        return fail(QR_EINVAL, "qr_set_batch_mode: unknown mode");
+    idx->batch_mode = mode;
+    return QR_OK;
+}
+
+int qr_rank_plan(const qr_index* idx, uint64_t m, int rank4, int* plan) {
+    if (!idx || !plan) return fail(QR_EINVAL, "qr_rank_plan: NULL argument");
+    if (rank4 < 0 || rank4 > 2) return fail(QR_EINVAL, "qr_rank_plan: rank4 must be 0, 1 or 2");
+    bool regions = false;
+    if (m > 0 && region_supported(idx, rank4) && idx->batch_mode != QR_BATCH_DIRECT)
+        regions = idx->batch_mode == QR_BATCH_REGIONS ? m < (1ull << 32) : region_auto(idx, m);
+    *plan = regions ? QR_BATCH_REGIONS : QR_BATCH_DIRECT;
+    return QR_OK;
+}
+
+int qr_region_timing(qr_index* idx, int enable, float* ms3) {
+    if (!idx) return fail(QR_EINVAL, "qr_region_timing: NULL index");
+    if (ms3) {
+        if (!idx->region_ev[3]) return fail(QR_EINVAL, "qr_region_timing: timing was never enabled");
+        QR_CUDA_TRY(cudaEventSynchronize(idx->region_ev[3]));
+        for (int k = 0; k < 3; k++) {
+            float x = 0;
+            QR_CUDA_TRY(cudaEventElapsedTime(&x, idx->region_ev[k], idx->region_ev[k + 1]));
+            ms3[k] = x;
+        }
+    }
+    if (enable)
+        for (auto& e : idx->region_ev)
+            if (!e) QR_CUDA_TRY(cudaEventCreate(&e));
+    idx->region_timing = enable != 0;
+    return QR_OK;
+}
+
+int qr_set_region_tuning(qr_index* idx, int variant) {
+    if (!idx) return fail(QR_EINVAL, "qr_set_region_tuning: NULL index");
+    if (variant < 0 || variant > 3) return fail(QR_EINVAL, "qr_set_region_tuning: variant must be 0..3");
+    idx->region_variant = variant;
+    return QR_OK;
+}
+
+int qr_release_scratch(void) { return region_trim(); }
 
 int qr_status(qr_index* idx, void* stream) {
     if (!idx) return fail(QR_EINVAL, "qr_status: NULL index");

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 
 #include "quadrank.h"
@@ -363,6 +364,10 @@ struct qr_index {
     uint32_t* status = nullptr;  // device status word
     int device = 0;
     qr_tuning_t tune{4, 256, 0, 0};
+    int batch_mode = QR_BATCH_AUTO;  // direct kernels or region batching (qr_set_batch_mode)
+    int region_variant = 0;          // rank pass launch variant, 0..3 (qr_set_region_tuning)
+    bool region_timing = false;      // record events between the region passes
+    cudaEvent_t region_ev[4] = {};
     // host-buffer pipeline (lazy): kPipe streams, one staging slot each
     static constexpr int kPipe = 4;
     void* stage = nullptr;
@@ -381,8 +386,25 @@ int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
 // rank(q, c), 1: rank_4, 2: prefix_rank(q, c).
 int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                 int rank4, cudaStream_t s);
+// The direct kernels alone (gate: see RankArgs; NULL = always run).
+int launch_direct(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                  int rank4, cudaStream_t s, const unsigned long long* gate, unsigned long long gate_limit);
 int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out,
                  cudaStream_t s);
+// Region batching (qr_region.cu): which calls it serves, the automatic rule,
+// the launch (marks: 4 events recorded around the three passes, or NULL) and
+// the release of its pooled scratch.
+bool region_supported(const qr_index* idx, int rank4);
+bool region_auto(const qr_index* idx, uint64_t m);
+// direct (may be NULL): launches the direct kernels gated by a device count
+// (they run only when *count <= limit); with it, region batching adds the
+// probe that sets the count, and its passes run only when *count > limit.
+using DirectLaunch = std::function<int(const unsigned long long* count, unsigned long long limit)>;
+int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                        cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct);
+int region_trim();
+int region_tile_queries();
+int region_count_regions();
 int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
                  int k, int threads, cudaStream_t s);
 }  // namespace qr

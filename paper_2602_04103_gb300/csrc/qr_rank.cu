@@ -20,6 +20,7 @@ namespace {
 
 template <int K, int LOAD, int KIND>
 __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
+    if (a.gate && *a.gate > a.gate_limit) return;
     constexpr bool kQuad = KIND >= kQuadScalar;
     const uint64_t tile = (uint64_t)blockDim.x * K;
     uint32_t bad_flags = 0;
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(512) rank_kernel(RankArgs a) {
 // the line that holds both the query's bits and the delta to their middle.
 template <int K, int KIND>
 __global__ void __launch_bounds__(512) rank_sector_kernel(RankArgs a) {
+    if (a.gate && *a.gate > a.gate_limit) return;
     constexpr bool kQuad = KIND >= kQuadScalar;
     const uint64_t tile = (uint64_t)blockDim.x * K;
     uint32_t bad_flags = 0;
@@ -490,6 +492,23 @@ __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ b
 int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                 int rank4, cudaStream_t s) {
     if (m == 0) return QR_OK;
+    if (region_supported(idx, rank4) && idx->batch_mode != QR_BATCH_DIRECT &&
+        (idx->batch_mode == QR_BATCH_REGIONS ? m < (1ull << 32) : region_auto(idx, m))) {
+        // the automatic rule adds a device-side probe: a clustered (e.g.
+        // sorted) batch is answered by the direct kernels after all
+        const DirectLaunch direct = [&](const unsigned long long* count, unsigned long long limit) {
+            return launch_direct(idx, q, cvec, c, m, out, rank4, s, count, limit);
+        };
+        cudaEvent_t* marks = idx->region_timing ? (cudaEvent_t*)idx->region_ev : nullptr;
+        const int rc = launch_rank_regions(idx, q, cvec, c, m, out, s, marks,
+                                           idx->batch_mode == QR_BATCH_AUTO ? &direct : nullptr);
+        if (rc != QR_ENOMEM) return rc;  // without scratch memory the direct kernels answer the batch
+    }
+    return launch_direct(idx, q, cvec, c, m, out, rank4, s, nullptr, 0);
+}
+
+int launch_direct(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                  int rank4, cudaStream_t s, const unsigned long long* gate, unsigned long long gate_limit) {
     int kind;
     if (idx->sigma == 2) kind = cvec ? kBiVec : kBiScalar;
     else kind = rank4 == 2 ? kQuadPrefix : rank4 ? kQuad4 : (cvec ? kQuadVec : kQuadScalar);
@@ -497,7 +516,7 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
     KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR,
                             idx->layout == QR_LAYOUT_LINE128);
     if (!fn) return fail(QR_EINVAL, "no rank kernel for this tuning");
-    RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status};
+    RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status, gate, gate_limit};
     const uint64_t tiles = (m + (uint64_t)t.block_threads * t.queries_per_thread - 1) /
                            ((uint64_t)t.block_threads * t.queries_per_thread);
     uint64_t grid = t.grid_blocks > 0 ? (uint64_t)t.grid_blocks : resident_grid(fn, t.block_threads);
@@ -510,7 +529,7 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
 int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint64_t steps, int c, uint64_t* out,
                  cudaStream_t s) {
     if (nchains == 0) return QR_OK;
-    RankArgs a{idx->lines, idx->supers, idx->n, q0, nullptr, c, nchains, out, idx->status};
+    RankArgs a{idx->lines, idx->supers, idx->n, q0, nullptr, c, nchains, out, idx->status, nullptr, 0};
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR;
     ChainFn fn = idx->layout == QR_LAYOUT_LINE128
                      ? pick_chain_line(quad)

@@ -23,6 +23,10 @@ struct RankArgs {
     uint64_t m;
     uint64_t* __restrict__ out;
     uint32_t* status;
+    // set when region batching was chosen by the automatic rule: the kernel
+    // runs only when *gate <= gate_limit (a clustered batch)
+    const unsigned long long* gate;
+    unsigned long long gate_limit;
 };
 
 using KernelFn = void (*)(RankArgs);

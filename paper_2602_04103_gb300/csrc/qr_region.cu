@@ -1,0 +1,694 @@
+// Region-batched rank: a large batch of queries is grouped by text region
+// before it is answered, so that every region of the index is read from HBM
+// about once per batch and its lines are then served from L2.
+//
+// On GB300 a random 64-byte line costs a whole 128-byte DRAM fill, and random
+// fills arrive at ~38 G/s, far below the rate at which the same DRAM streams.
+// A batch of m uniform queries over an index of L lines touches each line
+// about m / L times (2^28 queries over the 3.5e7 lines of a 2^34-bit
+// BiRank16 index: 7.75 times), so for such batches it pays to move the
+// queries instead of the lines.  Every query is still answered from its own
+// line by the paper's query arithmetic (Sec. 3 Eq. 1, Sec. 4 rank1); only
+// the order in which lines are visited changes, so results are identical.
+//
+// Three passes over a batch cut into tiles of 8192 queries and 256 regions
+// (region = q >> shift, the smallest shift that maps [0, n] onto 256):
+//   sort    tile t sorts its queries by region in shared memory (a counting
+//           sort) and writes them back to its own slice of the work array;
+//           an item packs the query, its symbol and its index inside the
+//           tile; the start and length of each region's run go to a
+//           region-major segment table, seg[r * tiles + t];
+//   rank    warps take steps of 16 segments of the table, in table order,
+//           from a device work queue, i.e. region after region, so the lines
+//           of the one or two regions in flight stay in L2; each item is
+//           replaced by its result (same packing);
+//   unsort  tile t reads its slice back, puts every result at its index in
+//           shared memory and writes the tile's outputs in order.
+// The sort and unsort passes read and write whole tiles (coalesced); the rank
+// pass reads runs of ~32 items per (region, tile).  The work array (8 bytes
+// per query) and the segment table come from a memory pool of the library
+// that keeps them for later calls.  Measured on GB300 and kept out: a count
+// pass plus a global scan to place runs region-major (one more read of the
+// queries, and __match_any_sync grouping ran at 1.2 TB/s); blocks walking 64
+// runs with a shared-memory search (barrier-bound); strided warp steps
+// (warps drift apart, the regions in flight outgrow L2); bulk L2 prefetch of
+// the next region's lines and of the next runs (slower).
+//
+// Sorted batches: each tile is one run, so a warp step would hold whole
+// tiles; such batches are sent to the direct kernels by the probe (see Gate).
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "qr_common.cuh"
+#include "qr_rank.cuh"
+
+namespace qr {
+namespace {
+
+constexpr uint32_t kTile = 8192;    // queries per tile
+constexpr uint32_t kRegions = 256;  // regions of the text
+constexpr int kPassThreads = 512;   // sort / unsort
+constexpr int kPer = kTile / kPassThreads;
+constexpr int kRankThreads = 256;
+
+// Item: bits 0..44 the position q (later its result, both < 2^45), 45..46
+// the symbol, 47..59 the index inside the tile, 63 set for a query that is
+// out of range (q > n) or has a bad symbol.
+constexpr uint64_t kValMask = (1ull << 45) - 1;
+constexpr int kSymShift = 45;
+constexpr int kIdxShift = 47;
+constexpr uint64_t kIdxBits = (uint64_t)(kTile - 1) << kIdxShift;
+constexpr uint64_t kBadItem = 1ull << 63;
+constexpr uint32_t kAll = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t region_of(uint64_t q, int shift) {
+    const uint64_t r = q >> shift;
+    return r < kRegions ? (uint32_t)r : kRegions - 1;
+}
+
+// Exclusive scan of v over the first 32 * nw threads of a block (nw <= 8
+// warps); ws = 8 words of shared scratch; *total (may be NULL) receives the
+// sum.  Every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, int nw, uint32_t* ws, uint32_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (w < nw && lane == 31) ws[w] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int k = 0; k < nw; k++) {
+        const uint32_t x = ws[k];
+        before += k < w ? x : 0u;
+        all += x;
+    }
+    if (total) *total = all;
+    __syncthreads();
+    return before + incl - v;
+}
+
+// ---------------------------------------------------------------- gate
+// With region batching chosen by the automatic rule, a probe kernel counts
+// the distinct regions among the first queries of a few tiles spread over
+// the batch.  Few regions per tile mean a clustered (e.g. sorted) batch, which
+// the direct kernels answer faster (neighbouring queries share lines); the
+// direct kernel and the three region passes are all launched, and each reads
+// the count first and returns at once unless it is the path chosen.
+// gate == NULL: no probe, run unconditionally.
+struct Gate {
+    const unsigned long long* count;
+    unsigned long long limit;  // clustered when *count <= limit
+};
+__device__ __forceinline__ bool regions_chosen(const Gate& g) { return !g.count || *g.count > g.limit; }
+
+constexpr int kProbeTiles = 64;     // tiles probed
+constexpr int kProbeQueries = 1024; // leading queries of each probed tile
+constexpr int kClusterMax = 4;      // mean distinct regions per probe at most -> direct
+
+__global__ void __launch_bounds__(256) region_probe(const uint64_t* __restrict__ q, uint64_t m, int shift,
+                                                    uint64_t tiles, unsigned long long* __restrict__ count) {
+    __shared__ uint32_t bits[kRegions / 32];
+    if (threadIdx.x < kRegions / 32) bits[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t = (uint64_t)blockIdx.x * tiles / gridDim.x, base = t * kTile;
+    const uint64_t len = m - base < (uint64_t)kProbeQueries ? m - base : (uint64_t)kProbeQueries;
+    for (uint32_t i0 = 0; i0 < kProbeQueries; i0 += blockDim.x) {
+        const uint32_t i = i0 + threadIdx.x;
+        const uint32_t r = i < len ? region_of(q[base + i], shift) : ~0u;
+#pragma unroll
+        for (int w = 0; w < (int)(kRegions / 32); w++) {
+            const uint32_t mine = (r >> 5) == (uint32_t)w ? 1u << (r & 31) : 0u;
+            const uint32_t all = __reduce_or_sync(kAll, mine);
+            if ((threadIdx.x & 31) == 0 && all) atomicOr(&bits[w], all);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t c = threadIdx.x < kRegions / 32 ? __popc(bits[threadIdx.x]) : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kAll, c, o);
+        if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)c);
+    }
+}
+
+// ---------------------------------------------------------------- sort
+// Counting sort of one tile by region.  The rank of a query inside its region
+// comes from a shared-memory atomic; a warp whose queries all fall in one
+// region (sorted batches) takes one atomic for all its lanes.  The second
+// phase reads the tile's queries again (L2 hits) rather than keeping 16 of
+// them per thread in registers across the block-wide scan.
+template <bool VEC>
+__global__ void __launch_bounds__(kPassThreads, 2) region_sort(const uint64_t* __restrict__ q,
+                                                               const uint8_t* __restrict__ cv, uint32_t c0,
+                                                               uint32_t sigma, uint64_t m, uint64_t n, int shift,
+                                                               uint64_t tiles, uint64_t* __restrict__ work,
+                                                               uint32_t* __restrict__ seg, uint32_t* status,
+                                                               Gate gate) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* stage = (uint64_t*)smem;                      // kTile items in region order
+    uint16_t* rank_in = (uint16_t*)(smem + kTile * 8);      // rank of query i inside its region
+    uint32_t* h = (uint32_t*)(smem + kTile * 10);           // region sizes, then starts
+    uint32_t* ws = h + kRegions;
+    if (!regions_chosen(gate)) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t flags = 0;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t base = t * kTile;
+    const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
+    for (uint32_t r = threadIdx.x; r < kRegions; r += blockDim.x) h[r] = 0;
+    __syncthreads();
+    {
+        uint64_t v[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const uint32_t i = threadIdx.x + k * kPassThreads;
+            v[k] = i < len ? q[base + i] : 0;  // default policy: read again below, from L2
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const uint32_t i = threadIdx.x + k * kPassThreads;
+            const bool live = i < len;
+            const uint32_t r = region_of(v[k], shift);
+            const unsigned act = __ballot_sync(kAll, live);
+            if (!act) continue;
+            const int lead = __ffs(act) - 1;
+            const uint32_t r0 = __shfl_sync(kAll, r, lead);
+            if (__all_sync(kAll, !live || r == r0)) {
+                uint32_t b = 0;
+                if (lane == lead) b = atomicAdd(&h[r0], (uint32_t)__popc(act));
+                b = __shfl_sync(kAll, b, lead);
+                if (live) rank_in[i] = (uint16_t)(b + __popc(act & ((1u << lane) - 1u)));
+            } else if (live) {
+                rank_in[i] = (uint16_t)atomicAdd(&h[r], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t sz = threadIdx.x < kRegions ? h[threadIdx.x] : 0u;
+    const uint32_t st = block_scan(sz, kRegions / 32, ws, nullptr);
+    if (threadIdx.x < kRegions) {
+        h[threadIdx.x] = st;
+        seg[(uint64_t)threadIdx.x * tiles + t] = st | (sz << 16);
+    }
+    __syncthreads();
+    {
+        uint64_t x[kPer];
+        uint32_t cw[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const uint32_t i = threadIdx.x + k * kPassThreads;
+            x[k] = i < len ? ld_stream_u64(q + base + i) : 0;
+            cw[k] = VEC ? (i < len ? (uint32_t)ld_stream_u8(cv + base + i) : 0u) : c0;
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const uint32_t i = threadIdx.x + k * kPassThreads;
+            if (i < len) {
+                const bool range_bad = x[k] > n, sym_bad = cw[k] >= sigma;
+                flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                const uint64_t item = ((uint64_t)i << kIdxShift) |
+                                      (range_bad || sym_bad ? kBadItem : (x[k] | ((uint64_t)cw[k] << kSymShift)));
+                stage[h[region_of(x[k], shift)] + rank_in[i]] = item;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const uint32_t p = threadIdx.x + k * kPassThreads;
+        if (p < len) work[base + p] = stage[p];
+    }
+    __syncthreads();  // the next tile reuses the shared arrays
+    }
+    if (flags) atomicOr(status, flags);
+}
+
+constexpr size_t kSortSmem = (size_t)kTile * 10 + (kRegions + 8) * 4;
+
+// ---------------------------------------------------------------- unsort
+__global__ void __launch_bounds__(kPassThreads, 2) region_unsort(const uint64_t* __restrict__ work, uint64_t m,
+                                                                 uint64_t tiles, uint64_t* __restrict__ out,
+                                                                 Gate gate) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* res = (uint64_t*)smem;
+    if (!regions_chosen(gate)) return;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t base = t * kTile;
+    const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
+    uint64_t it[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const uint32_t p = threadIdx.x + k * kPassThreads;
+        it[k] = p < len ? ld_stream_u64(work + base + p) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const uint32_t p = threadIdx.x + k * kPassThreads;
+        if (p < len) res[(it[k] & kIdxBits) >> kIdxShift] = (it[k] & kBadItem) ? ~0ull : (it[k] & kValMask);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        const uint32_t i = threadIdx.x + k * kPassThreads;
+        if (i < len) st_stream_u64(out + base + i, res[i]);
+    }
+    __syncthreads();  // the next tile reuses res
+    }
+}
+
+constexpr size_t kUnsortSmem = (size_t)kTile * 8;
+
+// ---------------------------------------------------------------- rank
+// Paper layout (BiRank16 / QuadRank16): the 32-byte half of the line that
+// holds the query's bits, plus the first 8 or 16 bytes (the deltas) when that
+// is the upper half.  Sector layout: the one self-contained half.
+template <bool SECTOR, bool QUAD>
+struct RegionLoad {
+    u64x4 X;
+    uint64_t w0, w1;
+    uint32_t s;
+    uint32_t pos;
+};
+
+template <bool SECTOR, bool QUAD>
+__device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD>& L, const uint4* __restrict__ lines,
+                                             const void* __restrict__ supers, uint64_t q, uint32_t c) {
+    if (SECTOR) {
+        uint64_t j;
+        uint32_t h;
+        if (!QUAD) {
+            j = div480(q);
+            const uint32_t p = (uint32_t)(q - j * kB2s);
+            h = p >= kHalf2s;
+            L.pos = p - h * (uint32_t)kHalf2s;
+            L.s = __ldg((const uint32_t*)supers + (j >> 7));
+        } else {
+            j = div192(q);
+            const uint32_t d = (uint32_t)(q - j * kB4s);
+            h = d >= kHalf4s;
+            L.pos = d - h * (uint32_t)kHalf4s;
+            L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+        }
+        L.X = ld_line32(lines + 4 * j + 2 * h);
+        L.w0 = L.w1 = 0;
+    } else {
+        uint64_t j;
+        bool upper;
+        if (!QUAD) {
+            j = div496(q);
+            L.pos = (uint32_t)(q - j * kB2);
+            upper = L.pos >= kMid2;
+            L.s = __ldg((const uint32_t*)supers + (j >> 7));
+        } else {
+            j = div224(q);
+            L.pos = (uint32_t)(q - j * kB4) + 32;
+            upper = L.pos >= 128;
+            L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+        }
+        const uint4* P = lines + 4 * j;
+        L.X = ld_line32(P + 2 * upper);
+        L.w0 = L.w1 = 0;
+        if (upper) {
+            const uint4 d = ld_line16(P);
+            L.w0 = lo64(d);
+            L.w1 = hi64(d);
+        }
+    }
+}
+
+template <bool SECTOR, bool QUAD>
+__device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD>& L, uint64_t q, uint32_t c) {
+    if (SECTOR) {
+        if (!QUAD) {
+            const uint64_t r1 = birank_sector_finish(L.s, L.X, L.pos);
+            return c == 1 ? r1 : q - r1;
+        }
+        return quad_sector_finish1(L.s, L.X, L.pos, (int)c);
+    }
+    const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
+    if (!QUAD) {
+        const bool upper = L.pos >= kMid2;
+        const uint64_t r1 = birank_finish(L.s, upper ? L.w0 : L.X.a, x, L.pos);
+        return c == 1 ? r1 : q - r1;
+    }
+    const bool upper = L.pos >= 128;
+    const uint64_t w0 = upper ? L.w0 : L.X.a, w1 = upper ? L.w1 : L.X.b;
+    return quad_finish1(L.s, quad_delta(w0, w1, (int)c), x, L.pos, (int)c);
+}
+
+// The rank pass.  Every warp walks its own runs of 32 consecutive segments of
+// the region-major table (warp-steps in table order across the grid, so the
+// whole GPU moves through the regions together): the lengths are scanned
+// with shuffles, the runs' items are laid end to end and each lane answers
+// items lane, lane + 32, ..., K of them per round; the run holding an item
+// is found by a 5-step search over the 32 starts held in the lanes.
+// With PF, two bulk L2 prefetches (the TMA unit's cp.async.bulk.prefetch)
+// keep the loads of a step hitting L2: each warp-step streams its share of
+// the NEXT region's index lines into L2 (sequential DRAM reads instead of
+// first-touch misses), and every lane prefetches the items of its segment of
+// the warp's next step.  The items of round t + P - 1 are loaded while round
+// t fetches its lines and counts.  No shared memory, no block barrier.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int K>
+struct ItemSlot {
+    uint64_t it[K], at[K];
+};
+
+template <int K, int SEGS>
+__device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint64_t* __restrict__ work, uint32_t j0,
+                                            uint32_t total, uint32_t start, uint64_t sbase, int lane) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const uint32_t j = j0 + lane + 32 * k;
+        // the last segment s with start[s] <= j
+        uint32_t sidx = 0;
+#pragma unroll
+        for (int b = SEGS / 2; b >= 1; b >>= 1) {
+            const uint32_t st = __shfl_sync(kAll, start, sidx + b);
+            if (st <= j) sidx += b;
+        }
+        const uint64_t sb = __shfl_sync(kAll, sbase, sidx);
+        const uint32_t s0 = __shfl_sync(kAll, start, sidx);
+        S.at[k] = sb + (j - s0);
+        S.it[k] = j < total ? ld_stream_u64(work + S.at[k]) : kBadItem;
+    }
+}
+
+struct RankPassArgs {
+    uint64_t* work;
+    const uint32_t* seg;
+    uint64_t nseg, tiles;
+    const uint4* lines;
+    const void* supers;
+    uint32_t c0;
+    uint64_t n;             // text length
+    int shift;              // region = q >> shift
+    uint64_t block_chars;   // chars per line
+    uint64_t nblocks;       // lines of the index
+    uint64_t line_bytes;
+    unsigned long long* queue;  // step counter (QUEUE variants), zero at launch
+    Gate gate;
+};
+
+template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, bool PF, int SEGS, bool QUEUE>
+__global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
+    if (!regions_chosen(a.gate)) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (kRankThreads / 32);
+    constexpr int kWarpSegs = SEGS;
+    const uint64_t nsteps = (a.nseg + kWarpSegs - 1) / kWarpSegs;
+    const uint64_t parts = (a.tiles + kWarpSegs - 1) / kWarpSegs;  // warp-steps per region (about)
+    constexpr uint32_t kRound = 32 * K;
+    uint64_t* __restrict__ work = a.work;
+    // the warp's next step: a strided sequence, or (QUEUE) taken in table order
+    // from a device counter, so that the steps in flight stay close together
+    auto next_step = [&](uint64_t cur) -> uint64_t {
+        if (!QUEUE) return cur + warps;
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(a.queue, 1ull);
+        return __shfl_sync(kAll, v, 0);
+    };
+    uint64_t g = QUEUE ? next_step(0) : (uint64_t)blockIdx.x * (kRankThreads / 32) + (threadIdx.x >> 5);
+    // this lane's segment of the warp's current step: length and first item
+    auto seg_of = [&](uint64_t step, uint32_t& len, uint64_t& sbase) {
+        len = 0;
+        sbase = 0;
+        const uint64_t w = step * kWarpSegs + lane;
+        if (lane < kWarpSegs && step < nsteps && w < a.nseg) {
+            const uint32_t e = __ldg(a.seg + w);
+            len = e >> 16;
+            sbase = (w % a.tiles) * kTile + (e & 0xFFFFu);
+        }
+    };
+    uint32_t len;
+    uint64_t sbase;
+    seg_of(g, len, sbase);
+    while (g < nsteps) {
+        uint32_t nlen = 0;
+        uint64_t nbase = 0;
+        const uint64_t gn = next_step(g);
+        if (PF) {
+            seg_of(gn, nlen, nbase);
+            if (nlen) {  // the items of this lane's segment of the next step
+                const uint64_t b0 = (nbase * 8) & ~15ull, b1 = ((nbase + nlen) * 8 + 15) & ~15ull;
+                prefetch_l2((const char*)work + b0, (uint32_t)(b1 - b0));
+            }
+            if (lane == 0) {  // this step's share of the next region's index lines
+                const uint64_t w0 = g * kWarpSegs, r = w0 / a.tiles + 1, part = (w0 % a.tiles) / kWarpSegs;
+                if (r < kRegions && (r << a.shift) <= a.n) {
+                    const uint64_t l0 = (r << a.shift) / a.block_chars;
+                    uint64_t l1 = (((r + 1) << a.shift) - 1) / a.block_chars + 1;
+                    if (l1 > a.nblocks) l1 = a.nblocks;
+                    const uint64_t bytes = (l1 - l0) * a.line_bytes;
+                    const uint64_t chunk = ((bytes + parts - 1) / parts + 127) & ~127ull;
+                    const uint64_t o0 = l0 * a.line_bytes + part * chunk;
+                    uint64_t o1 = o0 + (chunk < (1ull << 20) ? chunk : (1ull << 20));  // a hint: at most 1 MiB
+                    if (o1 > l1 * a.line_bytes) o1 = l1 * a.line_bytes;
+                    if (o0 < o1) prefetch_l2((const char*)a.lines + o0, (uint32_t)(o1 - o0));
+                }
+            }
+        }
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < kWarpSegs; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(kAll, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const uint32_t start = incl - len;  // first item of this lane's segment
+        const uint32_t total = __shfl_sync(kAll, incl, kWarpSegs - 1);
+        constexpr int PS = P > 0 ? P : 1;
+        ItemSlot<K> S[PS];
+#pragma unroll
+        for (int p = 0; p < P; p++) fetch_items<K, SEGS>(S[p], work, p * kRound, total, start, sbase, lane);
+        for (uint32_t j0 = 0; j0 < total; j0 += kRound) {
+            ItemSlot<K> cur;
+            if (P == 0) {
+                fetch_items<K, SEGS>(cur, work, j0, total, start, sbase, lane);
+            } else {
+                cur = S[0];
+#pragma unroll
+                for (int p = 0; p + 1 < P; p++) S[p] = S[p + 1];
+                if (j0 + P * kRound < total)
+                    fetch_items<K, SEGS>(S[PS - 1], work, j0 + P * kRound, total, start, sbase, lane);
+            }
+            RegionLoad<SECTOR, QUAD> L[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const bool bad = cur.it[k] & kBadItem;
+                const uint64_t qq = bad ? 0 : cur.it[k] & kValMask;  // bad items (and idle lanes) read line 0
+                const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
+                region_issue<SECTOR, QUAD>(L[k], a.lines, a.supers, qq, c);
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (cur.it[k] & kBadItem) continue;
+                const uint64_t qq = cur.it[k] & kValMask;
+                const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
+                const uint64_t r = region_finish<SECTOR, QUAD>(L[k], qq, c);
+                st_stream_u64(work + cur.at[k], r | (cur.it[k] & kIdxBits));
+            }
+        }
+        len = nlen;
+        sbase = nbase;
+        if (!PF) seg_of(gn, len, sbase);
+        g = gn;
+    }
+}
+
+// ---------------------------------------------------------------- scratch pool
+// One pool per device whose memory stays with the library after a call
+// returns it, so that repeated large batches do not map and unmap their
+// scratch every time.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+int region_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    QR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(QR_EINVAL, "region pool: device index");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps p = {};
+        p.allocType = cudaMemAllocationTypePinned;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        QR_CUDA_TRY(cudaMemPoolCreate(&pool, &p));
+        uint64_t keep = ~0ull;
+        cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return cuda_fail(e, "region pool: release threshold");
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return QR_OK;
+}
+
+template <typename F>
+int set_smem(F fn, size_t bytes) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return QR_OK;
+}
+
+using RankFn = void (*)(RankPassArgs);
+
+// Rank-pass variants (items per lane and round, resident blocks per SM,
+// rounds of items loaded ahead, bulk L2 prefetch, segments per warp-step,
+// steps from a device queue).
+template <bool SECTOR, bool QUAD, bool VEC>
+RankFn pick_variant(int v) {
+    switch (v) {
+        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, false, 16, true>;
+        case 1: return region_rank<SECTOR, QUAD, VEC, 2, 4, 2, false, 16, true>;
+        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, false, 32, true>;
+        case 3: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, true, 16, true>;
+        default: return nullptr;
+    }
+}
+
+RankFn pick_region_rank(bool sector, bool quad, bool vec, int v) {
+    if (sector) {
+        if (quad) return vec ? pick_variant<true, true, true>(v) : pick_variant<true, true, false>(v);
+        return vec ? pick_variant<true, false, true>(v) : pick_variant<true, false, false>(v);
+    }
+    if (quad) return vec ? pick_variant<false, true, true>(v) : pick_variant<false, true, false>(v);
+    return vec ? pick_variant<false, false, true>(v) : pick_variant<false, false, false>(v);
+}
+
+}  // namespace
+
+bool region_supported(const qr_index* idx, int rank4) {
+    return rank4 == 0 && idx->layout != QR_LAYOUT_LINE128;
+}
+
+bool region_auto(const qr_index* idx, uint64_t m) {
+    if (m < (1ull << 20) || m >= (1ull << 32)) return false;
+    const uint64_t bytes = line_bytes(idx->layout) * idx->nblocks;
+    const uint64_t l2 = (uint64_t)device_props().l2_bytes;
+    // an index that fits comfortably in L2 gains nothing; a batch with fewer
+    // than two queries per 128-byte DRAM line of the index has too little
+    // reuse to pay for moving the queries
+    return bytes > l2 / 2 && m * 64 >= bytes;
+}
+
+int region_tile_queries() { return (int)kTile; }
+int region_count_regions() { return (int)kRegions; }
+
+
+int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
+                        cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct) {
+    if (m == 0) return QR_OK;
+    if (m >= (1ull << 32)) return fail(QR_EINVAL, "region batch: m must be below 2^32");
+    const uint64_t tiles = (m + kTile - 1) / kTile;
+    const uint64_t nseg = (uint64_t)kRegions * tiles;
+    int shift = 0;
+    while ((idx->n >> shift) >= kRegions) shift++;
+    cudaMemPool_t pool;
+    int rc = region_pool(&pool);
+    if (rc) return rc;
+    const size_t work_bytes = (m * 8 + 255) & ~(size_t)255;
+    const size_t seg_bytes = (nseg * 4 + 255) & ~(size_t)255;
+    void* buf = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&buf, work_bytes + seg_bytes + 16, pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QR_ENOMEM, "region batch: no scratch memory");
+    }
+    uint64_t* work = (uint64_t*)buf;
+    uint32_t* seg = (uint32_t*)((char*)buf + work_bytes);
+    unsigned long long* counters = (unsigned long long*)((char*)buf + work_bytes + seg_bytes);  // queue, probe
+    static std::once_flag once[64];
+    static int once_rc[64];
+    const int dev = device_props().device & 63;
+    std::call_once(once[dev], [&] {
+        once_rc[dev] = set_smem(region_sort<false>, kSortSmem);
+        if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort<true>, kSortSmem);
+        if (!once_rc[dev]) once_rc[dev] = set_smem(region_unsort, kUnsortSmem);
+    });
+    rc = once_rc[dev];
+    const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR, vec = cvec != nullptr;
+    const int sms = device_props().sms;
+    Gate gate{nullptr, 0};
+    if (!rc) {
+        e = cudaMemsetAsync(counters, 0, 16, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "region batch: counter reset");
+    }
+    if (!rc && direct) {
+        // probe, then the direct kernels: they run only for a clustered batch
+        const uint64_t probes = tiles < (uint64_t)kProbeTiles ? tiles : (uint64_t)kProbeTiles;
+        region_probe<<<(unsigned)probes, 256, 0, s>>>(q, m, shift, tiles, counters + 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_probe");
+        gate = Gate{counters + 1, (unsigned long long)probes * kClusterMax};
+        if (!rc) rc = (*direct)(gate.count, gate.limit);
+    }
+    if (!rc && marks) cudaEventRecord(marks[0], s);
+    if (!rc) {
+        const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
+        if (vec)
+            region_sort<true><<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(
+                q, cvec, (uint32_t)c, (uint32_t)idx->sigma, m, idx->n, shift, tiles, work, seg, idx->status, gate);
+        else
+            region_sort<false><<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(
+                q, nullptr, (uint32_t)c, (uint32_t)idx->sigma, m, idx->n, shift, tiles, work, seg, idx->status, gate);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_sort");
+    }
+    if (!rc && marks) cudaEventRecord(marks[1], s);
+    if (!rc) {
+        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const uint64_t nsteps = (nseg + 7) / 8;
+        const uint64_t need = (nsteps + kRankThreads / 32 - 1) / (kRankThreads / 32);
+        uint64_t grid = (uint64_t)per_sm * sms;
+        if (grid > need) grid = need;
+        RankPassArgs ra;
+        ra.work = work;
+        ra.seg = seg;
+        ra.nseg = nseg;
+        ra.tiles = tiles;
+        ra.lines = idx->lines;
+        ra.supers = idx->supers;
+        ra.c0 = (uint32_t)c;
+        ra.n = idx->n;
+        ra.shift = shift;
+        ra.block_chars = block_chars(idx->sigma, idx->layout);
+        ra.nblocks = idx->nblocks;
+        ra.line_bytes = line_bytes(idx->layout);
+        ra.queue = counters;
+        ra.gate = gate;
+        fn<<<(unsigned)grid, kRankThreads, 0, s>>>(ra);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_rank");
+    }
+    if (!rc && marks) cudaEventRecord(marks[2], s);
+    if (!rc) {
+        const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
+        region_unsort<<<(unsigned)grid, kPassThreads, kUnsortSmem, s>>>(work, m, tiles, out, gate);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort");
+    }
+    if (!rc && marks) cudaEventRecord(marks[3], s);
+    cudaFreeAsync(buf, s);
+    return rc;
+}
+
+int region_trim() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& p : g_pool)
+        if (p) QR_CUDA_TRY(cudaMemPoolTrimTo(p, 0));
+    return QR_OK;
+}
+
+}  // namespace qr

@@ -46,6 +46,12 @@ def test_birank_full_size(p, sorted_q):
         got = host_u64(out)[sample]
         want, rc = oracle.rank(text, n, 2, q[sample], c)
         assert rc == 0 and np.array_equal(got, want), (layout, c)
+    # the other batch path (region batching or the direct kernels) agrees on every output
+    plan = capi.qr_rank_plan(idx, q.size)
+    capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT if plan == capi.QR_BATCH_REGIONS else capi.QR_BATCH_REGIONS)
+    other = torch.empty_like(dq)
+    capi.qr_rank(idx, dq, 0, other)
+    assert torch.equal(other, out), (layout, plan)
     assert capi.qr_status(idx) == 0
     idx.free()
 
@@ -63,7 +69,13 @@ def test_quadrank_full_size(kind):
     sample = workloads.sample_indices(q.size, 1 << 20, 6)
     want, rc = oracle.rank_c(text, n, 4, q[sample], c[sample])
     assert rc == 0 and np.array_equal(host_u64(out)[sample], want)
-    del out
+    plan = capi.qr_rank_plan(idx, q.size)
+    capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT if plan == capi.QR_BATCH_REGIONS else capi.QR_BATCH_REGIONS)
+    other = torch.empty_like(dq)
+    capi.qr_rank_c(idx, dq, dc, other)
+    assert torch.equal(other, out), (layout, plan)
+    capi.qr_set_batch_mode(idx, capi.QR_BATCH_AUTO)
+    del out, other
     out4 = torch.empty((q.size, 4), dtype=torch.int64, device="cuda")
     capi.qr_rank4(idx, dq, out4)
     want4, _ = oracle.rank4(text, n, q[sample])

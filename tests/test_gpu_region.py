@@ -1,0 +1,282 @@
+"""GPU parity of region-batched rank (qr_set_batch_mode QR_BATCH_REGIONS)
+against the oracle, bit-exact.
+
+Region batching sorts every tile of 8192 queries by text region (256
+regions), answers the sorted runs region after region and puts the results
+back in query order.  The cases cover several tiles with a ragged last tile, every region,
+out-of-range positions and symbols inside the batch, degenerate orders (all
+queries equal, sorted, reversed, everything in the first or last region),
+tiny texts where regions are single positions, batch sizes around the tile
+size, the automatic rule, two streams at once, and agreement with the direct
+kernels on a large batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_04103_gb300 import synth
+from tests.gpu_util import build, dev_u64, dev_u8, host_u64
+
+pytestmark = pytest.mark.gpu
+
+TILE = 8192
+B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
+LAYOUTS = [0, 1]  # the paper and sector layouts (the 128-byte line layout always runs direct)
+U64MAX = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def regions_index(words, n, sigma, layout):
+    from paper_2602_04103_gb300 import capi
+    idx = build(words, n, sigma, layout)
+    capi.qr_set_batch_mode(idx, capi.QR_BATCH_REGIONS)
+    return idx
+
+
+def run(idx, q, c):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    assert capi.qr_rank_plan(idx, q.size) == (capi.QR_BATCH_REGIONS if q.size else capi.QR_BATCH_DIRECT)
+    dq = dev_u64(q)
+    out = torch.empty_like(dq)
+    if isinstance(c, (int, np.integer)):
+        capi.qr_rank(idx, dq, int(c), out)
+    else:
+        capi.qr_rank_c(idx, dq, dev_u8(c), out)
+    return host_u64(out)
+
+
+def expect(words, n, sigma, q, c):
+    """Oracle ranks, UINT64_MAX where q > n or the symbol is out of range."""
+    c_arr = np.full(q.size, c, dtype=np.uint8) if isinstance(c, (int, np.integer)) else c
+    ok = (q <= n) & (c_arr < sigma)
+    want = np.full(q.size, U64MAX, dtype=np.uint64)
+    if ok.any():
+        w, rc = oracle.rank_c(words, n, sigma, q[ok], c_arr[ok])
+        assert rc == 0
+        want[ok] = w
+    return want
+
+
+def check(idx, words, n, sigma, q, c, status=0):
+    from paper_2602_04103_gb300 import capi
+    got = run(idx, q, c)
+    want = expect(words, n, sigma, q, c)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (n, sigma, q.size, bad[:5], got[bad[:5]], want[bad[:5]])
+    assert capi.qr_status(idx) == status
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_bits_tiles_ragged(layout):
+    n = 3 * S2 + 1234
+    words = synth.bits(synth.base_seed(40), n, 0.5)
+    idx = regions_index(words, n, 2, layout)
+    m = 3 * TILE + 77
+    q = synth.queries(synth.base_seed(41), n, m)
+    for c in (0, 1):
+        check(idx, words, n, 2, q, c)
+    cv = synth.symbols(synth.base_seed(42), m, 2)
+    check(idx, words, n, 2, q, cv)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_dna_tiles_ragged(layout):
+    n = 3 * S4 + 777
+    words = synth.dna_gc_runs(synth.base_seed(43), n, 0.4, 0.05, 10, 1000)
+    idx = regions_index(words, n, 4, layout)
+    m = 2 * TILE + 4099
+    q = synth.queries(synth.base_seed(44), n, m)
+    for c in range(4):
+        check(idx, words, n, 4, q, c)
+    check(idx, words, n, 4, q, synth.symbols(synth.base_seed(45), m, 4))
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("sigma", [2, 4])
+def test_bad_queries_inside_batch(layout, sigma):
+    from paper_2602_04103_gb300 import capi
+    n = 2 * (S2 if sigma == 2 else S4) + 999
+    words = synth.bits(7, n, 0.3) if sigma == 2 else synth.dna_uniform(8, n)
+    idx = regions_index(words, n, sigma, layout)
+    m = TILE + 500
+    q = synth.queries(synth.base_seed(46), n, m)
+    q[::97] = n + 1 + np.arange(q[::97].size, dtype=np.uint64)   # out of range
+    q[5] = U64MAX
+    q[6] = n                                                     # largest valid position
+    check(idx, words, n, sigma, q, 1, status=capi.QR_ERANGE)
+    cv = synth.symbols(synth.base_seed(47), m, sigma)
+    cv[::89] = sigma                                             # bad symbols
+    cv[3] = 255
+    q2 = synth.queries(synth.base_seed(48), n, m)
+    check(idx, words, n, sigma, q2, cv, status=capi.QR_EBADSYM)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("order", ["equal", "sorted", "reversed", "first_region", "last_region", "zero", "n"])
+def test_degenerate_orders(layout, order):
+    n = 5 * S2 + 17
+    words = synth.bits(synth.base_seed(49), n, 0.5)
+    idx = regions_index(words, n, 2, layout)
+    m = 2 * TILE + 333
+    q = synth.queries(synth.base_seed(50), n, m)
+    if order == "equal":
+        q[:] = q[0]
+    elif order == "sorted":
+        q.sort()
+    elif order == "reversed":
+        q = np.sort(q)[::-1].copy()
+    elif order == "first_region":
+        q = q % np.uint64(max(1, n >> 9))
+    elif order == "last_region":
+        q = np.uint64(n) - q % np.uint64(max(1, n >> 9))
+    elif order == "zero":
+        q[:] = 0
+    else:
+        q[:] = n
+    check(idx, words, n, 2, q, 1)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("n", [0, 1, 2, 255, 256, 257, 495, 496, 497, 1000])
+def test_tiny_texts(layout, n):
+    """Texts shorter than 256 regions: a region is one or a few positions."""
+    words = synth.bits(n + 11, n, 0.5)
+    idx = regions_index(words, n, 2, layout)
+    q = np.concatenate([np.arange(n + 1, dtype=np.uint64), synth.queries(n + 12, n, 3000)])
+    for c in (0, 1):
+        check(idx, words, n, 2, q, c)
+    dwords = synth.dna_uniform(n + 13, n)
+    idx4 = regions_index(dwords, n, 4, layout)
+    check(idx4, dwords, n, 4, q, synth.symbols(n + 14, q.size, 4))
+
+
+@pytest.mark.parametrize("m", [1, 2, 31, 32, 33, TILE - 1, TILE, TILE + 1, 2 * TILE])
+def test_batch_sizes(m):
+    n = 2 * S2 + 5
+    words = synth.bits(synth.base_seed(51), n, 0.5)
+    for layout in LAYOUTS:
+        idx = regions_index(words, n, 2, layout)
+        check(idx, words, n, 2, synth.queries(synth.base_seed(52) + m, n, m), 1)
+
+
+def test_empty_batch():
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1000
+    idx = regions_index(synth.bits(3, n, 0.5), n, 2, 0)
+    empty = torch.empty(0, dtype=torch.int64, device="cuda")
+    capi.qr_rank(idx, empty, 1, empty)
+    assert capi.qr_status(idx) == 0
+
+
+def test_agrees_with_direct_large_batch():
+    """2^22 queries over a 2^30-bit text (138 MB index, larger than half of L2):
+    region batching and the direct kernels agree on every output, and a
+    sample matches the oracle.  The automatic rule picks region batching here."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 30
+    words = synth.bits(synth.base_seed(53), n, 0.5)
+    q = synth.queries(synth.base_seed(54), n, 1 << 22)
+    dq = dev_u64(q)
+    for layout in LAYOUTS:
+        idx = build(words, n, 2, layout)
+        assert capi.qr_rank_plan(idx, q.size) == capi.QR_BATCH_REGIONS
+        assert capi.qr_rank_plan(idx, 1 << 16) == capi.QR_BATCH_DIRECT
+        a, b = torch.empty_like(dq), torch.empty_like(dq)
+        capi.qr_rank(idx, dq, 1, a)                      # automatic: regions
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
+        assert capi.qr_rank_plan(idx, q.size) == capi.QR_BATCH_DIRECT
+        capi.qr_rank(idx, dq, 1, b)
+        assert torch.equal(a, b), layout
+        sample = np.arange(0, q.size, 997)
+        want, rc = oracle.rank(words, n, 2, q[sample], 1)
+        assert rc == 0 and np.array_equal(host_u64(a)[sample], want)
+        assert capi.qr_status(idx) == 0
+        idx.free()
+
+
+@pytest.mark.parametrize("order", ["sorted", "equal", "half_sorted"])
+def test_auto_clustered_batches(order):
+    """Under the automatic rule a device probe sends clustered batches to the
+    direct kernels (and the region passes return at once); the outputs are
+    the same whichever path runs."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 30
+    words = synth.bits(synth.base_seed(58), n, 0.5)
+    q = synth.queries(synth.base_seed(59), n, 1 << 22)
+    if order == "sorted":
+        q.sort()
+    elif order == "equal":
+        q[:] = q[7]
+    else:
+        q[: q.size // 2].sort()
+    dq = dev_u64(q)
+    for layout in LAYOUTS:
+        idx = build(words, n, 2, layout)
+        assert capi.qr_rank_plan(idx, q.size) == capi.QR_BATCH_REGIONS
+        a, b = torch.empty_like(dq), torch.empty_like(dq)
+        capi.qr_rank(idx, dq, 0, a)
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
+        capi.qr_rank(idx, dq, 0, b)
+        assert torch.equal(a, b), (order, layout)
+        sample = np.arange(0, q.size, 1009)
+        want, rc = oracle.rank(words, n, 2, q[sample], 0)
+        assert rc == 0 and np.array_equal(host_u64(a)[sample], want)
+        assert capi.qr_status(idx) == 0
+        idx.free()
+
+
+def test_auto_rule_small_index_stays_direct():
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 24   # 2.2 MB index: L2-resident
+    idx = build(synth.bits(5, n, 0.5), n, 2, 0)
+    assert capi.qr_rank_plan(idx, 1 << 26) == capi.QR_BATCH_DIRECT
+    assert capi.qr_rank_plan(idx, 1 << 26, 1) == capi.QR_BATCH_DIRECT
+    capi.qr_set_batch_mode(idx, capi.QR_BATCH_REGIONS)
+    assert capi.qr_rank_plan(idx, 1 << 26) == capi.QR_BATCH_REGIONS
+    assert capi.qr_rank_plan(idx, 1 << 26, 1) == capi.QR_BATCH_DIRECT   # rank_4 always direct
+    idx128 = build(synth.bits(5, n, 0.5), n, 2, 2)
+    capi.qr_set_batch_mode(idx128, capi.QR_BATCH_REGIONS)
+    assert capi.qr_rank_plan(idx128, 1 << 26) == capi.QR_BATCH_DIRECT   # 128-byte lines always direct
+    with pytest.raises(capi.QRError):
+        capi.qr_set_batch_mode(idx, 7)
+
+
+def test_two_streams_and_timing():
+    """Region-batched calls on two streams at once (each with its own pooled
+    scratch), then the per-pass timing aid."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 4 * S2 + 3
+    words = synth.bits(synth.base_seed(55), n, 0.5)
+    idx = regions_index(words, n, 2, 0)
+    qa = synth.queries(synth.base_seed(56), n, 5 * TILE + 1)
+    qb = synth.queries(synth.base_seed(57), n, 3 * TILE + 9)
+    dqa, dqb = dev_u64(qa), dev_u64(qb)
+    oa, ob = torch.empty_like(dqa), torch.empty_like(dqb)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        capi.qr_rank(idx, dqa, 1, oa, stream=sa)
+        capi.qr_rank(idx, dqb, 0, ob, stream=sb)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_u64(oa), expect(words, n, 2, qa, 1))
+    assert np.array_equal(host_u64(ob), expect(words, n, 2, qb, 0))
+    capi.qr_region_timing(idx, True)
+    capi.qr_rank(idx, dqa, 1, oa)
+    ms = capi.qr_region_timing(idx, False, read=True)
+    assert len(ms) == 3 and all(x >= 0 for x in ms)
+    assert np.array_equal(host_u64(oa), expect(words, n, 2, qa, 1))
+    capi.qr_release_scratch()
+    capi.qr_rank(idx, dqa, 1, oa)                     # the pool refills after a release
+    assert np.array_equal(host_u64(oa), expect(words, n, 2, qa, 1))
+    assert capi.qr_status(idx) == 0

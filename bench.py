@@ -226,7 +226,9 @@ def region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream, 
     achieved = pbytes[dom] * m / (pass_ms[dom] * 1e-3) / 1e9
     tr = traffic_record(f"birank_region_{dom}")
     step_bytes = sum(pbytes.values())
-    launches = len(REGION_PASSES)
+    # under the automatic rule every step also launches the probe and the
+    # direct kernel, which returns at once when the probe picks region batching
+    launches = len(REGION_PASSES) + 2
     return ({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
              "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
              "peak_kind": f"of {peak_kind} (copy bandwidth)", "kernel": REGION_KERNELS[dom],
@@ -539,7 +541,14 @@ def run_quadrank(args, stream, peak):
     gq = m / (ms * 1e-3) / 1e9
     bpq = bytes_per_query(4, layout4, tuning4["load_mode"], per_query_c=True)
     res["quadrank_rank_random_c"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": tuning4,
-                                     "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4)}
+                                     "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4),
+                                     "batch_path": "regions" if capi.qr_rank_plan(idx4, m) == capi.QR_BATCH_REGIONS
+                                     else "direct"}
+    # prefix_rank(q, 2): characters <= G before q, same index and queries
+    ms = best_ms(lambda: capi.qr_prefix_rank(idx4, dq, 2, o), stream)
+    res["quadrank_prefix_rank"] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "layout": layout4,
+                                   "batch_path": "regions" if capi.qr_rank_plan(idx4, m, 2) == capi.QR_BATCH_REGIONS
+                                   else "direct"}
     del o
     o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
     t4r = capi.qr_autotune(idx4, dq[: 1 << 24], o4, rank4=True)

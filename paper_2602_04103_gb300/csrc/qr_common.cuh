@@ -401,7 +401,7 @@ bool region_auto(const qr_index* idx, uint64_t m);
 // probe that sets the count, and its passes run only when *count > limit.
 using DirectLaunch = std::function<int(const unsigned long long* count, unsigned long long limit)>;
 int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
-                        cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct);
+                        int rank4, cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct);
 int region_trim();
 int region_tile_queries();
 int region_count_regions();

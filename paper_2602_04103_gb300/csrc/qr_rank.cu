@@ -500,7 +500,7 @@ int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int
             return launch_direct(idx, q, cvec, c, m, out, rank4, s, count, limit);
         };
         cudaEvent_t* marks = idx->region_timing ? (cudaEvent_t*)idx->region_ev : nullptr;
-        const int rc = launch_rank_regions(idx, q, cvec, c, m, out, s, marks,
+        const int rc = launch_rank_regions(idx, q, cvec, c, m, out, rank4, s, marks,
                                            idx->batch_mode == QR_BATCH_AUTO ? &direct : nullptr);
         if (rc != QR_ENOMEM) return rc;  // without scratch memory the direct kernels answer the batch
     }

@@ -266,16 +266,19 @@ constexpr size_t kUnsortSmem = (size_t)kTile * 8;
 // Paper layout (BiRank16 / QuadRank16): the 32-byte half of the line that
 // holds the query's bits, plus the first 8 or 16 bytes (the deltas) when that
 // is the upper half.  Sector layout: the one self-contained half.
-template <bool SECTOR, bool QUAD>
+// PREFIX (sigma 4): prefix_rank(q, c), the sum of the four counts up to c,
+// from all four superblock offsets.
+template <bool SECTOR, bool QUAD, bool PREFIX = false>
 struct RegionLoad {
     u64x4 X;
     uint64_t w0, w1;
     uint32_t s;
+    uint4 s4;
     uint32_t pos;
 };
 
-template <bool SECTOR, bool QUAD>
-__device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD>& L, const uint4* __restrict__ lines,
+template <bool SECTOR, bool QUAD, bool PREFIX = false>
+__device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L, const uint4* __restrict__ lines,
                                              const void* __restrict__ supers, uint64_t q, uint32_t c) {
     if (SECTOR) {
         uint64_t j;
@@ -291,7 +294,8 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD>& L, const 
             const uint32_t d = (uint32_t)(q - j * kB4s);
             h = d >= kHalf4s;
             L.pos = d - h * (uint32_t)kHalf4s;
-            L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+            if (PREFIX) L.s4 = __ldg((const uint4*)supers + (j >> 8));
+            else L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
         }
         L.X = ld_line32(lines + 4 * j + 2 * h);
         L.w0 = L.w1 = 0;
@@ -307,7 +311,8 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD>& L, const 
             j = div224(q);
             L.pos = (uint32_t)(q - j * kB4) + 32;
             upper = L.pos >= 128;
-            L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+            if (PREFIX) L.s4 = __ldg((const uint4*)supers + (j >> 8));
+            else L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
         }
         const uint4* P = lines + 4 * j;
         L.X = ld_line32(P + 2 * upper);
@@ -320,8 +325,23 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD>& L, const 
     }
 }
 
-template <bool SECTOR, bool QUAD>
-__device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD>& L, uint64_t q, uint32_t c) {
+template <bool SECTOR, bool QUAD, bool PREFIX = false>
+__device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD, PREFIX>& L, uint64_t q, uint32_t c) {
+    if (PREFIX) {
+        const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
+        uint64_t r[4];
+        if (SECTOR) {
+            quad_sector_finish4(s4, L.X, L.pos, r);
+        } else {
+            const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
+            const bool upper = L.pos >= 128;
+            quad_finish4(s4, upper ? L.w0 : L.X.a, upper ? L.w1 : L.X.b, x, L.pos, r);
+        }
+        uint64_t sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) sum += k <= c ? r[k] : 0;
+        return sum;
+    }
     if (SECTOR) {
         if (!QUAD) {
             const uint64_t r1 = birank_sector_finish(L.s, L.X, L.pos);
@@ -397,7 +417,7 @@ struct RankPassArgs {
     Gate gate;
 };
 
-template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, bool PF, int SEGS, bool QUEUE>
+template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, bool PF, int SEGS, bool QUEUE, bool PREFIX = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
     if (!regions_chosen(a.gate)) return;
     const int lane = threadIdx.x & 31;
@@ -478,20 +498,20 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                 if (j0 + P * kRound < total)
                     fetch_items<K, SEGS>(S[PS - 1], work, j0 + P * kRound, total, start, sbase, lane);
             }
-            RegionLoad<SECTOR, QUAD> L[K];
+            RegionLoad<SECTOR, QUAD, PREFIX> L[K];
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 const bool bad = cur.it[k] & kBadItem;
                 const uint64_t qq = bad ? 0 : cur.it[k] & kValMask;  // bad items (and idle lanes) read line 0
                 const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                region_issue<SECTOR, QUAD>(L[k], a.lines, a.supers, qq, c);
+                region_issue<SECTOR, QUAD, PREFIX>(L[k], a.lines, a.supers, qq, c);
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 if (cur.it[k] & kBadItem) continue;
                 const uint64_t qq = cur.it[k] & kValMask;
                 const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                const uint64_t r = region_finish<SECTOR, QUAD>(L[k], qq, c);
+                const uint64_t r = region_finish<SECTOR, QUAD, PREFIX>(L[k], qq, c);
                 st_stream_u64(work + cur.at[k], r | (cur.it[k] & kIdxBits));
             }
         }
@@ -555,7 +575,11 @@ RankFn pick_variant(int v) {
     }
 }
 
-RankFn pick_region_rank(bool sector, bool quad, bool vec, int v) {
+RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix) {
+    if (prefix) {  // sigma 4, one symbol, default variant
+        return sector ? region_rank<true, true, false, 2, 4, 1, false, 16, true, true>
+                      : region_rank<false, true, false, 2, 4, 1, false, 16, true, true>;
+    }
     if (sector) {
         if (quad) return vec ? pick_variant<true, true, true>(v) : pick_variant<true, true, false>(v);
         return vec ? pick_variant<true, false, true>(v) : pick_variant<true, false, false>(v);
@@ -567,7 +591,10 @@ RankFn pick_region_rank(bool sector, bool quad, bool vec, int v) {
 }  // namespace
 
 bool region_supported(const qr_index* idx, int rank4) {
-    return rank4 == 0 && idx->layout != QR_LAYOUT_LINE128;
+    // rank_4 stays direct: its four 8-byte results would be moved three times
+    // (about 129 bytes per query in all), no less than the direct kernel's
+    // 168 bytes at the random-fill rate
+    return (rank4 == 0 || (rank4 == 2 && idx->sigma == 4)) && idx->layout != QR_LAYOUT_LINE128;
 }
 
 bool region_auto(const qr_index* idx, uint64_t m) {
@@ -585,7 +612,7 @@ int region_count_regions() { return (int)kRegions; }
 
 
 int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
-                        cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct) {
+                        int rank4, cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct) {
     if (m == 0) return QR_OK;
     if (m >= (1ull << 32)) return fail(QR_EINVAL, "region batch: m must be below 2^32");
     const uint64_t tiles = (m + kTile - 1) / kTile;
@@ -645,7 +672,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc && marks) cudaEventRecord(marks[1], s);
     if (!rc) {
-        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant);
+        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, rank4 == 2);
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;

@@ -99,6 +99,31 @@ def test_dna_tiles_ragged(layout):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
+def test_prefix_rank_tiles_ragged(layout):
+    """prefix_rank (the count of characters at most c before q) through
+    region batching, against the oracle, with out-of-range positions."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 2 * S4 + 4321
+    words = synth.dna_gc_runs(synth.base_seed(60), n, 0.4, 0.05, 10, 1000)
+    idx = regions_index(words, n, 4, layout)
+    m = 2 * TILE + 123
+    q = synth.queries(synth.base_seed(61), n, m)
+    q[::211] = n + 5
+    ok = q <= n
+    assert capi.qr_rank_plan(idx, m, 2) == capi.QR_BATCH_REGIONS
+    dq = dev_u64(q)
+    out = torch.empty_like(dq)
+    for c in range(4):
+        capi.qr_prefix_rank(idx, dq, c, out)
+        got = host_u64(out)
+        want, rc = oracle.prefix_rank(words, n, 4, q[ok], c)
+        assert rc == 0 and np.array_equal(got[ok], want), (layout, c)
+        assert (got[~ok] == U64MAX).all()
+        assert capi.qr_status(idx) == capi.QR_ERANGE
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("sigma", [2, 4])
 def test_bad_queries_inside_batch(layout, sigma):
     from paper_2602_04103_gb300 import capi

@@ -303,10 +303,12 @@ def run_ours(args):
     def step():
         capi.qr_rank(idx, dq, 1, out)
 
-    for _ in range(args.warmup):
-        step()
-    barrier_sync(ws)
+    # the sampler starts first, so that the timed steps follow the warm-up
+    # steps without an idle gap (an idle GPU lowers its clocks)
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        barrier_sync(ws)
         total_ms, per = time_launches(step, args.steps, stream)
         barrier_sync(ws)
     total_ms = max_over_ranks(total_ms, ws)

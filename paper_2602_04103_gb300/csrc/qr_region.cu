@@ -31,8 +31,9 @@
 // pass plus a global scan to place runs region-major (one more read of the
 // queries, and __match_any_sync grouping ran at 1.2 TB/s); blocks walking 64
 // runs with a shared-memory search (barrier-bound); strided warp steps
-// (warps drift apart, the regions in flight outgrow L2); bulk L2 prefetch of
-// the next region's lines and of the next runs (slower).
+// (warps drift apart, the regions in flight outgrow L2); bulk L2 prefetch
+// (cp.async.bulk.prefetch.L2) of the next region's lines and of the next
+// runs (slower).
 //
 // Sorted batches: each tile is one run, so a warp step would hold whole
 // tiles; such batches are sent to the direct kernels by the probe (see Gate).
@@ -360,22 +361,16 @@ __device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD,
     return quad_finish1(L.s, quad_delta(w0, w1, (int)c), x, L.pos, (int)c);
 }
 
-// The rank pass.  Every warp walks its own runs of 32 consecutive segments of
-// the region-major table (warp-steps in table order across the grid, so the
-// whole GPU moves through the regions together): the lengths are scanned
-// with shuffles, the runs' items are laid end to end and each lane answers
-// items lane, lane + 32, ..., K of them per round; the run holding an item
-// is found by a 5-step search over the 32 starts held in the lanes.
-// With PF, two bulk L2 prefetches (the TMA unit's cp.async.bulk.prefetch)
-// keep the loads of a step hitting L2: each warp-step streams its share of
-// the NEXT region's index lines into L2 (sequential DRAM reads instead of
-// first-touch misses), and every lane prefetches the items of its segment of
-// the warp's next step.  The items of round t + P - 1 are loaded while round
-// t fetches its lines and counts.  No shared memory, no block barrier.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
+// The rank pass.  Every warp walks its own runs of SEGS consecutive
+// segments of the region-major table, taking its steps in table order from a
+// device work queue (QUEUE) or by a stride: the lengths are scanned with
+// shuffles, the runs' items are laid end to end and each lane answers items
+// lane, lane + 32, ..., K of them per round; the run holding an item is found
+// by a log2(SEGS)-step search over the starts held in the lanes.  The items
+// of round t + P are loaded while round t fetches its lines and counts, and
+// the table entries of the next step while this step runs.  No shared
+// memory, no block barrier.  With the queue the steps in flight stay close
+// together in the table, so the regions they touch stay in L2.
 template <int K>
 struct ItemSlot {
     uint64_t it[K], at[K];
@@ -408,23 +403,17 @@ struct RankPassArgs {
     const uint4* lines;
     const void* supers;
     uint32_t c0;
-    uint64_t n;             // text length
-    int shift;              // region = q >> shift
-    uint64_t block_chars;   // chars per line
-    uint64_t nblocks;       // lines of the index
-    uint64_t line_bytes;
     unsigned long long* queue;  // step counter (QUEUE variants), zero at launch
     Gate gate;
 };
 
-template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, bool PF, int SEGS, bool QUEUE, bool PREFIX = false>
+template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, bool PREFIX = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
     if (!regions_chosen(a.gate)) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (kRankThreads / 32);
     constexpr int kWarpSegs = SEGS;
     const uint64_t nsteps = (a.nseg + kWarpSegs - 1) / kWarpSegs;
-    const uint64_t parts = (a.tiles + kWarpSegs - 1) / kWarpSegs;  // warp-steps per region (about)
     constexpr uint32_t kRound = 32 * K;
     uint64_t* __restrict__ work = a.work;
     // the warp's next step: a strided sequence, or (QUEUE) taken in table order
@@ -451,30 +440,10 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
     uint64_t sbase;
     seg_of(g, len, sbase);
     while (g < nsteps) {
-        uint32_t nlen = 0;
-        uint64_t nbase = 0;
         const uint64_t gn = next_step(g);
-        if (PF) {
-            seg_of(gn, nlen, nbase);
-            if (nlen) {  // the items of this lane's segment of the next step
-                const uint64_t b0 = (nbase * 8) & ~15ull, b1 = ((nbase + nlen) * 8 + 15) & ~15ull;
-                prefetch_l2((const char*)work + b0, (uint32_t)(b1 - b0));
-            }
-            if (lane == 0) {  // this step's share of the next region's index lines
-                const uint64_t w0 = g * kWarpSegs, r = w0 / a.tiles + 1, part = (w0 % a.tiles) / kWarpSegs;
-                if (r < kRegions && (r << a.shift) <= a.n) {
-                    const uint64_t l0 = (r << a.shift) / a.block_chars;
-                    uint64_t l1 = (((r + 1) << a.shift) - 1) / a.block_chars + 1;
-                    if (l1 > a.nblocks) l1 = a.nblocks;
-                    const uint64_t bytes = (l1 - l0) * a.line_bytes;
-                    const uint64_t chunk = ((bytes + parts - 1) / parts + 127) & ~127ull;
-                    const uint64_t o0 = l0 * a.line_bytes + part * chunk;
-                    uint64_t o1 = o0 + (chunk < (1ull << 20) ? chunk : (1ull << 20));  // a hint: at most 1 MiB
-                    if (o1 > l1 * a.line_bytes) o1 = l1 * a.line_bytes;
-                    if (o0 < o1) prefetch_l2((const char*)a.lines + o0, (uint32_t)(o1 - o0));
-                }
-            }
-        }
+        uint32_t nlen;
+        uint64_t nbase;
+        seg_of(gn, nlen, nbase);  // the next step's table entries, loaded early
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < kWarpSegs; o <<= 1) {
@@ -517,7 +486,6 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
         }
         len = nlen;
         sbase = nbase;
-        if (!PF) seg_of(gn, len, sbase);
         g = gn;
     }
 }
@@ -562,23 +530,23 @@ int set_smem(F fn, size_t bytes) {
 using RankFn = void (*)(RankPassArgs);
 
 // Rank-pass variants (items per lane and round, resident blocks per SM,
-// rounds of items loaded ahead, bulk L2 prefetch, segments per warp-step,
-// steps from a device queue).
+// rounds of items loaded ahead, segments per warp-step, steps from a device
+// queue).
 template <bool SECTOR, bool QUAD, bool VEC>
 RankFn pick_variant(int v) {
     switch (v) {
-        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, false, 16, true>;
-        case 1: return region_rank<SECTOR, QUAD, VEC, 2, 4, 2, false, 16, true>;
-        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, false, 32, true>;
-        case 3: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, true, 16, true>;
+        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true>;
+        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true>;
+        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 5, 1, 16, true>;
+        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true>;
         default: return nullptr;
     }
 }
 
 RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix) {
     if (prefix) {  // sigma 4, one symbol, default variant
-        return sector ? region_rank<true, true, false, 2, 4, 1, false, 16, true, true>
-                      : region_rank<false, true, false, 2, 4, 1, false, 16, true, true>;
+        return sector ? region_rank<true, true, false, 2, 4, 1, 16, true, true>
+                      : region_rank<false, true, false, 2, 4, 1, 16, true, true>;
     }
     if (sector) {
         if (quad) return vec ? pick_variant<true, true, true>(v) : pick_variant<true, true, false>(v);
@@ -661,12 +629,10 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     if (!rc && marks) cudaEventRecord(marks[0], s);
     if (!rc) {
         const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
-        if (vec)
-            region_sort<true><<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(
-                q, cvec, (uint32_t)c, (uint32_t)idx->sigma, m, idx->n, shift, tiles, work, seg, idx->status, gate);
-        else
-            region_sort<false><<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(
-                q, nullptr, (uint32_t)c, (uint32_t)idx->sigma, m, idx->n, shift, tiles, work, seg, idx->status, gate);
+        auto sort_fn = vec ? region_sort<true> : region_sort<false>;
+        sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
+                                                                (uint32_t)idx->sigma, m, idx->n, shift, tiles, work,
+                                                                seg, idx->status, gate);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_sort");
     }
@@ -688,11 +654,6 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         ra.lines = idx->lines;
         ra.supers = idx->supers;
         ra.c0 = (uint32_t)c;
-        ra.n = idx->n;
-        ra.shift = shift;
-        ra.block_chars = block_chars(idx->sigma, idx->layout);
-        ra.nblocks = idx->nblocks;
-        ra.line_bytes = line_bytes(idx->layout);
         ra.queue = counters;
         ra.gate = gate;
         fn<<<(unsigned)grid, kRankThreads, 0, s>>>(ra);

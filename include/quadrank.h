@@ -307,10 +307,11 @@ int qr_rank_plan(const qr_index* idx, uint64_t m, int rank4, int* plan);
  * handle.  Errors: QR_EINVAL (ms3 before timing was enabled), QR_ECUDA. */
 int qr_region_timing(qr_index* idx, int enable, float* ms3);
 
-/* Launch tuning of the rank pass of region batching: variant 0..3 picks
- * the items in flight per lane, the resident blocks per SM, how far ahead
- * work items are loaded, the sorted runs per warp-step and whether steps are
- * handed out by a device queue.  Errors: QR_EINVAL. */
+/* Launch tuning of the rank pass of region batching: variant 0..3 =
+ * (items in flight per lane, resident blocks of 256 threads per SM, rounds
+ * of work items loaded ahead) of (2, 4, 1) (default), (1, 6, 2), (2, 4, 1)
+ * with the index lines loaded under an L2 evict-last policy, (4, 3, 1).
+ * Errors: QR_EINVAL. */
 int qr_set_region_tuning(qr_index* idx, int variant);
 
 /* Return the pooled scratch memory of region batching to the device (on every

@@ -50,6 +50,7 @@ namespace {
 constexpr uint32_t kTile = 8192;    // queries per tile
 constexpr uint32_t kRegions = 256;  // regions of the text
 constexpr int kPassThreads = 512;   // sort / unsort
+constexpr int kPassBlocks = 2;      // resident sort / unsort blocks per SM
 constexpr int kPer = kTile / kPassThreads;
 constexpr int kRankThreads = 256;
 
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) region_probe(const uint64_t* __restrict__
 // phase reads the tile's queries again (L2 hits) rather than keeping 16 of
 // them per thread in registers across the block-wide scan.
 template <bool VEC>
-__global__ void __launch_bounds__(kPassThreads, 2) region_sort(const uint64_t* __restrict__ q,
+__global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const uint64_t* __restrict__ q,
                                                                const uint8_t* __restrict__ cv, uint32_t c0,
                                                                uint32_t sigma, uint64_t m, uint64_t n, int shift,
                                                                uint64_t tiles, uint64_t* __restrict__ work,
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) region_sort(const uint64_t* _
 constexpr size_t kSortSmem = (size_t)kTile * 10 + (kRegions + 8) * 4;
 
 // ---------------------------------------------------------------- unsort
-__global__ void __launch_bounds__(kPassThreads, 2) region_unsort(const uint64_t* __restrict__ work, uint64_t m,
+__global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_unsort(const uint64_t* __restrict__ work, uint64_t m,
                                                                  uint64_t tiles, uint64_t* __restrict__ out,
                                                                  Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -278,9 +279,26 @@ struct RegionLoad {
     uint32_t pos;
 };
 
-template <bool SECTOR, bool QUAD, bool PREFIX = false>
+// EL: index lines and superblock entries are loaded with an L2 evict-last
+// policy (pol), so that they outlive the streaming work items until the
+// region's other queries have used them.
+template <bool EL>
+__device__ __forceinline__ u64x4 ix_ld32(const uint4* p, uint64_t pol) {
+    return EL ? ld_line32_hint(p, pol) : ld_line32(p);
+}
+template <bool EL>
+__device__ __forceinline__ uint4 ix_ld16(const uint4* p, uint64_t pol) {
+    return EL ? ld_line16_hint(p, pol) : ld_line16(p);
+}
+template <bool EL>
+__device__ __forceinline__ uint32_t ix_ld_u32(const uint32_t* p, uint64_t pol) {
+    return EL ? ld_u32_hint(p, pol) : __ldg(p);
+}
+
+template <bool SECTOR, bool QUAD, bool PREFIX = false, bool EL = false>
 __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L, const uint4* __restrict__ lines,
-                                             const void* __restrict__ supers, uint64_t q, uint32_t c) {
+                                             const void* __restrict__ supers, uint64_t q, uint32_t c,
+                                             uint64_t pol = 0) {
     if (SECTOR) {
         uint64_t j;
         uint32_t h;
@@ -289,16 +307,16 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L
             const uint32_t p = (uint32_t)(q - j * kB2s);
             h = p >= kHalf2s;
             L.pos = p - h * (uint32_t)kHalf2s;
-            L.s = __ldg((const uint32_t*)supers + (j >> 7));
+            L.s = ix_ld_u32<EL>((const uint32_t*)supers + (j >> 7), pol);
         } else {
             j = div192(q);
             const uint32_t d = (uint32_t)(q - j * kB4s);
             h = d >= kHalf4s;
             L.pos = d - h * (uint32_t)kHalf4s;
             if (PREFIX) L.s4 = __ldg((const uint4*)supers + (j >> 8));
-            else L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+            else L.s = ix_ld_u32<EL>((const uint32_t*)supers + 4 * (j >> 8) + c, pol);
         }
-        L.X = ld_line32(lines + 4 * j + 2 * h);
+        L.X = ix_ld32<EL>(lines + 4 * j + 2 * h, pol);
         L.w0 = L.w1 = 0;
     } else {
         uint64_t j;
@@ -307,19 +325,19 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L
             j = div496(q);
             L.pos = (uint32_t)(q - j * kB2);
             upper = L.pos >= kMid2;
-            L.s = __ldg((const uint32_t*)supers + (j >> 7));
+            L.s = ix_ld_u32<EL>((const uint32_t*)supers + (j >> 7), pol);
         } else {
             j = div224(q);
             L.pos = (uint32_t)(q - j * kB4) + 32;
             upper = L.pos >= 128;
             if (PREFIX) L.s4 = __ldg((const uint4*)supers + (j >> 8));
-            else L.s = __ldg((const uint32_t*)supers + 4 * (j >> 8) + c);
+            else L.s = ix_ld_u32<EL>((const uint32_t*)supers + 4 * (j >> 8) + c, pol);
         }
         const uint4* P = lines + 4 * j;
-        L.X = ld_line32(P + 2 * upper);
+        L.X = ix_ld32<EL>(P + 2 * upper, pol);
         L.w0 = L.w1 = 0;
         if (upper) {
-            const uint4 d = ld_line16(P);
+            const uint4 d = ix_ld16<EL>(P, pol);
             L.w0 = lo64(d);
             L.w1 = hi64(d);
         }
@@ -407,7 +425,8 @@ struct RankPassArgs {
     Gate gate;
 };
 
-template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, bool PREFIX = false>
+template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, bool PREFIX = false,
+          bool EL = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
     if (!regions_chosen(a.gate)) return;
     const int lane = threadIdx.x & 31;
@@ -416,6 +435,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
     const uint64_t nsteps = (a.nseg + kWarpSegs - 1) / kWarpSegs;
     constexpr uint32_t kRound = 32 * K;
     uint64_t* __restrict__ work = a.work;
+    const uint64_t pol = EL ? l2_policy_evict_last() : 0;
     // the warp's next step: a strided sequence, or (QUEUE) taken in table order
     // from a device counter, so that the steps in flight stay close together
     auto next_step = [&](uint64_t cur) -> uint64_t {
@@ -473,7 +493,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                 const bool bad = cur.it[k] & kBadItem;
                 const uint64_t qq = bad ? 0 : cur.it[k] & kValMask;  // bad items (and idle lanes) read line 0
                 const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                region_issue<SECTOR, QUAD, PREFIX>(L[k], a.lines, a.supers, qq, c);
+                region_issue<SECTOR, QUAD, PREFIX, EL>(L[k], a.lines, a.supers, qq, c, pol);
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -531,13 +551,14 @@ using RankFn = void (*)(RankPassArgs);
 
 // Rank-pass variants (items per lane and round, resident blocks per SM,
 // rounds of items loaded ahead, segments per warp-step, steps from a device
-// queue).
+// queue, evict-last index loads).  Measured on GB300 (2^28 uniform queries,
+// sector layout): 0 1.78 ms, 1 2.11 ms, 2 1.78 ms, 3 1.91 ms.
 template <bool SECTOR, bool QUAD, bool VEC>
 RankFn pick_variant(int v) {
     switch (v) {
         case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true>;
         case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true>;
-        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 5, 1, 16, true>;
+        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, true>;
         case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true>;
         default: return nullptr;
     }
@@ -628,7 +649,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc && marks) cudaEventRecord(marks[0], s);
     if (!rc) {
-        const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
+        const uint64_t grid = tiles < (uint64_t)sms * kPassBlocks ? tiles : (uint64_t)sms * kPassBlocks;
         auto sort_fn = vec ? region_sort<true> : region_sort<false>;
         sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
                                                                 (uint32_t)idx->sigma, m, idx->n, shift, tiles, work,
@@ -662,7 +683,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc && marks) cudaEventRecord(marks[2], s);
     if (!rc) {
-        const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
+        const uint64_t grid = tiles < (uint64_t)sms * kPassBlocks ? tiles : (uint64_t)sms * kPassBlocks;
         region_unsort<<<(unsigned)grid, kPassThreads, kUnsortSmem, s>>>(work, m, tiles, out, gate);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort");

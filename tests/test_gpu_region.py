@@ -182,7 +182,7 @@ def test_tiny_texts(layout, n):
     check(idx4, dwords, n, 4, q, synth.symbols(n + 14, q.size, 4))
 
 
-@pytest.mark.parametrize("m", [1, 2, 31, 32, 33, TILE - 1, TILE, TILE + 1, 2 * TILE])
+@pytest.mark.parametrize("m", [1, 2, 31, 32, 33, 4095, 4096, 4097, TILE - 1, TILE, TILE + 1, 2 * TILE + 1])
 def test_batch_sizes(m):
     n = 2 * S2 + 5
     words = synth.bits(synth.base_seed(51), n, 0.5)

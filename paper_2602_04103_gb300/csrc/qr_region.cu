@@ -614,7 +614,14 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     const size_t work_bytes = (m * 8 + 255) & ~(size_t)255;
     const size_t seg_bytes = (nseg * 4 + 255) & ~(size_t)255;
     void* buf = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&buf, work_bytes + seg_bytes + 16, pool, s);
+    // under stream capture the scratch becomes a graph memory node
+    // (cudaMallocAsync); otherwise it comes from the library's pool
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "region batch: capture status");
+    const size_t scratch = work_bytes + seg_bytes + 16;
+    e = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&buf, scratch, s)
+                                             : cudaMallocFromPoolAsync(&buf, scratch, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(QR_ENOMEM, "region batch: no scratch memory");

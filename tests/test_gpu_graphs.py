@@ -74,3 +74,38 @@ def test_qfm_count_in_cuda_graph():
     sub = np.concatenate([pats[off[k]:off[k + 1]] for k in sample])
     sub_off = np.concatenate([[0], np.cumsum((off[sample + 1] - off[sample]).astype(np.int64))]).astype(np.uint64)
     assert np.array_equal(want[sample], oracle.count_brute_batch(t, sub, sub_off))
+
+
+@pytest.mark.parametrize("mode", ["regions", "auto"])
+def test_region_batching_in_cuda_graph(mode):
+    """Region batching under capture: its scratch becomes a graph memory node,
+    and the probe of the automatic rule runs inside the graph."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    torch.cuda.set_device(0)
+    if mode == "regions":
+        n, m = 3 * 63488 + 17, 3 * 8192 + 5
+    else:
+        n, m = 1 << 30, 1 << 22          # 143 MB index, 2^22 queries: the automatic rule picks region batching
+    words = synth.bits(321, n, 0.5)
+    q = synth.queries(322, n, m)
+    idx = capi.qr_build(dev_u64(words), n, 2, layout=1)
+    if mode == "regions":
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_REGIONS)
+    assert capi.qr_rank_plan(idx, m) == capi.QR_BATCH_REGIONS
+    dq = dev_u64(q)
+    out = torch.empty_like(dq)
+    capi.qr_rank(idx, dq, 1, out)          # first call outside capture (per-device set-up)
+    torch.cuda.synchronize()
+    want = host_u64(out).copy()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        capi.qr_rank(idx, dq, 1, out)
+    for _ in range(2):
+        out.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host_u64(out), want)
+    sample = np.arange(0, m, 101)
+    assert np.array_equal(want[sample], oracle.rank(words, n, 2, q[sample], 1)[0])
+    assert capi.qr_status(idx) == 0

@@ -566,9 +566,11 @@ def run_quadrank(args, stream, peak):
     return res
 
 
-def run_fm(args, stream):
+def run_fm(args, stream, part="all"):
     """QuadFm count over the 2^26-char text, 10^7 patterns of length 16..150:
-    one persistent launch vs one launch per search step."""
+    one persistent launch vs one launch per search step; then locate and
+    approximate counts.  part = "locate" or "approx" runs the persistent count
+    and that row alone (few launches: profiling runs)."""
     import torch
     from paper_2602_04103_gb300 import capi, workloads
     text, pats, off = workloads.fm_inputs(args.fm_log_n, args.fm_m)
@@ -585,6 +587,14 @@ def run_fm(args, stream):
     o = torch.empty(m, dtype=torch.int64, device="cuda")
     ms_p = best_ms(lambda: capi.qfm_count(fidx, dp, doff, o), stream)
     ref = o.clone()
+    if part != "all":
+        res = {"qfm_count_persistent": {"patterns_per_s": round(m / (ms_p * 1e-3)), "ms": round(ms_p, 3)}}
+        fidx.free()
+        if part == "locate":
+            res.update(fm_locate_row(dt, text.size, dp, doff, m, ref, ms_p, stream))
+        else:
+            res.update(fm_approx_row(dt, text.size, dp, doff, ref, stream))
+        return res
     ms_s = best_ms(lambda: capi.qfm_count_stepwise(fidx, dp, doff, o), stream)
     assert torch.equal(ref, o)
     # both strands in one launch (the paper's read-counting benchmark counts each read forward
@@ -608,10 +618,18 @@ def run_fm(args, stream):
         res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_config4.json)"
     log(f"[bench] qfm: persistent {m / ms_p / 1e3:.1f} M/s, stepwise {m / ms_s / 1e3:.1f} M/s")
     fidx.free()
-    # locate: the same text indexed with suffix-array sampling factor 32; every
-    # occurrence of all 10^7 patterns (count with intervals, scan, LF walks)
+    res.update(fm_locate_row(dt, text.size, dp, doff, m, ref, ms_p, stream))
+    res.update(fm_approx_row(dt, text.size, dp, doff, ref, stream))
+    return res
+
+
+def fm_locate_row(dt, n, dp, doff, m, ref, ms_p, stream):
+    """Locate every occurrence of all patterns on the same text indexed with
+    suffix-array sampling factor 32 (count with intervals, scan, LF walks)."""
+    import torch
+    from paper_2602_04103_gb300 import capi
     sample = 32
-    lidx = capi.qfm_build(dt, text.size, 0, sa_sample=sample)
+    lidx = capi.qfm_build(dt, n, 0, sa_sample=sample)
     linfo = capi.qfm_info(lidx)
     occ = torch.empty(m + 1, dtype=torch.int64, device="cuda")
     total = capi.qfm_locate(lidx, dp, doff, occ)
@@ -619,31 +637,36 @@ def run_fm(args, stream):
     ms_l = best_ms(lambda: capi.qfm_locate(lidx, dp, doff, occ, pos), stream)
     assert torch.equal(occ[1:] - occ[:-1], ref)
     assert capi.qfm_status(lidx) == 0
-    res["qfm_locate"] = {"patterns_per_s": round(m / (ms_l * 1e-3)), "occurrences": total,
-                         "occurrences_per_s": round(total / (ms_l * 1e-3)), "ms": round(ms_l, 3),
-                         "ms_beyond_count": round(ms_l - ms_p, 3), "sa_sample": sample,
-                         "bytes_locate": linfo["bytes_locate"],
-                         "note": "whole qfm_locate call: count with intervals, scan, total read-back, one "
-                                 "thread per occurrence walking at most 31 LF steps"}
+    row = {"patterns_per_s": round(m / (ms_l * 1e-3)), "occurrences": total,
+           "occurrences_per_s": round(total / (ms_l * 1e-3)), "ms": round(ms_l, 3),
+           "ms_beyond_count": round(ms_l - ms_p, 3), "sa_sample": sample, "bytes_locate": linfo["bytes_locate"],
+           "note": "whole qfm_locate call: count with intervals, scan, total read-back, one thread per "
+                   "occurrence walking at most 31 LF steps"}
     log(f"[bench] qfm locate: {total} occurrences in {ms_l:.3f} ms")
     lidx.free()
-    # approximate counts (at most k substitutions) on leading subsets of the
-    # same patterns: rank_4 of both interval ends at every search node
-    fidx = capi.qfm_build(dt, text.size)
-    res["qfm_count_approx"] = {}
+    return {"qfm_locate": row}
+
+
+def fm_approx_row(dt, n, dp, doff, ref, stream):
+    """Approximate counts (at most k substitutions) on leading subsets of the
+    patterns: rank_4 of both interval ends at every search node."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    fidx = capi.qfm_build(dt, n)
+    rows = {}
     for k, mk in [(0, 10 ** 6), (1, 10 ** 6), (2, 10 ** 5)]:
+        mk = min(mk, ref.numel())
         ok = doff[: mk + 1]
         oa = torch.empty(mk, dtype=torch.int64, device="cuda")
         ms_a = best_ms(lambda: capi.qfm_count_approx(fidx, dp, ok, k, oa), stream)
         if k == 0:
             assert torch.equal(oa, ref[:mk])
-        res["qfm_count_approx"][f"k={k}"] = {"patterns": mk, "patterns_per_s": round(mk / (ms_a * 1e-3)),
-                                             "ms": round(ms_a, 3),
-                                             "mean_count": round(float(oa.double().mean()), 3)}
+        rows[f"k={k}"] = {"patterns": mk, "patterns_per_s": round(mk / (ms_a * 1e-3)), "ms": round(ms_a, 3),
+                          "mean_count": round(float(oa.double().mean()), 3)}
         log(f"[bench] qfm approx k={k}: {mk / ms_a / 1e3:.2f} M patterns/s")
     assert capi.qfm_status(fidx) == 0
     fidx.free()
-    return res
+    return {"qfm_count_approx": rows}
 
 
 def run_serving(args):
@@ -767,15 +790,15 @@ def main():
     ap.add_argument("--serve-log-n", type=int, default=28)
     ap.add_argument("--serve-stream-calls", action="store_true",
                     help="also run the batching server without CUDA graphs")
-    ap.add_argument("--only", choices=["fm", "quadrank", "serving", "probe", "layouts"], default=None,
-                    help="run one extra row alone and print it (profiling runs)")
+    ap.add_argument("--only", choices=["fm", "fm_locate", "fm_approx", "quadrank", "serving", "probe", "layouts"],
+                    default=None, help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
         stream = torch.cuda.current_stream()
-        if args.only == "fm":
-            res = run_fm(args, stream)
+        if args.only in ("fm", "fm_locate", "fm_approx"):
+            res = run_fm(args, stream, part=args.only[3:] or "all")
         elif args.only == "serving":
             res = run_serving(args)
         elif args.only == "layouts":

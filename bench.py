@@ -662,7 +662,8 @@ def fm_approx_row(dt, n, dp, doff, ref, stream):
         if k == 0:
             assert torch.equal(oa, ref[:mk])
         rows[f"k={k}"] = {"patterns": mk, "patterns_per_s": round(mk / (ms_a * 1e-3)), "ms": round(ms_a, 3),
-                          "mean_count": round(float(oa.double().mean()), 3)}
+                          "mean_count": round(float(oa.double().mean()), 3),
+                          "kernel": "count_persistent (exact)" if k == 0 else "count_approx_kernel"}
         log(f"[bench] qfm approx k={k}: {mk / ms_a / 1e3:.2f} M patterns/s")
     assert capi.qfm_status(fidx) == 0
     fidx.free()

@@ -58,7 +58,8 @@ int qfm_build(const uint8_t* codes, uint64_t n, int codes_on_device, int flags, 
  * extends its interval by all four characters from rank_4 of both ends; the
  * prefix table is not used (a mismatch may fall in the last 8 characters).
  * One persistent launch with a device work queue, as qfm_count.
- *   max_mismatches  0..3 (0 gives the exact counts of qfm_count).
+ *   max_mismatches  0..3 (0 gives the exact counts of qfm_count, and runs
+ *                   its kernel).
  * The empty pattern counts n + 1.  A pattern holding a byte > 3 anywhere, or
  * with out-of-order offsets, yields 0 and sets QR_EBADSYM.  The work grows
  * with the number of strings within the distance that occur in T: about

@@ -238,7 +238,11 @@ extern "C" int qfm_count_approx(qfm_index* idx, const uint8_t* patterns, const u
     QR_CUDA_TRY(cudaMallocAsync((void**)&queue, 16, s));
     cudaError_t e = cudaMemsetAsync(queue, 0, 16, s);
     int rc = QR_OK;
-    if (e == cudaSuccess) rc = launch_count_approx(idx, patterns, offsets, m, (uint32_t)max_mismatches, out, queue, s);
+    // no substitution allowed: the exact count (prefix table, one rank per end)
+    if (e == cudaSuccess)
+        rc = max_mismatches == 0
+                 ? launch_count(idx, patterns, offsets, m, out, queue, s, 1)
+                 : launch_count_approx(idx, patterns, offsets, m, (uint32_t)max_mismatches, out, queue, s);
     cudaFreeAsync(queue, s);
     if (e != cudaSuccess) return cuda_fail(e, "qfm_count_approx: queue reset");
     return rc;

@@ -571,3 +571,30 @@ def test_probe_gather_rejects_quad_mode_on_small_records():
     out = torch.zeros(16, dtype=torch.int64, device="cuda")
     with pytest.raises(RuntimeError):
         capi.qr_probe_gather(buf, 128, 64, 16, 7, out, 1, 256, load_bytes=128)
+
+
+def test_small_configuration_every_output():
+    """The small BiRank configuration: n = 2^24 i.i.d. bits (p = 0.5), 10^6
+    uniform queries in [0, n]; every output of every layout and of the tuned
+    build, both symbols, against the oracle's linear prefix sweep."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    n = 1 << 24
+    words = synth.bits(synth.base_seed(1), n, 0.5)
+    q = synth.queries(synth.substream(synth.base_seed(1), 2), n, 10 ** 6)
+    want1, rc = oracle.rank(words, n, 2, q, 1)
+    assert rc == 0
+    want0 = q - want1
+    dq = dev_u64(q)
+    out = torch.empty_like(dq)
+    for layout in LAYOUTS:
+        idx = build(words, n, 2, layout)
+        for c, want in ((1, want1), (0, want0)):
+            capi.qr_rank(idx, dq, c, out)
+            assert np.array_equal(host_u64(out), want), (layout, c)
+        assert capi.qr_status(idx) == 0
+        idx.free()
+    idx, layout, _ = workloads.build_tuned(dev_u64(words), n, 2, dq, c=1)
+    capi.qr_rank(idx, dq, 1, out)
+    assert np.array_equal(host_u64(out), want1), layout
+    idx.free()

@@ -403,8 +403,6 @@ using DirectLaunch = std::function<int(const unsigned long long* count, unsigned
 int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                         int rank4, cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct);
 int region_trim();
-int region_tile_queries();
-int region_count_regions();
 int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
                  int k, int threads, cudaStream_t s);
 }  // namespace qr

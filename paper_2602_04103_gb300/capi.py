@@ -78,6 +78,7 @@ _sig("qr_rank_plan", [vp, u64, i32, C.POINTER(C.c_int)])
 _sig("qr_region_timing", [vp, i32, C.POINTER(C.c_float)])
 _sig("qr_release_scratch", [])
 _sig("qr_set_region_tuning", [vp, i32])
+_sig("qr_set_region_fault", [vp, i32])
 
 
 def _check(rc: int, where: str) -> None:
@@ -246,6 +247,10 @@ def qr_region_timing(idx: QRIndex, enable: bool, read: bool = False) -> list[flo
 
 def qr_set_region_tuning(idx: QRIndex, variant: int = 0) -> None:
     _check(lib.qr_set_region_tuning(idx, variant), "qr_set_region_tuning")
+
+
+def qr_set_region_fault(idx: QRIndex, withhold: bool) -> None:
+    _check(lib.qr_set_region_fault(idx, int(withhold)), "qr_set_region_fault")
 
 
 def qr_release_scratch() -> None:

@@ -477,6 +477,12 @@ int qr_set_region_tuning(qr_index* idx, int variant) {
     return QR_OK;
 }
 
+int qr_set_region_fault(qr_index* idx, int withhold) {
+    if (!idx) return fail(QR_EINVAL, "qr_set_region_fault: NULL index");
+    idx->region_withhold = withhold != 0;
+    return QR_OK;
+}
+
 int qr_release_scratch(void) { return region_trim(); }
 
 int qr_status(qr_index* idx, void* stream) {

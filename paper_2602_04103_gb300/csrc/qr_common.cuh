@@ -367,6 +367,7 @@ struct qr_index {
     int batch_mode = QR_BATCH_AUTO;  // direct kernels or region batching (qr_set_batch_mode)
     int region_variant = 0;          // rank pass launch variant, 0..3 (qr_set_region_tuning)
     bool region_timing = false;      // record events between the region passes
+    int region_withhold = 0;         // test hook (qr_set_region_fault)
     cudaEvent_t region_ev[4] = {};
     // host-buffer pipeline (lazy): kPipe streams, one staging slot each
     static constexpr int kPipe = 4;

@@ -101,11 +101,17 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, int nw, uint32_t* ws,
 // direct kernel and the three region passes are all launched, and each reads
 // the count first and returns at once unless it is the path chosen.
 // gate == NULL: no probe, run unconditionally.
+// abort: set by the sort pass when one of its bounded waits expires (its
+// work array is then incomplete), so that the rank and unsort passes return
+// at once instead of reading it.
 struct Gate {
     const unsigned long long* count;
     unsigned long long limit;  // clustered when *count <= limit
+    unsigned long long* abort;
 };
-__device__ __forceinline__ bool regions_chosen(const Gate& g) { return !g.count || *g.count > g.limit; }
+__device__ __forceinline__ bool regions_chosen(const Gate& g) {
+    return (!g.count || *g.count > g.limit) && !(g.abort && *(volatile unsigned long long*)g.abort);
+}
 
 constexpr int kProbeTiles = 64;     // tiles probed
 constexpr int kProbeQueries = 1024; // leading queries of each probed tile
@@ -260,11 +266,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// at most 2^22 polls (each may suspend for a short while): far beyond the
-// microseconds a 64 KB copy takes, and finite
+// A wait gives up after 0.25 s of the GPU's global timer (a 64 KB copy takes
+// microseconds) or 2^26 polls, whichever comes first.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t kWaitNs = 250000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); it++)
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); it++) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
@@ -294,7 +309,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
                                                                    uint32_t sigma, uint64_t m, uint64_t n, int shift,
                                                                    uint64_t tiles, uint64_t* __restrict__ work,
                                                                    uint32_t* __restrict__ seg, uint32_t* status,
-                                                                   Gate gate) {
+                                                                   Gate gate, int withhold) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* raw0 = (uint64_t*)smem;                        // queries of the tile, in order (two buffers)
     uint64_t* raw1 = raw0 + kTile;
@@ -317,7 +332,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
     }
     __syncthreads();
     uint64_t t = blockIdx.x;
-    if (threadIdx.x == 0 && full(t)) {
+    // withhold (test hook): block 0 never issues its first load, so its first
+    // wait runs out and the timeout path is taken
+    if (threadIdx.x == 0 && full(t) && !(withhold && blockIdx.x == 0)) {
         mbar_expect_tx(&bar[0], kTile * 8);
         bulk_load(raw0, q + t * kTile, kTile * 8, &bar[0]);
     }
@@ -344,6 +361,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
             }
             if (full(t) && !mbar_wait_bounded(&bar[b], (j >> 1) & 1)) {
                 atomicOr(status, kStatusTimeout);
+                if (gate.abort) *(volatile unsigned long long*)gate.abort = 1;
                 s_abort = 1;
             }
         }
@@ -385,6 +403,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
             bulk_wait_read_all();  // the previous tile's store has read `stage`
             if (VEC && full(t) && !mbar_wait_bounded(&bar[2], j & 1)) {
                 atomicOr(status, kStatusTimeout);
+                if (gate.abort) *(volatile unsigned long long*)gate.abort = 1;
                 s_abort = 1;
             }
         }
@@ -810,7 +829,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(e, "region batch: capture status");
-    const size_t scratch = work_bytes + seg_bytes + 16;
+    const size_t scratch = work_bytes + seg_bytes + 32;
     e = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&buf, scratch, s)
                                              : cudaMallocFromPoolAsync(&buf, scratch, pool, s);
     if (e != cudaSuccess) {
@@ -819,7 +838,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     uint64_t* work = (uint64_t*)buf;
     uint32_t* seg = (uint32_t*)((char*)buf + work_bytes);
-    unsigned long long* counters = (unsigned long long*)((char*)buf + work_bytes + seg_bytes);  // queue, probe
+    unsigned long long* counters = (unsigned long long*)((char*)buf + work_bytes + seg_bytes);  // queue, probe, abort
     static std::once_flag once[64];
     static int once_rc[64];
     const int dev = device_props().device & 63;
@@ -833,9 +852,9 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     rc = once_rc[dev];
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR, vec = cvec != nullptr;
     const int sms = device_props().sms;
-    Gate gate{nullptr, 0};
+    Gate gate{nullptr, 0, counters + 2};
     if (!rc) {
-        e = cudaMemsetAsync(counters, 0, 16, s);
+        e = cudaMemsetAsync(counters, 0, 24, s);
         if (e != cudaSuccess) rc = cuda_fail(e, "region batch: counter reset");
     }
     if (!rc && direct) {
@@ -844,7 +863,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         region_probe<<<(unsigned)probes, 256, 0, s>>>(q, m, shift, tiles, counters + 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_probe");
-        gate = Gate{counters + 1, (unsigned long long)probes * kClusterMax};
+        gate = Gate{counters + 1, (unsigned long long)probes * kClusterMax, counters + 2};
         if (!rc) rc = (*direct)(gate.count, gate.limit);
     }
     if (!rc && marks) cudaEventRecord(marks[0], s);
@@ -857,7 +876,8 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
             auto sort_fn = vec ? region_sort_tma<true> : region_sort_tma<false>;
             sort_fn<<<(unsigned)g1, kTmaThreads, kSortTmaSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
                                                                      (uint32_t)idx->sigma, m, idx->n, shift, tiles,
-                                                                     work, seg, idx->status, gate);
+                                                                     work, seg, idx->status, gate,
+                                                                     idx->region_withhold);
         } else {
             auto sort_fn = vec ? region_sort<true> : region_sort<false>;
             sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,

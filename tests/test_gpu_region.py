@@ -324,3 +324,27 @@ def test_two_streams_and_timing():
     capi.qr_rank(idx, dqa, 1, oa)                     # the pool refills after a release
     assert np.array_equal(host_u64(oa), expect(words, n, 2, qa, 1))
     assert capi.qr_status(idx) == 0
+
+
+def test_sort_wait_runs_out_and_reports_timeout():
+    """Failure path without a GPU fault: the test hook withholds one bulk copy
+    of the sort pass, so its bounded wait (0.25 s) runs out.  The call reports
+    QR_ETIMEOUT, its other passes return at once, and the next call on the
+    same context is correct."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S2 + 7
+    words = synth.bits(synth.base_seed(64), n, 0.5)
+    idx = regions_index(words, n, 2, 1)
+    m = 4 * TILE                                # whole tiles: the sort pass moves them by bulk copies
+    q = synth.queries(synth.base_seed(65), n, m)
+    dq = dev_u64(q)
+    out = torch.full((m,), -7, dtype=torch.int64, device="cuda")
+    capi.qr_set_region_fault(idx, True)
+    capi.qr_rank(idx, dq, 1, out)
+    assert capi.qr_status(idx) == capi.QR_ETIMEOUT
+    assert (out == -7).all()                    # the unsort pass returned without writing
+    capi.qr_set_region_fault(idx, False)
+    capi.qr_rank(idx, dq, 1, out)
+    assert np.array_equal(host_u64(out), expect(words, n, 2, q, 1))
+    assert capi.qr_status(idx) == 0

@@ -301,8 +301,13 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 constexpr int kTmaThreads = 1024;             // one block per SM: more warps hide the shared-memory latency
 constexpr int kTmaPer = kTile / kTmaThreads;
-constexpr size_t kSortTmaSmem = (size_t)kTile * 8 * 3 + (size_t)kTile * 2 + (size_t)kTile + (kRegions + 8) * 4 + 32;
+constexpr size_t kSortTmaSmem = (size_t)kTile * 8 * 3 + (size_t)kTile * 2 + (size_t)kTile * 2 + (kRegions + 8) * 4 + 16;
+static_assert(kSortTmaSmem <= 227 * 1024 - 64, "sort pass: shared memory above the per-block limit");
 
+// Full tiles take a branch-free form of the region count that keeps each
+// item's region and its rank inside the region in registers, so that the
+// shared-memory atomics, and later the scatter, of a thread's items overlap
+// (0.82 against 0.91 ms per 2^28 queries with a branch per item).
 template <bool VEC>
 __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t* __restrict__ q,
                                                                    const uint8_t* __restrict__ cv, uint32_t c0,
@@ -315,10 +320,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
     uint64_t* raw1 = raw0 + kTile;
     uint64_t* stage = raw1 + kTile;                          // items in region order
     uint16_t* rank_in = (uint16_t*)(stage + kTile);          // rank of query i inside its region
-    uint8_t* csym = (uint8_t*)(rank_in + kTile);             // per-query symbols of the tile (VEC)
-    uint32_t* h = (uint32_t*)(csym + kTile);                 // region sizes, then starts
+    uint8_t* csym0 = (uint8_t*)(rank_in + kTile);            // per-query symbols of the tile (VEC, two buffers)
+    uint8_t* csym1 = csym0 + kTile;
+    uint32_t* h = (uint32_t*)(csym1 + kTile);                // region sizes, then starts
     uint32_t* ws = h + kRegions;
-    uint64_t* bar = (uint64_t*)(ws + 8);                     // one mbarrier per query buffer, one for csym
+    uint64_t* bar = (uint64_t*)(ws + 8);                     // one mbarrier per buffer pair (queries, symbols)
     __shared__ int s_abort;
     if (!regions_chosen(gate)) return;
     const int lane = threadIdx.x & 31;
@@ -326,7 +332,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], 1);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -334,30 +339,29 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
     uint64_t t = blockIdx.x;
     // withhold (test hook): block 0 never issues its first load, so its first
     // wait runs out and the timeout path is taken
+    constexpr uint32_t kTileBytes = kTile * 8 + (VEC ? kTile : 0);  // one tile's queries (and symbols)
     if (threadIdx.x == 0 && full(t) && !(withhold && blockIdx.x == 0)) {
-        mbar_expect_tx(&bar[0], kTile * 8);
+        mbar_expect_tx(&bar[0], kTileBytes);
         bulk_load(raw0, q + t * kTile, kTile * 8, &bar[0]);
+        if (VEC) bulk_load(csym0, cv + t * kTile, kTile, &bar[0]);
     }
     uint32_t flags = 0, j = 0;
     bool pending = false;  // thread 0: a load issued into the other buffer and not yet waited for
     for (; t < tiles; t += gridDim.x, j++) {
         const uint32_t b = j & 1;
         uint64_t* raw = b ? raw1 : raw0;
+        uint8_t* csym = b ? csym1 : csym0;
         const uint64_t base = t * kTile;
         const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
         const uint64_t tn = t + gridDim.x;
         if (threadIdx.x == 0) {
             pending = false;
-            if (full(tn)) {  // the other buffer was last read before the previous iteration's final barrier
+            if (full(tn)) {  // the other buffers were last read before the previous iteration's final barrier
                 fence_proxy_async();
-                mbar_expect_tx(&bar[b ^ 1], kTile * 8);
+                mbar_expect_tx(&bar[b ^ 1], kTileBytes);
                 bulk_load(b ? raw0 : raw1, q + tn * kTile, kTile * 8, &bar[b ^ 1]);
+                if (VEC) bulk_load(b ? csym0 : csym1, cv + tn * kTile, kTile, &bar[b ^ 1]);
                 pending = true;
-            }
-            if (VEC && full(t)) {  // this tile's symbols: read only after the scan, so the copy is hidden
-                fence_proxy_async();
-                mbar_expect_tx(&bar[2], kTile);
-                bulk_load(csym, cv + base, kTile, &bar[2]);
             }
             if (full(t) && !mbar_wait_bounded(&bar[b], (j >> 1) & 1)) {
                 atomicOr(status, kStatusTimeout);
@@ -374,22 +378,45 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         __syncthreads();
         if (s_abort) break;
         if (full(t) && threadIdx.x != 0) mbar_try_wait(&bar[b], (j >> 1) & 1);  // (completed: acquire the data)
+        const bool pipe = len == kTile;
+        uint32_t rr[kTmaPer], rk[kTmaPer];  // (pipe) region of each item and its rank inside the region
+        if (pipe) {
+            bool u[kTmaPer];
+            uint32_t v[kTmaPer];
 #pragma unroll
-        for (int k = 0; k < kTmaPer; k++) {
-            const uint32_t i = threadIdx.x + k * kTmaThreads;
-            const bool live = i < len;
-            const uint32_t r = region_of(live ? raw[i] : 0, shift);
-            const unsigned act = __ballot_sync(kAll, live);
-            if (!act) continue;
-            const int lead = __ffs(act) - 1;
-            const uint32_t r0 = __shfl_sync(kAll, r, lead);
-            if (__all_sync(kAll, !live || r == r0)) {
-                uint32_t bb = 0;
-                if (lane == lead) bb = atomicAdd(&h[r0], (uint32_t)__popc(act));
-                bb = __shfl_sync(kAll, bb, lead);
-                if (live) rank_in[i] = (uint16_t)(bb + __popc(act & ((1u << lane) - 1u)));
-            } else if (live) {
-                rank_in[i] = (uint16_t)atomicAdd(&h[r], 1u);
+            for (int k = 0; k < kTmaPer; k++) rr[k] = region_of(raw[threadIdx.x + k * kTmaThreads], shift);
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) u[k] = __all_sync(kAll, rr[k] == __shfl_sync(kAll, rr[k], 0));
+            // a warp whose 32 items share a region takes 32 places with one atomic
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) {
+                v[k] = 0;
+                if (!u[k] || lane == 0) v[k] = atomicAdd(&h[rr[k]], u[k] ? 32u : 1u);
+            }
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) {
+                const uint32_t w = __shfl_sync(kAll, v[k], 0);
+                rk[k] = u[k] ? w + (uint32_t)lane : v[k];
+            }
+        }
+        if (!pipe) {
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) {
+                const uint32_t i = threadIdx.x + k * kTmaThreads;
+                const bool live = i < len;
+                const uint32_t r = region_of(live ? raw[i] : 0, shift);
+                const unsigned act = __ballot_sync(kAll, live);
+                if (!act) continue;
+                const int lead = __ffs(act) - 1;
+                const uint32_t r0 = __shfl_sync(kAll, r, lead);
+                if (__all_sync(kAll, !live || r == r0)) {
+                    uint32_t bb = 0;
+                    if (lane == lead) bb = atomicAdd(&h[r0], (uint32_t)__popc(act));
+                    bb = __shfl_sync(kAll, bb, lead);
+                    if (live) rank_in[i] = (uint16_t)(bb + __popc(act & ((1u << lane) - 1u)));
+                } else if (live) {
+                    rank_in[i] = (uint16_t)atomicAdd(&h[r], 1u);
+                }
             }
         }
         __syncthreads();
@@ -399,28 +426,40 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
             h[threadIdx.x] = st;
             seg[(uint64_t)threadIdx.x * tiles + t] = st | (sz << 16);
         }
-        if (threadIdx.x == 0) {
-            bulk_wait_read_all();  // the previous tile's store has read `stage`
-            if (VEC && full(t) && !mbar_wait_bounded(&bar[2], j & 1)) {
-                atomicOr(status, kStatusTimeout);
-                if (gate.abort) *(volatile unsigned long long*)gate.abort = 1;
-                s_abort = 1;
+        if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read `stage`
+        __syncthreads();
+        if (pipe) {
+            uint32_t pos[kTmaPer], cc[kTmaPer];
+            uint64_t x[kTmaPer];
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) pos[k] = h[rr[k]] + rk[k];
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) {
+                x[k] = raw[threadIdx.x + k * kTmaThreads];
+                cc[k] = VEC ? (uint32_t)csym[threadIdx.x + k * kTmaThreads] : c0;
+            }
+#pragma unroll
+            for (int k = 0; k < kTmaPer; k++) {
+                const uint32_t i = threadIdx.x + k * kTmaThreads;
+                const bool range_bad = x[k] > n, sym_bad = cc[k] >= sigma;
+                flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                stage[pos[k]] = ((uint64_t)i << kIdxShift) |
+                                (range_bad || sym_bad ? kBadItem : (x[k] | ((uint64_t)cc[k] << kSymShift)));
             }
         }
-        __syncthreads();
-        if (s_abort) break;
-        if (VEC && full(t) && threadIdx.x != 0) mbar_try_wait(&bar[2], j & 1);  // (completed: acquire the data)
+        if (!pipe) {
 #pragma unroll
-        for (int k = 0; k < kTmaPer; k++) {
-            const uint32_t i = threadIdx.x + k * kTmaThreads;
-            if (i < len) {
-                const uint64_t x = raw[i];
-                const uint32_t c = VEC ? (uint32_t)csym[i] : c0;
-                const bool range_bad = x > n, sym_bad = c >= sigma;
-                flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                const uint64_t item = ((uint64_t)i << kIdxShift) |
-                                      (range_bad || sym_bad ? kBadItem : (x | ((uint64_t)c << kSymShift)));
-                stage[h[region_of(x, shift)] + rank_in[i]] = item;
+            for (int k = 0; k < kTmaPer; k++) {
+                const uint32_t i = threadIdx.x + k * kTmaThreads;
+                if (i < len) {
+                    const uint64_t x = raw[i];
+                    const uint32_t c = VEC ? (uint32_t)csym[i] : c0;
+                    const bool range_bad = x > n, sym_bad = c >= sigma;
+                    flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
+                    const uint64_t item = ((uint64_t)i << kIdxShift) |
+                                          (range_bad || sym_bad ? kBadItem : (x | ((uint64_t)c << kSymShift)));
+                    stage[h[region_of(x, shift)] + rank_in[i]] = item;
+                }
             }
         }
         fence_proxy_async();  // this thread's writes to `stage` are visible to the bulk store
@@ -433,9 +472,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         }
     }
     if (threadIdx.x == 0) {
-        if (s_abort) {  // copies in flight after a timed-out wait: wait for them, bounded
+        // copies in flight after a timed-out wait (this tile's, and the next
+        // one's if issued): wait for them, bounded
+        if (s_abort) {
+            mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1);
             if (pending) mbar_wait_bounded(&bar[(j & 1) ^ 1], ((j + 1) >> 1) & 1);
-            if (VEC && full(t)) mbar_wait_bounded(&bar[2], j & 1);
         }
         bulk_wait_all();  // every store is complete before the block exits
     }
@@ -507,7 +548,10 @@ __device__ __forceinline__ uint32_t ix_ld_u32(const uint32_t* p, uint64_t pol) {
     return EL ? ld_u32_hint(p, pol) : __ldg(p);
 }
 
-template <bool SECTOR, bool QUAD, bool PREFIX = false, bool EL = false>
+// N32 (sector layouts, n < 2^37): the line index from a 32-bit high multiply,
+// x = q >> 5 (or q >> 6) < 2^32 and the usual magic numbers for 15 and 3,
+// ceil(2^35 / 15) and ceil(2^33 / 3), exact for every 32-bit x.
+template <bool SECTOR, bool QUAD, bool PREFIX = false, bool EL = false, bool N32 = false>
 __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L, const uint4* __restrict__ lines,
                                              const void* __restrict__ supers, uint64_t q, uint32_t c,
                                              uint64_t pol = 0) {
@@ -515,14 +559,28 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L
         uint64_t j;
         uint32_t h;
         if (!QUAD) {
-            j = div480(q);
-            const uint32_t p = (uint32_t)(q - j * kB2s);
+            uint32_t p;
+            if (N32) {
+                const uint32_t j32 = __umulhi((uint32_t)(q >> 5), 0x88888889u) >> 3;
+                j = j32;
+                p = (uint32_t)q - j32 * (uint32_t)kB2s;
+            } else {
+                j = div480(q);
+                p = (uint32_t)(q - j * kB2s);
+            }
             h = p >= kHalf2s;
             L.pos = p - h * (uint32_t)kHalf2s;
             L.s = ix_ld_u32<EL>((const uint32_t*)supers + (j >> 7), pol);
         } else {
-            j = div192(q);
-            const uint32_t d = (uint32_t)(q - j * kB4s);
+            uint32_t d;
+            if (N32) {
+                const uint32_t j32 = __umulhi((uint32_t)(q >> 6), 0xAAAAAAABu) >> 1;
+                j = j32;
+                d = (uint32_t)q - j32 * (uint32_t)kB4s;
+            } else {
+                j = div192(q);
+                d = (uint32_t)(q - j * kB4s);
+            }
             h = d >= kHalf4s;
             L.pos = d - h * (uint32_t)kHalf4s;
             if (PREFIX) L.s4 = __ldg((const uint4*)supers + (j >> 8));
@@ -603,12 +661,13 @@ __device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD,
 // together in the table, so the regions they touch stay in L2.
 template <int K>
 struct ItemSlot {
-    uint64_t it[K], at[K];
+    uint64_t it[K];
+    uint32_t at[K];  // place in the work array (m < 2^32)
 };
 
 template <int K, int SEGS>
 __device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint64_t* __restrict__ work, uint32_t j0,
-                                            uint32_t total, uint32_t start, uint64_t sbase, int lane) {
+                                            uint32_t total, uint32_t start, uint32_t sbase, int lane) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const uint32_t j = j0 + lane + 32 * k;
@@ -619,7 +678,7 @@ __device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint64_t* __re
             const uint32_t st = __shfl_sync(kAll, start, sidx + b);
             if (st <= j) sidx += b;
         }
-        const uint64_t sb = __shfl_sync(kAll, sbase, sidx);
+        const uint32_t sb = __shfl_sync(kAll, sbase, sidx);
         const uint32_t s0 = __shfl_sync(kAll, start, sidx);
         S.at[k] = sb + (j - s0);
         S.it[k] = j < total ? ld_stream_u64(work + S.at[k]) : kBadItem;
@@ -638,7 +697,7 @@ struct RankPassArgs {
 };
 
 template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, bool PREFIX = false,
-          bool EL = false>
+          bool EL = false, bool N32 = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
     if (!regions_chosen(a.gate)) return;
     const int lane = threadIdx.x & 31;
@@ -658,23 +717,24 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
     };
     uint64_t g = QUEUE ? next_step(0) : (uint64_t)blockIdx.x * (kRankThreads / 32) + (threadIdx.x >> 5);
     // this lane's segment of the warp's current step: length and first item
-    auto seg_of = [&](uint64_t step, uint32_t& len, uint64_t& sbase) {
+    // (nseg = 256 tiles < 2^27 and m < 2^32: 32-bit arithmetic)
+    auto seg_of = [&](uint64_t step, uint32_t& len, uint32_t& sbase) {
         len = 0;
         sbase = 0;
         const uint64_t w = step * kWarpSegs + lane;
         if (lane < kWarpSegs && step < nsteps && w < a.nseg) {
             const uint32_t e = __ldg(a.seg + w);
             len = e >> 16;
-            sbase = (w % a.tiles) * kTile + (e & 0xFFFFu);
+            sbase = ((uint32_t)w % (uint32_t)a.tiles) * kTile + (e & 0xFFFFu);
         }
     };
     uint32_t len;
-    uint64_t sbase;
+    uint32_t sbase;
     seg_of(g, len, sbase);
     while (g < nsteps) {
         const uint64_t gn = next_step(g);
         uint32_t nlen;
-        uint64_t nbase;
+        uint32_t nbase;
         seg_of(gn, nlen, nbase);  // the next step's table entries, loaded early
         uint32_t incl = len;
 #pragma unroll
@@ -705,7 +765,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                 const bool bad = cur.it[k] & kBadItem;
                 const uint64_t qq = bad ? 0 : cur.it[k] & kValMask;  // bad items (and idle lanes) read line 0
                 const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                region_issue<SECTOR, QUAD, PREFIX, EL>(L[k], a.lines, a.supers, qq, c, pol);
+                region_issue<SECTOR, QUAD, PREFIX, EL, N32>(L[k], a.lines, a.supers, qq, c, pol);
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -765,21 +825,28 @@ using RankFn = void (*)(RankPassArgs);
 // rounds of items loaded ahead, segments per warp-step, steps from a device
 // queue, evict-last index loads).  Measured on GB300 (2^28 uniform queries,
 // sector layout): 0 1.78 ms, 1 2.11 ms, 2 1.78 ms, 3 1.91 ms.
-template <bool SECTOR, bool QUAD, bool VEC>
+template <bool SECTOR, bool QUAD, bool VEC, bool N32 = false>
 RankFn pick_variant(int v) {
     switch (v) {
-        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true>;
-        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true>;
-        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, true>;
-        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true>;
+        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, false, N32>;
+        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true, false, false, N32>;
+        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, true, N32>;
+        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true, false, false, N32>;
         default: return nullptr;
     }
 }
 
-RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix) {
+// n32: sector layout with n < 2^37 (the 32-bit line-index division)
+RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix, bool n32) {
     if (prefix) {  // sigma 4, one symbol, default variant
-        return sector ? region_rank<true, true, false, 2, 4, 1, 16, true, true>
-                      : region_rank<false, true, false, 2, 4, 1, 16, true, true>;
+        if (sector)
+            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, true, false, true>
+                       : region_rank<true, true, false, 2, 4, 1, 16, true, true>;
+        return region_rank<false, true, false, 2, 4, 1, 16, true, true>;
+    }
+    if (sector && n32) {
+        if (quad) return vec ? pick_variant<true, true, true, true>(v) : pick_variant<true, true, false, true>(v);
+        return vec ? pick_variant<true, false, true, true>(v) : pick_variant<true, false, false, true>(v);
     }
     if (sector) {
         if (quad) return vec ? pick_variant<true, true, true>(v) : pick_variant<true, true, false>(v);
@@ -889,7 +956,8 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc && marks) cudaEventRecord(marks[1], s);
     if (!rc) {
-        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, rank4 == 2);
+        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, rank4 == 2,
+                                     sector && idx->n < (1ull << 37));
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;

@@ -68,3 +68,37 @@ def test_division_constants():
         assert ((q >> 5) * M7 >> 64) >> 2 == q // 224
     src = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_common.cuh").read_text()
     assert "0x8421084210842109" in src and "0x924924924924924A" in src
+
+
+def test_division_constants_sector_and_32bit():
+    """The other line-index divisions: 480 = 32 * 15 and 192 = 64 * 3 (sector
+    layouts), 1008 = 16 * 63, and the 32-bit forms the region pass takes when
+    n < 2^37 (q >> 5 or q >> 6 below 2^32).  Each 32-bit magic M = ceil(2^s / d)
+    is exact for every x below 2^32 when (d M - 2^s) (2^32 - 1) < 2^s, the
+    Granlund-Montgomery bound; the samples check it at the edges."""
+    import random
+    M15, M3, M63 = 0x8888888888888889, 0xAAAAAAAAAAAAAAAB, 0x8208208208208209
+    m15, m3, m7 = 0x88888889, 0xAAAAAAAB, 0x24924925
+    assert (15 * m15 - (1 << 35)) * ((1 << 32) - 1) < (1 << 35)
+    assert (3 * m3 - (1 << 33)) * ((1 << 32) - 1) < (1 << 33)
+    assert (7 * m7 - (1 << 32)) * ((1 << 27) - 1) < (1 << 32)   # div224_32: x < 2^27
+    rnd = random.Random(2)
+    edges = [0, 1, 191, 192, 193, 479, 480, 481, 1007, 1008, 1009, (1 << 37) - 1, (1 << 37) - 480, (1 << 36) + 7]
+    qs = edges + [rnd.getrandbits(63) for _ in range(20000)] + [rnd.getrandbits(37) for _ in range(20000)]
+    for q in qs:
+        assert ((q >> 5) * M15 >> 64) >> 3 == q // 480
+        assert ((q >> 6) * M3 >> 64) >> 1 == q // 192
+        assert ((q >> 4) * M63 >> 64) >> 5 == q // 1008
+        if q < (1 << 37):
+            assert ((q >> 5) * m15 >> 32) >> 3 == q // 480
+            assert ((q >> 6) * m3 >> 32) >> 1 == q // 192
+        if q < (1 << 32):
+            assert (q >> 5) * m7 >> 32 == q // 224
+    for d, M in ((15, m15), (3, m3)):   # the largest dividend below 2^32 of each residue
+        for r in range(d):
+            x = (1 << 32) - 1 - r
+            assert (x * M >> 32) >> (3 if d == 15 else 1) == x // d
+    src = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_common.cuh").read_text()
+    assert all(h in src for h in ("0x8888888888888889", "0xAAAAAAAAAAAAAAAB", "0x8208208208208209", "0x24924925"))
+    reg = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_region.cu").read_text()
+    assert "0x88888889u" in reg and "0xAAAAAAABu" in reg

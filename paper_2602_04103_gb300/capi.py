@@ -106,16 +106,11 @@ def numel(x) -> int:
     return x.numel() if hasattr(x, "numel") else x.size
 
 
-class QRIndex:
-    """Owner of a qr_index* (freed with qr_free)."""
+class _Handle:
+    """Owner of an opaque library handle (freed by `free`)."""
 
     def __init__(self, handle: int):
         self.handle = handle
-
-    def free(self) -> None:
-        if self.handle:
-            lib.qr_free(self.handle)
-            self.handle = None
 
     def __del__(self):
         try:
@@ -126,6 +121,45 @@ class QRIndex:
     @property
     def _as_parameter_(self):
         return vp(self.handle)
+
+
+class QRIndex(_Handle):
+    """Owner of a qr_index* (freed with qr_free).  The methods allocate the
+    output on the queries' device when `out` is None and call the entry point
+    of the same name; like those, they are asynchronous on `stream`."""
+
+    def free(self) -> None:
+        if self.handle:
+            lib.qr_free(self.handle)
+            self.handle = None
+
+    def rank(self, q, c, out=None, stream=None):
+        """rank(q, c) of every position in q: qr_rank for an int symbol,
+        qr_rank_c for a per-query uint8 symbol tensor."""
+        import torch
+        out = torch.empty_like(q) if out is None else out
+        if isinstance(c, int):
+            qr_rank(self, q, c, out, stream)
+        else:
+            qr_rank_c(self, q, c, out, stream)
+        return out
+
+    def rank4(self, q, out4=None, stream=None):
+        """All four symbol ranks of every position (sigma = 4): an m x 4 tensor."""
+        import torch
+        out4 = torch.empty((numel(q), 4), dtype=q.dtype, device=q.device) if out4 is None else out4
+        qr_rank4(self, q, out4, stream)
+        return out4
+
+    def prefix_rank(self, q, c: int, out=None, stream=None):
+        """The number of symbols <= c before each position (sigma = 4)."""
+        import torch
+        out = torch.empty_like(q) if out is None else out
+        qr_prefix_rank(self, q, c, out, stream)
+        return out
+
+    def status(self, stream=None) -> int:
+        return qr_status(self, stream)
 
 
 def qr_build(text, n: int, sigma: int, stream=None, layout: int = QR_LAYOUT_PAPER) -> QRIndex:
@@ -293,13 +327,27 @@ _sig("qfm_status", [vp, vp])
 _sig("qfm_free", [vp])
 
 
-class QFMIndex(QRIndex):
-    """Owner of a qfm_index* (freed with qfm_free)."""
+class QFMIndex(_Handle):
+    """Owner of a qfm_index* (freed with qfm_free); `count` allocates the
+    output when `out` is None and calls qfm_count_ex."""
 
     def free(self) -> None:
         if self.handle:
             lib.qfm_free(self.handle)
             self.handle = None
+
+    def count(self, patterns, offsets, flags: int = 0, out=None, stream=None):
+        """Occurrence counts of the m patterns (2m with QFM_BOTH_STRANDS)."""
+        import torch
+        m = numel(offsets) - 1
+        if out is None:
+            n_out = 2 * m if flags & QFM_BOTH_STRANDS else m
+            out = torch.empty(n_out, dtype=torch.int64, device=offsets.device)
+        qfm_count_ex(self, patterns, offsets, out, flags, stream)
+        return out
+
+    def status(self, stream=None) -> int:
+        return qfm_status(self, stream)
 
 
 def qfm_build(codes, n: int | None = None, flags: int = 0, stream=None, sa_sample: int = 0) -> QFMIndex:

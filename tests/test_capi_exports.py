@@ -102,3 +102,16 @@ def test_division_constants_sector_and_32bit():
     assert all(h in src for h in ("0x8888888888888889", "0xAAAAAAAAAAAAAAAB", "0x8208208208208209", "0x24924925"))
     reg = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_region.cu").read_text()
     assert "0x88888889u" in reg and "0xAAAAAAABu" in reg
+
+
+def test_handle_classes():
+    # the FM handle offers count, not the rank calls of a rank index
+    from paper_2602_04103_gb300 import capi
+    assert not issubclass(capi.QFMIndex, capi.QRIndex)
+    for name in ("rank", "rank4", "prefix_rank", "status", "free"):
+        assert callable(getattr(capi.QRIndex, name))
+    for name in ("count", "status", "free"):
+        assert callable(getattr(capi.QFMIndex, name))
+    assert not hasattr(capi.QFMIndex, "rank")
+    idx = capi.QRIndex(None)       # an empty handle frees as a no-op
+    idx.free()

@@ -274,14 +274,16 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
  *                     choice is made on the device: both paths are launched
  *                     and the one not chosen returns at once.
  *   QR_BATCH_DIRECT   always the direct kernels (one line load per query).
- *   QR_BATCH_REGIONS  region batching for every m < 2^32.
+ *   QR_BATCH_REGIONS  region batching for every m < 2^32 (larger batches
+ *                     run direct).
  * Scope: qr_rank, qr_rank_c and qr_prefix_rank on the paper and sector
  * layouts.  rank_4 always runs direct (its four 8-byte results would be moved
  * three times, about 129 bytes per query, no less than the direct kernel's
  * 168 bytes at the random-fill rate), and so do chains and the 128-byte line
  * layout.
  * Scratch: 8 bytes per query plus 4 bytes per (region, tile) pair (1/8
- * byte per query), from a memory pool of the library that keeps the memory
+ * byte per query) plus 32 bytes of counters (work queue, probe count, abort
+ * word), from a memory pool of the library that keeps the memory
  * for later calls (released by qr_release_scratch).  When that memory cannot
  * be had, the call runs the direct kernels instead.
  * Status bits and sentinel outputs are those of the direct kernels.

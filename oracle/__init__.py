@@ -38,7 +38,7 @@ def build(force: bool = False) -> Path:
     """Compile liboracle.so with gcc (portable C, no ISA-specific flags)."""
     SO.parent.mkdir(exist_ok=True)
     if force or not SO.exists() or SO.stat().st_mtime < SRC.stat().st_mtime:
-        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", str(SRC), "-o", str(SO)],
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", str(SRC), "-o", str(SO)],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
@@ -54,6 +54,7 @@ def _load():
         lib.or_char.argtypes = [_P, C.c_int, u64]
         lib.or_rank_naive.argtypes = [_P, u64, C.c_int, u64, C.c_int, _P]
         lib.or_rank_sweep.argtypes = [_P, u64, C.c_int, _P, u64, C.c_int, C.c_int, _P, _P]
+        lib.or_rank_sweep_mt.argtypes = [_P, u64, C.c_int, _P, u64, C.c_int, C.c_int, _P, _P, C.c_int]
         lib.or_suffix_array.argtypes = [_P, u64, _P]
         lib.or_bwt.argtypes = [_P, u64, _P, _P, _P]
         lib.or_sa_interval.argtypes = [_P, u64, _P, _P, u64, _P, _P]
@@ -99,34 +100,41 @@ def rank_naive(text: np.ndarray, n: int, sigma: int, q: int, c: int) -> int:
     return int(out[0])
 
 
-def rank(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: int) -> tuple[np.ndarray, int]:
-    """rank(q[k], c) for every k by one sweep; returns (out, rc)."""
+def _sweep(text, n, sigma, q, mode, c, c_arr, out, threads):
+    """or_rank_sweep, or its threaded form when threads > 1."""
+    lib = _load()
+    cp = _p(c_arr) if c_arr is not None else None
+    if threads > 1:
+        return lib.or_rank_sweep_mt(_p(text), n, sigma, _p(q), q.size, mode, c, cp, _p(out), threads)
+    return lib.or_rank_sweep(_p(text), n, sigma, _p(q), q.size, mode, c, cp, _p(out))
+
+
+def rank(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: int, threads: int = 1) -> tuple[np.ndarray, int]:
+    """rank(q[k], c) for every k by one sweep (on `threads` threads); returns (out, rc)."""
     text, q = _u64(text), _u64(q)
     out = np.empty(q.size, dtype=np.uint64)
-    rc = _load().or_rank_sweep(_p(text), n, sigma, _p(q), q.size, 0, c, None, _p(out))
-    return out, rc
+    return out, _sweep(text, n, sigma, q, 0, c, None, out, threads)
 
 
-def rank_c(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: np.ndarray) -> tuple[np.ndarray, int]:
+def rank_c(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: np.ndarray,
+           threads: int = 1) -> tuple[np.ndarray, int]:
     text, q, c = _u64(text), _u64(q), _u8(c)
     out = np.empty(q.size, dtype=np.uint64)
-    rc = _load().or_rank_sweep(_p(text), n, sigma, _p(q), q.size, 1, 0, _p(c), _p(out))
-    return out, rc
+    return out, _sweep(text, n, sigma, q, 1, 0, c, out, threads)
 
 
-def rank4(text: np.ndarray, n: int, q: np.ndarray) -> tuple[np.ndarray, int]:
+def rank4(text: np.ndarray, n: int, q: np.ndarray, threads: int = 1) -> tuple[np.ndarray, int]:
     text, q = _u64(text), _u64(q)
     out = np.empty((q.size, 4), dtype=np.uint64)
-    rc = _load().or_rank_sweep(_p(text), n, 4, _p(q), q.size, 2, 0, None, _p(out))
-    return out, rc
+    return out, _sweep(text, n, 4, q, 2, 0, None, out, threads)
 
 
-def prefix_rank(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: int) -> tuple[np.ndarray, int]:
+def prefix_rank(text: np.ndarray, n: int, sigma: int, q: np.ndarray, c: int,
+                threads: int = 1) -> tuple[np.ndarray, int]:
     """#{i < q[k] : t_i <= c} for every k by one sweep; returns (out, rc)."""
     text, q = _u64(text), _u64(q)
     out = np.empty(q.size, dtype=np.uint64)
-    rc = _load().or_rank_sweep(_p(text), n, sigma, _p(q), q.size, 3, c, None, _p(out))
-    return out, rc
+    return out, _sweep(text, n, sigma, q, 3, c, None, out, threads)
 
 
 def rank_chain(text: np.ndarray, n: int, sigma: int, q0: np.ndarray, steps: int, c: int) -> tuple[np.ndarray, int]:

@@ -28,9 +28,13 @@
  *          DNA text  char i = (w[i/32] >> (2*(i%32))) & 3 (A=0,C=1,G=2,T=3);
  *          DNA codes one byte per char.
  *
- * Parity pins live in tests/test_oracle_*.py.  Single-threaded on purpose.
+ * Parity pins live in tests/test_oracle_*.py.  Every function is
+ * single-threaded on purpose, except or_rank_sweep_mt: the same sweep cut into
+ * text chunks that threads answer side by side (pinned equal to the
+ * single-threaded sweep), used to time the oracle on all host cores.
  */
 #define _GNU_SOURCE
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -120,6 +124,150 @@ int or_rank_sweep(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q
         }
     }
     free(ord);
+    return rc;
+}
+
+/*
+ * The sweep of or_rank_sweep on `threads` threads (same modes, arguments,
+ * results and return codes).  The text is cut into `threads` chunks of equal
+ * length (a multiple of 64 positions); a query q belongs to the chunk that
+ * holds position q (q = n to the last one).  Each thread first counts the
+ * symbols of its chunk; a serial prefix sum of those totals gives the counts
+ * before every chunk; then each thread sorts its own chunk's queries and
+ * sweeps its chunk from that prefix, answering them as in or_rank_sweep.
+ */
+typedef struct {
+    const uint64_t* text;
+    uint64_t n, a, b;       /* chunk [a, b) of the text */
+    int sigma, mode, c;
+    const uint8_t* c_arr;
+    qpair* ord;             /* this chunk's queries */
+    uint64_t nq;
+    uint64_t base[4];       /* symbol counts before position a */
+    uint64_t total[4];      /* symbol counts of the chunk (phase 1) */
+    uint64_t* out;
+    int rc;
+} sweep_job;
+
+/* Phase 1: the symbol counts of t_a .. t_{b-1}. */
+static void* sweep_totals(void* arg) {
+    sweep_job* j = (sweep_job*)arg;
+    uint64_t cnt[4] = {0, 0, 0, 0};
+    for (uint64_t pos = j->a; pos < j->b;) {
+        if (j->sigma == 2 && pos % 64 == 0 && pos + 64 <= j->b) {
+            uint64_t ones = (uint64_t)__builtin_popcountll(j->text[pos / 64]);
+            cnt[1] += ones;
+            cnt[0] += 64 - ones;
+            pos += 64;
+        } else {
+            cnt[text_char(j->text, j->sigma, pos)]++;
+            pos++;
+        }
+    }
+    memcpy(j->total, cnt, sizeof cnt);
+    return NULL;
+}
+
+/* Phase 2: sort the chunk's queries and answer them by one sweep from a. */
+static void* sweep_answer(void* arg) {
+    sweep_job* j = (sweep_job*)arg;
+    qsort(j->ord, j->nq, sizeof(qpair), cmp_qpair);
+    uint64_t pos = j->a, cnt[4];
+    memcpy(cnt, j->base, sizeof cnt);
+    j->rc = OR_OK;
+    for (uint64_t k = 0; k < j->nq; k++) {
+        const uint64_t target = j->ord[k].q, idx = j->ord[k].idx;
+        while (pos < target) {
+            if (j->sigma == 2 && pos % 64 == 0 && pos + 64 <= target) {
+                uint64_t ones = (uint64_t)__builtin_popcountll(j->text[pos / 64]);
+                cnt[1] += ones;
+                cnt[0] += 64 - ones;
+                pos += 64;
+            } else {
+                cnt[text_char(j->text, j->sigma, pos)]++;
+                pos++;
+            }
+        }
+        if (j->mode == 0) j->out[idx] = cnt[j->c];
+        else if (j->mode == 3) {
+            uint64_t r = 0;
+            for (int s = 0; s <= j->c; s++) r += cnt[s];
+            j->out[idx] = r;
+        } else if (j->mode == 1) {
+            int cc = j->c_arr[idx];
+            if (cc >= j->sigma) { j->out[idx] = UINT64_MAX; j->rc = OR_EINVAL; }
+            else j->out[idx] = cnt[cc];
+        } else {
+            for (int s = 0; s < 4; s++) j->out[4 * idx + s] = cnt[s];
+        }
+    }
+    return NULL;
+}
+
+int or_rank_sweep_mt(const uint64_t* text, uint64_t n, int sigma, const uint64_t* q, uint64_t m,
+                     int mode, int c, const uint8_t* c_arr, uint64_t* out, int threads) {
+    if (sigma != 2 && sigma != 4) return OR_EINVAL;
+    if ((mode == 0 || mode == 3) && (c < 0 || c >= sigma)) return OR_EINVAL;
+    if (mode == 2 && sigma != 4) return OR_EINVAL;
+    if (mode < 0 || mode > 3 || threads < 1) return OR_EINVAL;
+    const uint64_t T = (uint64_t)threads;
+    uint64_t len = (n + T - 1) / T;
+    len = (len + 63) / 64 * 64;
+    if (len == 0) len = 64;
+    sweep_job* jobs = (sweep_job*)calloc(T, sizeof(sweep_job));
+    uint64_t* first = (uint64_t*)calloc(T + 1, sizeof(uint64_t));
+    qpair* ord = (qpair*)malloc((m ? m : 1) * sizeof(qpair));
+    pthread_t* tid = (pthread_t*)malloc(T * sizeof(pthread_t));
+    if (!jobs || !first || !ord || !tid) {
+        free(jobs); free(first); free(ord); free(tid);
+        return OR_ENOMEM;
+    }
+    int rc = OR_OK;
+    /* the chunk of every valid query; out-of-range queries are answered here */
+    for (uint64_t k = 0; k < m; k++) {
+        if (q[k] > n) continue;
+        uint64_t ch = q[k] / len;
+        if (ch >= T) ch = T - 1;
+        first[ch + 1]++;
+    }
+    for (uint64_t t = 0; t < T; t++) first[t + 1] += first[t];
+    uint64_t* fill = (uint64_t*)malloc(T * sizeof(uint64_t));
+    if (!fill) {
+        free(jobs); free(first); free(ord); free(tid);
+        return OR_ENOMEM;
+    }
+    memcpy(fill, first, T * sizeof(uint64_t));
+    for (uint64_t k = 0; k < m; k++) {
+        if (q[k] > n) {
+            rc = OR_ERANGE;
+            if (mode == 2) { for (int s = 0; s < 4; s++) out[4 * k + s] = UINT64_MAX; }
+            else out[k] = UINT64_MAX;
+            continue;
+        }
+        uint64_t ch = q[k] / len;
+        if (ch >= T) ch = T - 1;
+        ord[fill[ch]].q = q[k];
+        ord[fill[ch]].idx = k;
+        fill[ch]++;
+    }
+    free(fill);
+    for (uint64_t t = 0; t < T; t++) {
+        sweep_job* j = &jobs[t];
+        j->text = text; j->n = n; j->sigma = sigma; j->mode = mode; j->c = c; j->c_arr = c_arr; j->out = out;
+        j->a = t * len < n ? t * len : n;
+        j->b = (t + 1) * len < n ? (t + 1) * len : n;
+        j->ord = ord + first[t];
+        j->nq = first[t + 1] - first[t];
+    }
+    for (uint64_t t = 0; t < T; t++) pthread_create(&tid[t], NULL, sweep_totals, &jobs[t]);
+    for (uint64_t t = 0; t < T; t++) pthread_join(tid[t], NULL);
+    for (uint64_t t = 1; t < T; t++)
+        for (int s = 0; s < 4; s++) jobs[t].base[s] = jobs[t - 1].base[s] + jobs[t - 1].total[s];
+    for (uint64_t t = 0; t < T; t++) pthread_create(&tid[t], NULL, sweep_answer, &jobs[t]);
+    for (uint64_t t = 0; t < T; t++) pthread_join(tid[t], NULL);
+    for (uint64_t t = 0; t < T; t++)
+        if (jobs[t].rc != OR_OK && rc == OR_OK) rc = jobs[t].rc;
+    free(jobs); free(first); free(ord); free(tid);
     return rc;
 }
 

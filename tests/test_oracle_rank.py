@@ -197,3 +197,58 @@ def test_rank_chain_pins():
         assert got[k].tolist() == [q, r]
     bad, rc = oracle.rank_chain(words, n, 2, np.array([n + 1], dtype=np.uint64), 3, 1)
     assert rc == oracle.OR_ERANGE and bad[0, 0] == oracle.U64_MAX
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8, 33])
+def test_threaded_sweep_numpy_prefix_sums(threads):
+    # the threaded sweep (text cut into chunks answered side by side) against
+    # numpy prefix sums of the unpacked text, every q and all modes
+    n = 9001
+    words = synth.bits(3, n, 0.3)
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little")[:n].astype(np.uint64)
+    pref = np.concatenate([[0], np.cumsum(bits)]).astype(np.uint64)
+    q = synth.queries(5, n, 20000)
+    q[:3] = [0, n, n]
+    got, rc = oracle.rank(words, n, 2, q, 1, threads=threads)
+    assert rc == 0 and np.array_equal(got, pref[q])
+    got0, rc = oracle.rank(words, n, 2, q, 0, threads=threads)
+    assert rc == 0 and np.array_equal(got0, q - pref[q])
+    rng = np.random.default_rng(threads)
+    codes = rng.integers(0, 4, 7003).astype(np.uint8)
+    w4 = synth.pack2(codes)
+    q4 = np.arange(7004, dtype=np.uint64)[::-1].copy()        # every q, descending
+    prefs = [np.concatenate([[0], np.cumsum(codes == c)]).astype(np.uint64) for c in range(4)]
+    r4, rc = oracle.rank4(w4, 7003, q4, threads=threads)
+    assert rc == 0
+    for c in range(4):
+        assert np.array_equal(r4[:, c], prefs[c][q4])
+        assert np.array_equal(oracle.rank(w4, 7003, 4, q4, c, threads=threads)[0], prefs[c][q4])
+        le = sum(prefs[k] for k in range(c + 1))
+        assert np.array_equal(oracle.prefix_rank(w4, 7003, 4, q4, c, threads=threads)[0], le[q4])
+    cs = synth.symbols(6, q4.size, 4)
+    got, rc = oracle.rank_c(w4, 7003, 4, q4, cs, threads=threads)
+    assert rc == 0 and np.array_equal(got, r4[np.arange(q4.size), cs])
+
+
+@pytest.mark.parametrize("threads", [2, 5, 64])
+def test_threaded_sweep_equals_single_edges(threads):
+    # tiny texts (fewer positions than threads), closed forms, q = n, errors
+    for n in (1, 7, 64, 65, 130):
+        ones = synth.pack_bits(np.ones(n, dtype=np.uint8))
+        q = np.arange(n + 1, dtype=np.uint64)
+        got, rc = oracle.rank(ones, n, 2, q, 1, threads=threads)
+        assert rc == 0 and got.tolist() == list(range(n + 1))
+    n = 5000
+    words = synth.dna_uniform(21, n)
+    bad = np.array([0, n, n + 1, 2 ** 63, 17], dtype=np.uint64)
+    got, rc = oracle.rank(words, n, 4, bad, 2, threads=threads)
+    want, rc1 = oracle.rank(words, n, 4, bad, 2)
+    assert rc == rc1 == oracle.OR_ERANGE and np.array_equal(got, want)
+    syms = np.array([0, 1, 4, 3, 2], dtype=np.uint8)          # one symbol out of range
+    q = np.array([5, 6, 7, 8, 9], dtype=np.uint64)
+    got, rc = oracle.rank_c(words, n, 4, q, syms, threads=threads)
+    want, rc1 = oracle.rank_c(words, n, 4, q, syms)
+    assert rc == rc1 == oracle.OR_EINVAL and np.array_equal(got, want)
+    r4, rc = oracle.rank4(words, n, bad, threads=threads)
+    w4, rc1 = oracle.rank4(words, n, bad)
+    assert rc == rc1 and np.array_equal(r4, w4)

@@ -197,22 +197,31 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
 
 REGION_TILE, REGION_COUNT = 8192, 256
 REGION_PASSES = ("sort", "rank", "unsort")
-REGION_KERNELS = {"sort": "region_sort<VEC>", "rank": "region_rank<SECTOR,QUAD,VEC>", "unsort": "region_unsort"}
+REGION_KERNELS = {"sort": "region_sort_tma<VEC>", "rank": "region_rank<SECTOR,QUAD,VEC,MODE>",
+                  "unsort": "region_unsort (rank_4: region_unsort4)"}
 
 
-def region_pass_bytes(m: int, index_bytes: int, per_query_c: bool = False) -> dict:
+def region_pass_bytes(m: int, index_bytes: int, per_query_c: bool = False, rank4: bool = False) -> dict:
     """Algorithmic DRAM bytes per query of each region-batching pass: the
-    query word (and symbol) read once, 8-byte work items written and read
-    back, the 4-byte segment entries (one per region and tile of 8192
-    queries), and the index read once per batch in the rank pass."""
+    query word (and symbol) read once; a 4-byte key and a 2-byte index inside
+    the tile written by the sort; the 4-byte segment entries (one per region
+    and tile of 8192 queries) written twice by the sort (region-major for the
+    rank pass, tile-major for the unsort) and read once by each later pass;
+    the key read and the low 32 bits of the result written back by the rank
+    pass (rank_4: the low 32 bits of the four counts, 16 bytes, written in
+    sorted order); key (rank_4: the 16 bytes) and index read and the 8-byte
+    result (rank_4: the 32-byte row) written by the unsort; the index read
+    once per batch in the rank pass."""
     seg = 4.0 * REGION_COUNT / REGION_TILE
     sym = 1.0 if per_query_c else 0.0
-    return {"sort": 8 + sym + 8 + seg, "rank": 8 + 8 + seg + index_bytes / m, "unsort": 8 + 8}
+    if rank4:
+        return {"sort": 8 + sym + 6 + 2 * seg, "rank": 4 + 16 + seg + index_bytes / m, "unsort": 16 + 2 + seg + 32}
+    return {"sort": 8 + sym + 6 + 2 * seg, "rank": 4 + 4 + seg + index_bytes / m, "unsort": 6 + seg + 8}
 
 
-def region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream, per_query_c=False):
-    """Roofline of the dominant pass of a region-batched step, from CUDA
-    events the library records between its passes (median of 3 calls)."""
+def region_passes(idx, step, m, index_bytes, per_query_c=False, rank4=False):
+    """Per-pass times of a region-batched call (CUDA events the library
+    records between its passes, median of 3 calls) and the passes' bytes."""
     from paper_2602_04103_gb300 import capi
     capi.qr_region_timing(idx, True)
     runs = []
@@ -221,21 +230,29 @@ def region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream, 
         runs.append(capi.qr_region_timing(idx, True, read=True))
     capi.qr_region_timing(idx, False)
     pass_ms = {p: float(np.median([r[i] for r in runs])) for i, p in enumerate(REGION_PASSES)}
-    pbytes = region_pass_bytes(m, index_bytes, per_query_c)
+    return pass_ms, region_pass_bytes(m, index_bytes, per_query_c, rank4)
+
+
+def region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream, per_query_c=False, rank4=False,
+                    traffic_key="birank_region"):
+    """Roofline of the dominant pass of a region-batched step."""
+    pass_ms, pbytes = region_passes(idx, step, m, index_bytes, per_query_c, rank4)
     dom = max(pass_ms, key=pass_ms.get)
     achieved = pbytes[dom] * m / (pass_ms[dom] * 1e-3) / 1e9
-    tr = traffic_record(f"birank_region_{dom}")
+    tr = traffic_record(f"{traffic_key}_{dom}")
     step_bytes = sum(pbytes.values())
-    # under the automatic rule every step also launches the probe and the
-    # direct kernel, which returns at once when the probe picks region batching
-    launches = len(REGION_PASSES) + 2
+    passes = list(REGION_PASSES)
+    # under the automatic rule every step also launches the probe, the direct
+    # kernel (which returns at once when the probe picks region batching)
+    # and the kernel of the region bases
+    launches = len(passes) + 3
     return ({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
              "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
              "peak_kind": f"of {peak_kind} (copy bandwidth)", "kernel": REGION_KERNELS[dom],
              "algorithmic_bytes_per_query": round(pbytes[dom], 3), "queries_per_launch": m,
-             "passes_ms": {p: round(v, 4) for p, v in pass_ms.items()},
-             "passes_bytes_per_query": {p: round(v, 3) for p, v in pbytes.items()},
-             "passes_frac": {p: round(pbytes[p] * m / (pass_ms[p] * 1e-3) / 1e9 / peak, 4) for p in REGION_PASSES},
+             "passes_ms": {p: round(pass_ms[p], 4) for p in passes},
+             "passes_bytes_per_query": {p: round(pbytes[p], 3) for p in passes},
+             "passes_frac": {p: round(pbytes[p] * m / (pass_ms[p] * 1e-3) / 1e9 / peak, 4) for p in passes},
              "step_bytes_per_query": round(step_bytes, 3),
              "step_achieved_GB_s": round(step_bytes * m / (avg_ms * 1e-3) / 1e9, 1),
              "step_frac": round(step_bytes * m / (avg_ms * 1e-3) / 1e9 / peak, 4),
@@ -404,6 +421,8 @@ def run_ours(args):
         line["extra"] = extra
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, n, text, q)
+        if not args.no_extra:
+            line.setdefault("extra", {})["cpu_baseline_qfm_count"] = cpu_baseline_fm(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -528,40 +547,70 @@ def run_extras_other(args, stream, peak):
 
 
 def run_quadrank(args, stream, peak):
-    """QuadRank over 2^32 uniform DNA: rank(q, c) with random c, and rank_4."""
+    """QuadRank over 2^32 uniform DNA: rank(q, c) with random c, prefix_rank
+    and rank_4, each on the layout the tuned build picks for it."""
     import torch
     from paper_2602_04103_gb300 import capi, workloads
     res = {}
     m = 1 << args.log_m
     n4 = 1 << args.log_n4
+    peak_kind = peaks()[1]
     t4, q4, c4 = workloads.quadrank_inputs(args.log_n4, args.log_m, "uniform")
     dq, dc = dev_u64(q4), torch.from_numpy(c4).cuda()
-    idx4, layout4, tuning4 = workloads.build_tuned(dev_u64(t4), n4, 4, dq, c=dc)
+    d4 = dev_u64(t4)
     del t4
+    idx4, layout4, tuning4 = workloads.build_tuned(d4, n4, 4, dq, c=dc)
+    info = capi.qr_info(idx4)
+    index_bytes = info["bytes_blocks"] + info["bytes_super"]
     o = torch.empty_like(dq)
-    ms = best_ms(lambda: capi.qr_rank_c(idx4, dq, dc, o), stream)
+    step = lambda: capi.qr_rank_c(idx4, dq, dc, o)  # noqa: E731
+    ms = best_ms(step, stream)
     gq = m / (ms * 1e-3) / 1e9
-    bpq = bytes_per_query(4, layout4, tuning4["load_mode"], per_query_c=True)
-    res["quadrank_rank_random_c"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": tuning4,
-                                     "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4),
-                                     "batch_path": "regions" if capi.qr_rank_plan(idx4, m) == capi.QR_BATCH_REGIONS
-                                     else "direct"}
+    regions = capi.qr_rank_plan(idx4, m) == capi.QR_BATCH_REGIONS
+    row = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": tuning4,
+           "batch_path": "regions" if regions else "direct"}
+    if regions:
+        row["roofline"], _ = region_roofline(idx4, step, m, index_bytes, ms, peak, peak_kind, stream,
+                                             per_query_c=True, traffic_key="quadrank_region")
+    else:
+        bpq = bytes_per_query(4, layout4, tuning4["load_mode"], per_query_c=True)
+        row.update(algorithmic_bytes_per_query=bpq, roofline_frac=round(gq * bpq / peak, 4))
+    res["quadrank_rank_random_c"] = row
     # prefix_rank(q, 2): characters <= G before q, same index and queries
     ms = best_ms(lambda: capi.qr_prefix_rank(idx4, dq, 2, o), stream)
     res["quadrank_prefix_rank"] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "layout": layout4,
                                    "batch_path": "regions" if capi.qr_rank_plan(idx4, m, 2) == capi.QR_BATCH_REGIONS
                                    else "direct"}
+    idx4.free()
     del o
+    torch.cuda.empty_cache()
+    # rank_4 on the layout its own tuned build picks
     o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
-    t4r = capi.qr_autotune(idx4, dq[: 1 << 24], o4, rank4=True)
-    ms = best_ms(lambda: capi.qr_rank4(idx4, dq, o4), stream)
+    idx4, layout_r4, tuning_r4 = workloads.build_tuned(d4, n4, 4, dq, rank4=True)
+    info = capi.qr_info(idx4)
+    index_bytes = info["bytes_blocks"] + info["bytes_super"]
+    step4 = lambda: capi.qr_rank4(idx4, dq, o4)  # noqa: E731
+    ms = best_ms(step4, stream)
     gq = m / (ms * 1e-3) / 1e9
-    bpq = bytes_per_query(4, layout4, t4r["load_mode"], rank4=True)
-    res["quadrank_rank4"] = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout4, "tuning": t4r,
-                             "algorithmic_bytes_per_query": bpq, "roofline_frac": round(gq * bpq / peak, 4)}
+    regions = capi.qr_rank_plan(idx4, m, 1) == capi.QR_BATCH_REGIONS
+    row = {"Gq_s": round(gq, 3), "ms": round(ms, 3), "layout": layout_r4, "tuning": tuning_r4,
+           "batch_path": "regions" if regions else "direct"}
+    if regions:
+        row["roofline"], _ = region_roofline(idx4, step4, m, index_bytes, ms, peak, peak_kind, stream, rank4=True,
+                                             traffic_key="quadrank4_region")
+        capi.qr_set_batch_mode(idx4, capi.QR_BATCH_DIRECT)
+        ms_d = best_ms(step4, stream)
+        capi.qr_set_batch_mode(idx4, capi.QR_BATCH_AUTO)
+        row["direct_path"] = {"Gq_s": round(m / (ms_d * 1e-3) / 1e9, 3), "ms": round(ms_d, 3),
+                              "algorithmic_bytes_per_query": bytes_per_query(4, layout_r4, tuning_r4["load_mode"],
+                                                                             rank4=True)}
+    else:
+        bpq = bytes_per_query(4, layout_r4, tuning_r4["load_mode"], rank4=True)
+        row.update(algorithmic_bytes_per_query=bpq, roofline_frac=round(gq * bpq / peak, 4))
+    res["quadrank_rank4"] = row
     log(f"[bench] quadrank: {res['quadrank_rank_random_c']['Gq_s']} / {res['quadrank_rank4']['Gq_s']} Gq/s")
     idx4.free()
-    del dq, dc, o4
+    del dq, dc, o4, d4
     torch.cuda.empty_cache()
     return res
 
@@ -616,11 +665,63 @@ def run_fm(args, stream, part="all"):
         res["qfm_count_persistent"]["lf_steps_per_s"] = round(steps / (ms_p * 1e-3))
         res["qfm_count_persistent"]["rank_queries_per_s"] = round(2 * steps / (ms_p * 1e-3))
         res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_config4.json)"
+        res["qfm_count_persistent"]["roofline"] = fm_roofline(steps / (ms_p * 1e-3),
+                                                              info["bytes_rank"] + info["bytes_table"], stream)
     log(f"[bench] qfm: persistent {m / ms_p / 1e3:.1f} M/s, stepwise {m / ms_s / 1e3:.1f} M/s")
     fidx.free()
     res.update(fm_locate_row(dt, text.size, dp, doff, m, ref, ms_p, stream))
     res.update(fm_approx_row(dt, text.size, dp, doff, ref, stream))
     return res
+
+
+def l2_probe(index_bytes, stream):
+    """Random 64-byte record reads from an L2-resident buffer the size of
+    the FM index: (records/s with 4 independent reads per thread and round at
+    full occupancy, dependent record pairs/s at the count kernel's occupancy
+    of 1024 threads per SM)."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nrec = max(1, index_bytes // 64)
+    buf = torch.zeros(nrec * 8, dtype=torch.int64, device="cuda")
+    n0, r0 = sms * 2048, 256
+    n1, r1 = sms * 1024, 512
+    out = torch.empty(max(n0, n1), dtype=torch.int64, device="cuda")
+    ms0 = best_ms(lambda: capi.qr_probe_l2(buf, nrec, 0, n0, r0, 7, out), stream)
+    ms1 = best_ms(lambda: capi.qr_probe_l2(buf, nrec, 1, n1, r1, 7, out), stream)
+    del buf, out
+    torch.cuda.empty_cache()
+    return 4 * n0 * r0 / (ms0 * 1e-3), n1 * r1 / (ms1 * 1e-3)
+
+
+# L2 bytes one rank query reads from a QuadRank16 line (Sec. 4): a position in
+# the lower half (96 of the 224 characters) needs the line's first 32-byte
+# sector (deltas and counted characters); one in the upper half (128 of 224)
+# needs the 16 delta bytes and the second sector.  Uniform over a block:
+QFM_RANK_L2_BYTES = (96 * 32 + 128 * (16 + 32)) / 224
+
+
+def fm_roofline(lf_steps_per_s, index_bytes, stream):
+    """The count kernel against the L2 ceiling.  An LF step takes two rank
+    queries (the lo and hi ends), each reading QFM_RANK_L2_BYTES of its line
+    from the L2-resident index: 82.3 algorithmic L2 bytes per step (the
+    kernel fetches a half-line once when both ends fall in it, so it can
+    read less).  The peak is the L2 probe's random-read rate over a buffer
+    the size of the index, in bytes (64-byte records, two 32-byte sector
+    loads each, four records in flight per thread)."""
+    rec_s, pair_s = l2_probe(index_bytes, stream)
+    step_bytes = 2 * QFM_RANK_L2_BYTES
+    achieved = lf_steps_per_s * step_bytes / 1e9
+    peak = rec_s * 64 / 1e9
+    log(f"[bench] L2 probe: {rec_s / 1e9:.1f} G records/s, {pair_s / 1e9:.1f} G dependent pairs/s")
+    return {"bound": "l2", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": "of measured (qr_probe_l2: random 64-byte records "
+            "from an L2-resident buffer the size of the index, 4 independent reads in flight per thread)",
+            "algorithmic_bytes_per_lf_step": round(step_bytes, 2), "lf_steps_per_s": round(lf_steps_per_s),
+            "l2_records_per_s": round(rec_s), "l2_dependent_pairs_per_s": round(pair_s),
+            "frac_of_dependent_pair_rate": round(lf_steps_per_s / pair_s, 4),
+            "frac_two_64B_lines_per_step": round(lf_steps_per_s * 128 / (rec_s * 64), 4),
+            "index_bytes": index_bytes}
 
 
 def fm_locate_row(dt, n, dp, doff, m, ref, ms_p, stream):
@@ -723,17 +824,57 @@ def run_serving(args):
     return res
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(args, n, text, q):
-    """The oracle as it stands on a bounded sample: the first 2^k queries,
-    answered by one sort + linear sweep over the full text."""
+    """The oracle as it stands on a bounded sample, on all host cores: the
+    first 2^k queries answered by the threaded sort + sweep (the text cut into
+    one chunk per core, each chunk answering its own sorted queries)."""
     import oracle
+    cores = host_cores()
     sample = q[: 1 << args.cpu_log_sample].copy()
+    oracle.rank(text, n, 2, sample[:1024], 1, threads=cores)      # load the library, touch the text
     t0 = time.perf_counter()
-    oracle.rank(text, n, 2, sample, 1)
+    _, rc = oracle.rank(text, n, 2, sample, 1, threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": round(sample.size / dt / 1e9, 6), "unit": "Gqueries/s", "cores": 1, "kind": "oracle",
+    assert rc == 0
+    return {"value": round(sample.size / dt / 1e9, 6), "unit": "Gqueries/s", "cores": cores, "kind": "oracle",
             "sample": f"first 2^{args.cpu_log_sample} of the queries over the full 2^{args.log_n}-bit text "
-                      f"(sort + one linear sweep), {dt:.1f}s"}
+                      f"(threaded sort + sweep, one text chunk per core), {dt:.1f}s"}
+
+
+def cpu_baseline_fm(args, cores=None):
+    """QuadFm on the host: the oracle's brute-force counts (direct comparison
+    at every text position) of a sample of the count workload's patterns,
+    one slice of patterns per core."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2602_04103_gb300 import workloads
+    cores = cores or host_cores()
+    text, pats, off = workloads.fm_inputs(args.fm_log_n, args.fm_m)
+    k = min(args.cpu_fm_sample, off.size - 1)
+    sub_off = off[: k + 1]
+    cuts = np.linspace(0, k, cores + 1).astype(np.int64)
+
+    def part(i):
+        a, b = int(cuts[i]), int(cuts[i + 1])
+        return oracle.count_brute_batch(text, pats[int(sub_off[a]):int(sub_off[b])],
+                                        (sub_off[a:b + 1] - sub_off[a]).astype(np.uint64))
+
+    oracle.count_brute_batch(text, pats[:16], np.array([0, 16], dtype=np.uint64))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(part, range(cores)))
+    dt = time.perf_counter() - t0
+    return {"value": round(k / dt, 1), "unit": "patterns/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {k} patterns of the 10^7-pattern workload over the 2^{args.fm_log_n}-char text, "
+                      f"brute-force counts, {dt:.1f}s"}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -746,13 +887,14 @@ def run_reference(args):
     if rank != 0:
         return
     n = 1 << args.log_n
+    cores = host_cores()
     text, q = workloads.birank_inputs(args.log_n, args.log_m)
     sample = q[: 1 << args.ref_log_sample].copy()
     for _ in range(args.warmup):
-        oracle.rank(text, n, 2, sample[: 1 << 12], 1)
+        oracle.rank(text, n, 2, sample[: 1 << 12], 1, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.rank(text, n, 2, sample, 1)
+        oracle.rank(text, n, 2, sample, 1, threads=cores)
     dt = time.perf_counter() - t0
     value = args.steps * sample.size / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gqueries/s", "n_gpus": ws,
@@ -760,9 +902,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
                                    f"uniform uint64 queries per GPU", "n_bits": n, "queries_per_gpu": 1 << args.log_m},
-            "cpu_baseline": {"value": round(value, 6), "unit": "Gqueries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"2^{args.ref_log_sample} of the queries per step (sort + one sweep over "
-                                       f"the full text)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Gqueries/s", "cores": cores, "kind": "oracle",
+                             "sample": f"2^{args.ref_log_sample} of the queries per step (threaded sort + sweep "
+                                       f"over the full text, one text chunk per core)"},
             "e2e": {"value": round(value, 6), "unit": "Gqueries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -778,9 +920,11 @@ def main():
     ap.add_argument("--log-n4", type=int, default=32)
     ap.add_argument("--fm-log-n", type=int, default=26)
     ap.add_argument("--fm-m", type=int, default=10_000_000)
-    ap.add_argument("--cpu-log-sample", type=int, default=25,
-                    help="log2 of the queries the CPU oracle answers for cpu_baseline (~10 s on one core)")
-    ap.add_argument("--ref-log-sample", type=int, default=23,
+    ap.add_argument("--cpu-log-sample", type=int, default=26,
+                    help="log2 of the queries the CPU oracle answers for cpu_baseline (all host cores)")
+    ap.add_argument("--cpu-fm-sample", type=int, default=2048,
+                    help="patterns of the QuadFm CPU baseline (oracle brute-force counts, all host cores)")
+    ap.add_argument("--ref-log-sample", type=int, default=25,
                     help="log2 of the queries per step of --impl reference")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -276,16 +276,18 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
  *   QR_BATCH_DIRECT   always the direct kernels (one line load per query).
  *   QR_BATCH_REGIONS  region batching for every m < 2^32 (larger batches
  *                     run direct).
- * Scope: qr_rank, qr_rank_c and qr_prefix_rank on the paper and sector
- * layouts.  rank_4 always runs direct (its four 8-byte results would be moved
- * three times, about 129 bytes per query, no less than the direct kernel's
- * 168 bytes at the random-fill rate), and so do chains and the 128-byte line
- * layout.
- * Scratch: 8 bytes per query plus 4 bytes per (region, tile) pair (1/8
- * byte per query) plus 32 bytes of counters (work queue, probe count, abort
- * word), from a memory pool of the library that keeps the memory
- * for later calls (released by qr_release_scratch).  When that memory cannot
- * be had, the call runs the direct kernels instead.
+ * Scope: qr_rank, qr_rank_c, qr_prefix_rank and qr_rank4 on the paper and
+ * sector layouts, for n < 2^37 (a position inside its region must fit 29
+ * bits); chains, the 128-byte line layout and larger texts run direct.
+ * Between the passes a query keeps 4 bytes of result (rank_4: 16), the low
+ * 32 bits of each count, restored from the count at the first position of
+ * its region.
+ * Scratch: 6 bytes per query (a 4-byte key and a 2-byte index inside the
+ * tile; rank_4 16 more), 8 bytes per (region, tile) pair (1/4 byte per
+ * query), an 8 KiB table of region bases and 32 bytes of counters (work
+ * queue, probe count, abort word), from a memory pool of the library that
+ * keeps the memory for later calls (released by qr_release_scratch).  When
+ * that memory cannot be had, the call runs the direct kernels instead.
  * Status bits and sentinel outputs are those of the direct kernels.
  */
 #define QR_BATCH_AUTO 0
@@ -357,6 +359,31 @@ int qr_free(qr_index* idx);
  */
 int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed,
                     uint64_t* out, int queries_per_thread, int block_threads, void* stream);
+
+/*
+ * qr_probe_l2 -- measurement aid: the rate of random 64-byte record reads
+ * (two 32-byte vector loads each) from a buffer small enough to stay in L2,
+ * the memory the QuadFm count kernel reads its index from (App. D: an index
+ * of 2^26 characters is about 20 MB).  It gives the count kernel's ceiling,
+ * as qr_probe_gather gives the HBM ceiling of the rank kernels (Sec. 5.1,
+ * "Lower bounds").
+ *   buf       device buffer of nrec * 64 bytes, 32-byte aligned (the first
+ *             call brings it into L2; time the calls after it).
+ *   mode      0: each thread reads 4 independent records per round (the L2
+ *             random-read throughput); 1: each thread runs one chain, a
+ *             round reads 2 records whose indices depend on the previous
+ *             round's data, as the two interval ends of an LF step depend
+ *             on the step before.
+ *   nthreads  threads in all (one digest each); rounds >= 1 per thread.
+ *             Records read: 4 * nthreads * rounds (mode 0) or
+ *             2 * nthreads * rounds (mode 1).
+ *   seed      splitmix64 seed of the record indices (uniform in [0, nrec)).
+ *   out       device array of nthreads uint64 (digests).
+ * Errors: QR_EINVAL (mode, nrec = 0 or above 2^40, buf unaligned, rounds = 0,
+ * block_threads not 64..256 and a multiple of 32).
+ */
+int qr_probe_l2(const void* buf, uint64_t nrec, int mode, uint64_t nthreads, uint32_t rounds, uint64_t seed,
+                uint64_t* out, int block_threads, void* stream);
 
 #ifdef __cplusplus
 }

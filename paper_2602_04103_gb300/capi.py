@@ -73,6 +73,7 @@ _sig("qr_build_tuned", [vp, u64, i32, i32, C.c_double, vp, u64, i32, i32, vp, vp
 _sig("qr_status", [vp, vp])
 _sig("qr_free", [vp])
 _sig("qr_probe_gather", [vp, u64, i32, i32, u64, u64, vp, i32, i32, vp])
+_sig("qr_probe_l2", [vp, u64, i32, u64, C.c_uint32, u64, vp, i32, vp])
 _sig("qr_set_batch_mode", [vp, i32])
 _sig("qr_rank_plan", [vp, u64, i32, C.POINTER(C.c_int)])
 _sig("qr_region_timing", [vp, i32, C.POINTER(C.c_float)])
@@ -302,6 +303,14 @@ def qr_probe_gather(buf, nrec: int, nbytes: int, m: int, seed: int, out, queries
                     block_threads=256, load_bytes=16, stream=None) -> None:
     _check(lib.qr_probe_gather(ptr(buf), nrec, nbytes, load_bytes, m, seed, ptr(out), queries_per_thread,
                                block_threads, stream_ptr(stream)), "qr_probe_gather")
+
+
+def qr_probe_l2(buf, nrec: int, mode: int, nthreads: int, rounds: int, seed: int, out, block_threads=256,
+                stream=None) -> None:
+    """Random 64-byte record reads from an L2-resident buffer (mode 0:
+    independent, 4 per thread and round; mode 1: dependent pairs)."""
+    _check(lib.qr_probe_l2(ptr(buf), nrec, mode, nthreads, rounds, seed, ptr(out), block_threads,
+                           stream_ptr(stream)), "qr_probe_l2")
 
 
 # ---------------------------------------------------------------- QuadFm (include/quadfm.h)

@@ -157,7 +157,7 @@ int qfm_export(const qfm_index* idx, uint32_t* sa, uint8_t* bwt, uint64_t* table
 const qr_index* qfm_rank_index(const qfm_index* idx) { return idx ? idx->rank : nullptr; }
 
 int qfm_set_policy(qfm_index* idx, int policy) {
-    if (!idx || (policy != kFmPolicyDefault && policy != kFmPolicyKeepIndex))
+    if (!idx || (policy != kFmPolicyDefault && policy != kFmPolicyKeepIndex && policy != kFmPolicyKeepIndexOnly))
         return fail(QR_EINVAL, "qfm_set_policy: NULL index or unknown policy");
     idx->policy = policy;
     return QR_OK;

@@ -17,7 +17,7 @@ struct qfm_index {
     uint32_t* sa = nullptr;    // suffix array (only with QFM_KEEP_SA)
     uint32_t* status = nullptr;
     int device = 0;
-    int policy = 1;            // kFmPolicy* of the persistent count kernel
+    int policy = 2;            // kFmPolicy* of the persistent count kernel
     // locate (built when a sampling factor is given): rows whose suffix
     // starts at a multiple of sa_sample are marked in a BiRank16 index over
     // the n + 1 rows; samples[rank1(marks, row)] = SA[row] / sa_sample.
@@ -42,6 +42,7 @@ struct FmView {
 // L2 policies of the persistent count kernel (qfm_index::policy).
 constexpr int kFmPolicyDefault = 0;   // read-only path, no L1 allocation
 constexpr int kFmPolicyKeepIndex = 1; // index evict-last, patterns/offsets evict-first
+constexpr int kFmPolicyKeepIndexOnly = 2; // index evict-last, patterns/offsets the default L2 policy
 
 // 16-byte index load with the chosen L2 policy (KEEP: the evict-last policy `pol`).
 template <bool KEEP>

@@ -108,10 +108,11 @@ __device__ __forceinline__ int pattern_char(const uint8_t* __restrict__ pat, uin
 
 template <int POLICY, int STRANDS>
 __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
-    constexpr bool kKeep = POLICY == kFmPolicyKeepIndex;
+    constexpr bool kKeep = POLICY == kFmPolicyKeepIndex || POLICY == kFmPolicyKeepIndexOnly;
+    constexpr bool kFirst = POLICY == kFmPolicyKeepIndex;  // pattern / offset stream evict-first
     constexpr bool kBoth = STRANDS == 2;
     const uint64_t pol_last = kKeep ? l2_policy_evict_last() : 0;
-    const uint64_t pol_first = kKeep ? l2_policy_evict_first() : 0;
+    const uint64_t pol_first = kFirst ? l2_policy_evict_first() : 0;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t total = a.m ? a.off[a.m] : 0;  // bytes of the pattern buffer
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
                 if (id < work) {
                     rc = kBoth && id >= a.m;
                     const uint64_t pid = rc ? id - a.m : id;
-                    const uint64_t start = kKeep ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
-                    const uint64_t end = kKeep ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
+                    const uint64_t start = kFirst ? ld_u64_hint(a.off + pid, pol_first) : a.off[pid];
+                    const uint64_t end = kFirst ? ld_u64_hint(a.off + pid + 1, pol_first) : a.off[pid + 1];
                     const uint64_t len = end - start;
                     uint64_t lo0 = 0, hi0 = 0;
                     if (end < start || end > total || !fm_start(a.v, a.pat + start, len, rc, lo0, hi0, i)) {
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 4) count_persistent(CountArgs a) {
         // ---- one LF step for every active lane
         if (active) {
             if (i >= 0 && lo < hi) {
-                const int raw = pattern_char<kKeep>(a.pat, total, cur, win, pol_first);
+                const int raw = pattern_char<kFirst>(a.pat, total, cur, win, pol_first);
                 cur += dir;
                 win.k += dir;
                 const int c = rc && raw <= 3 ? 3 - raw : raw;
@@ -257,12 +258,13 @@ using CountFn = void (*)(CountArgs);
 
 CountFn count_fn(int policy, int strands) {
     if (policy == kFmPolicyKeepIndex) return strands == 2 ? count_persistent<1, 2> : count_persistent<1, 1>;
+    if (policy == kFmPolicyKeepIndexOnly) return strands == 2 ? count_persistent<2, 2> : count_persistent<2, 1>;
     return strands == 2 ? count_persistent<0, 2> : count_persistent<0, 1>;
 }
 
 unsigned persistent_grid(int policy, int strands = 1) {
-    static thread_local int per_sm[2][2] = {{0, 0}, {0, 0}};
-    int& k = per_sm[policy & 1][strands == 2];
+    static thread_local int per_sm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int& k = per_sm[policy >= 0 && policy <= 2 ? policy : 1][strands == 2];
     if (k == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, count_fn(policy, strands), kThreads, 0);
         if (e != cudaSuccess || k < 1) k = 1;

@@ -514,4 +514,16 @@ int qr_probe_gather(const void* buf, uint64_t nrec, int bytes, int load_bytes, u
                         (cudaStream_t)stream);
 }
 
+int qr_probe_l2(const void* buf, uint64_t nrec, int mode, uint64_t nthreads, uint32_t rounds, uint64_t seed,
+                uint64_t* out, int block_threads, void* stream) {
+    if (mode != 0 && mode != 1) return fail(QR_EINVAL, "qr_probe_l2: mode must be 0 or 1");
+    if (nrec == 0 || !buf || (nthreads > 0 && !out)) return fail(QR_EINVAL, "qr_probe_l2: empty buffer");
+    if (nrec > (1ull << 40)) return fail(QR_EINVAL, "qr_probe_l2: nrec above 2^40");
+    if (((uintptr_t)buf & 31) != 0) return fail(QR_EINVAL, "qr_probe_l2: buf must be 32-byte aligned");
+    if (rounds == 0) return fail(QR_EINVAL, "qr_probe_l2: rounds must be >= 1");
+    if (block_threads < 64 || block_threads > 256 || (block_threads & 31))
+        return fail(QR_EINVAL, "qr_probe_l2: block_threads must be 64..256, a multiple of 32");
+    return launch_probe_l2(buf, nrec, mode, nthreads, rounds, seed, out, block_threads, (cudaStream_t)stream);
+}
+
 }  // extern "C"

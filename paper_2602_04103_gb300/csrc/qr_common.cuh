@@ -186,6 +186,40 @@ __device__ __forceinline__ uint8_t ld_stream_u8(const uint8_t* p) {
     asm volatile("ld.global.cs.u8 %0, [%1];" : "=h"(v) : "l"(p));
     return (uint8_t)v;
 }
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint16_t ld_stream_u16(const uint16_t* p) {
+    uint16_t v;
+    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_stream_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_stream_v4u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ uint2 ld_stream_v2u32(const uint32_t* p) {
+    uint2 v;
+    asm volatile("ld.global.cs.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_stream_v4u32(const uint32_t* p) {
+    uint4 v;
+    asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_stream_v2u64(uint64_t* p, uint64_t a, uint64_t b) {
+    asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+// One 32-byte store (sm_100+ 256-bit vector store): a whole L2 sector written
+// by one request, so the L2 needs no fill from DRAM.  p must be 32-byte aligned.
+__device__ __forceinline__ void st_stream_v4u64(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
 __device__ __forceinline__ void st_stream_u64(uint64_t* p, uint64_t v) {
     asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -406,4 +440,6 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
 int region_trim();
 int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint64_t m, uint64_t seed, uint64_t* out,
                  int k, int threads, cudaStream_t s);
+int launch_probe_l2(const void* buf, uint64_t nrec, int mode, uint64_t nthreads, uint32_t rounds, uint64_t seed,
+                    uint64_t* out, int threads, cudaStream_t s);
 }  // namespace qr

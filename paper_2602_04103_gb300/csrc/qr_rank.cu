@@ -487,6 +487,44 @@ __global__ void __launch_bounds__(1024) probe_kernel(const uint4* __restrict__ b
     }
 }
 
+// L2 probe: random 64-byte records (two 32-byte loads each) of a buffer small
+// enough to stay in L2.  MODE 0: every thread issues four independent
+// records per round, their data folded into one digest (the random-request
+// throughput of L2).  MODE 1: every thread runs one chain; a round reads two
+// records whose indices come from the chain state, and the next state mixes
+// both records' data, as the two interval ends of an LF step depend on the
+// step before (the latency-bound rate of such chains at this occupancy).
+template <int MODE>
+__global__ void __launch_bounds__(256) probe_l2_kernel(const uint4* __restrict__ buf, uint64_t nrec, uint32_t rounds,
+                                                       uint64_t seed, uint64_t nthreads, uint64_t* __restrict__ out) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    uint64_t st = probe_mix(seed + (t + 1) * 0x9E3779B97F4A7C15ull);
+    uint64_t d = 0;
+    for (uint32_t r = 0; r < rounds; r++) {
+        if (MODE == 0) {
+            u64x4 x[4][2];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint64_t rec = mulhi64(probe_mix(st + (uint64_t)k * 0xD1B54A32D192ED03ull), nrec);
+                x[k][0] = ld_line32(buf + 4 * rec);
+                x[k][1] = ld_line32(buf + 4 * rec + 2);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) d ^= x[k][0].a ^ x[k][0].d ^ x[k][1].b ^ x[k][1].c;
+            st = probe_mix(st + 1);
+        } else {
+            const uint64_t ra = mulhi64(st, nrec), rb = mulhi64(probe_mix(st ^ 0xD1B54A32D192ED03ull), nrec);
+            const u64x4 a0 = ld_line32(buf + 4 * ra), a1 = ld_line32(buf + 4 * ra + 2);
+            const u64x4 b0 = ld_line32(buf + 4 * rb), b1 = ld_line32(buf + 4 * rb + 2);
+            const uint64_t v = a0.a ^ a0.d ^ a1.b ^ a1.c ^ b0.b ^ b0.c ^ b1.a ^ b1.d;
+            d ^= v;
+            st = probe_mix(st + v + 1);
+        }
+    }
+    st_stream_u64(out + t, d);
+}
+
 }  // namespace
 
 int launch_rank(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
@@ -569,6 +607,17 @@ int launch_probe(const void* buf, uint64_t nrec, int bytes, int load_bytes, uint
     uint64_t grid = (uint64_t)per_sm * device_props().sms;
     if (grid > tiles) grid = tiles;
     fn<<<(unsigned)grid, threads, 0, s>>>((const uint4*)buf, nrec, m, seed, out);
+    QR_CUDA_TRY(cudaGetLastError());
+    return QR_OK;
+}
+
+int launch_probe_l2(const void* buf, uint64_t nrec, int mode, uint64_t nthreads, uint32_t rounds, uint64_t seed,
+                    uint64_t* out, int threads, cudaStream_t s) {
+    if (nthreads == 0) return QR_OK;
+    const uint64_t grid = (nthreads + threads - 1) / threads;
+    if (grid > 0x7fffffffull) return fail(QR_EINVAL, "qr_probe_l2: too many threads");
+    auto fn = mode == 0 ? probe_l2_kernel<0> : probe_l2_kernel<1>;
+    fn<<<(unsigned)grid, threads, 0, s>>>((const uint4*)buf, nrec, rounds, seed, nthreads, out);
     QR_CUDA_TRY(cudaGetLastError());
     return QR_OK;
 }

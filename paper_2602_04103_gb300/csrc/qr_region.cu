@@ -8,30 +8,44 @@
 // about m / L times (2^28 queries over the 3.5e7 lines of a 2^34-bit
 // BiRank16 index: 7.75 times), so for such batches it pays to move the
 // queries instead of the lines.  Every query is still answered from its own
-// line by the paper's query arithmetic (Sec. 3 Eq. 1, Sec. 4 rank1); only
-// the order in which lines are visited changes, so results are identical.
+// line by the paper's query arithmetic (Sec. 3 Eq. 1, Sec. 4 rank1 and
+// rank_4); only the order in which lines are visited changes, so results are
+// identical.
 //
-// Three passes over a batch cut into tiles of 8192 queries and 256 regions
-// (region = q >> shift, the smallest shift that maps [0, n] onto 256):
+// Passes over a batch cut into tiles of 8192 queries and 256 regions
+// (region = q >> shift, the smallest shift that maps [0, n] onto 256; the
+// path needs shift <= 29, i.e. n < 2^37):
 //   sort    tile t sorts its queries by region in shared memory (a counting
-//           sort) and writes them back to its own slice of the work array;
-//           an item packs the query, its symbol and its index inside the
-//           tile; the start and length of each region's run go to a
-//           region-major segment table, seg[r * tiles + t];
+//           sort) and writes them back to its own slice of two arrays: a
+//           4-byte key (the position inside its region, its symbol, a bad
+//           flag) and a 2-byte index inside the tile (with the symbol and
+//           the flag again); the start and length of each region's run go to
+//           a region-major segment table, seg[r * tiles + t];
+//   base    rank and prefix_rank only: the result at the first position of
+//           every region, for every symbol (1024 queries);
 //   rank    warps take steps of 16 segments of the table, in table order,
 //           from a device work queue, i.e. region after region, so the lines
-//           of the one or two regions in flight stay in L2; each item is
-//           replaced by its result (same packing);
-//   unsort  tile t reads its slice back, puts every result at its index in
-//           shared memory and writes the tile's outputs in order.
-// The sort and unsort passes read and write whole tiles (coalesced); the rank
-// pass reads runs of ~32 items per (region, tile).  The work array (8 bytes
-// per query) and the segment table come from a memory pool of the library
-// that keeps them for later calls.  Measured on GB300 and kept out: a count
-// pass plus a global scan to place runs region-major (one more read of the
-// queries, and __match_any_sync grouping ran at 1.2 TB/s); blocks walking 64
-// runs with a shared-memory search (barrier-bound); strided warp steps
-// (warps drift apart, the regions in flight outgrow L2); bulk L2 prefetch
+//           of the one or two regions in flight stay in L2; rank and
+//           prefix_rank replace each key by the low 32 bits of its result,
+//           rank_4 writes the low 32 bits of its four counts (16 bytes) at
+//           the key's place in an array of its own;
+//   unsort  tile t reads its slice back, restores every result from its low
+//           32 bits and its region's base (results of one region differ from
+//           the base by less than 2^29), puts it at its index in shared
+//           memory and writes the tile's outputs in order.
+// Per query that moves 8 (q) + 6 bytes in the sort, 4 + 4 in the rank pass
+// and 6 + 8 in the unsort (rank_4: 4 + 16 and 18 + 32), plus the index once
+// per batch.  Writing rank_4's rows straight from the rank pass was measured
+// and dropped: a scattered 32-byte row, even written by one 32-byte store,
+// made the L2 read ~99 bytes from DRAM per query (ncu, 2^24 queries over
+// 2^30 characters) against the ~27 the pass needs.  The sort and unsort passes read and write whole tiles
+// (coalesced); the rank pass reads runs of ~32 keys per (region, tile).  The
+// scratch arrays come from a memory pool of the library that keeps them for
+// later calls.  Measured on GB300 and kept out: a count pass plus a global
+// scan to place runs region-major (one more read of the queries, and
+// __match_any_sync grouping ran at 1.2 TB/s); blocks walking 64 runs with a
+// shared-memory search (barrier-bound); strided warp steps (warps drift
+// apart, the regions in flight outgrow L2); bulk L2 prefetch
 // (cp.async.bulk.prefetch.L2) of the next region's lines and of the next
 // runs (slower).
 //
@@ -54,15 +68,27 @@ constexpr int kPassBlocks = 2;      // resident sort / unsort blocks per SM
 constexpr int kPer = kTile / kPassThreads;
 constexpr int kRankThreads = 256;
 
-// Item: bits 0..44 the position q (later its result, both < 2^45), 45..46
-// the symbol, 47..59 the index inside the tile, 63 set for a query that is
-// out of range (q > n) or has a bad symbol.
-constexpr uint64_t kValMask = (1ull << 45) - 1;
-constexpr int kSymShift = 45;
-constexpr int kIdxShift = 47;
-constexpr uint64_t kIdxBits = (uint64_t)(kTile - 1) << kIdxShift;
-constexpr uint64_t kBadItem = 1ull << 63;
+// Key (4 bytes, written by the sort, read by the rank pass): bits 0..28 the
+// position inside its region (q - (region << shift) < 2^shift <= 2^29), bit 29
+// set for a query that is out of range (q > n) or has a bad symbol, bits
+// 30..31 the symbol.  The rank pass of rank / prefix_rank overwrites it with
+// the low 32 bits of the result.
+// Index (2 bytes): bits 0..12 the index inside the tile, 13..14 the symbol,
+// bit 15 the bad flag.
+constexpr int kMaxShift = 29;
+constexpr uint32_t kKeyBad = 1u << 29;
+constexpr int kKeySymShift = 30;
+constexpr uint16_t kIdxBad = 0x8000;
+constexpr int kIdxSymShift = 13;
 constexpr uint32_t kAll = 0xffffffffu;
+constexpr int kBaseSyms = 4;  // base table: kRegions x 4 symbols of uint64
+
+__device__ __forceinline__ uint32_t make_key(uint64_t q, uint32_t c, bool bad, int shift) {
+    return bad ? kKeyBad : (uint32_t)(q & ((1ull << shift) - 1)) | (c << kKeySymShift);
+}
+__device__ __forceinline__ uint16_t make_idx(uint32_t i, uint32_t c, bool bad) {
+    return (uint16_t)(i | ((c & 3u) << kIdxSymShift) | (bad ? kIdxBad : 0u));
+}
 
 __device__ __forceinline__ uint32_t region_of(uint64_t q, int shift) {
     const uint64_t r = q >> shift;
@@ -148,18 +174,23 @@ __global__ void __launch_bounds__(256) region_probe(const uint64_t* __restrict__
 // comes from a shared-memory atomic; a warp whose queries all fall in one
 // region (sorted batches) takes one atomic for all its lanes.  The second
 // phase reads the tile's queries again (L2 hits) rather than keeping 16 of
-// them per thread in registers across the block-wide scan.
+// them per thread in registers across the block-wide scan.  This form (plain
+// loads and stores) serves query or symbol arrays that are not 16-byte
+// aligned; region_sort_tma below serves the rest.
 template <bool VEC>
 __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const uint64_t* __restrict__ q,
                                                                const uint8_t* __restrict__ cv, uint32_t c0,
                                                                uint32_t sigma, uint64_t m, uint64_t n, int shift,
-                                                               uint64_t tiles, uint64_t* __restrict__ work,
-                                                               uint32_t* __restrict__ seg, uint32_t* status,
+                                                               uint64_t tiles, uint32_t* __restrict__ keys,
+                                                               uint16_t* __restrict__ idxs,
+                                                               uint32_t* __restrict__ seg,
+                                                               uint32_t* __restrict__ segt, uint32_t* status,
                                                                Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* stage = (uint64_t*)smem;                      // kTile items in region order
-    uint16_t* rank_in = (uint16_t*)(smem + kTile * 8);      // rank of query i inside its region
-    uint32_t* h = (uint32_t*)(smem + kTile * 10);           // region sizes, then starts
+    uint32_t* key_st = (uint32_t*)smem;                     // kTile keys in region order
+    uint16_t* idx_st = (uint16_t*)(smem + kTile * 4);       // their indices
+    uint16_t* rank_in = (uint16_t*)(smem + kTile * 6);      // rank of query i inside its region
+    uint32_t* h = (uint32_t*)(smem + kTile * 8);            // region sizes, then starts
     uint32_t* ws = h + kRegions;
     if (!regions_chosen(gate)) return;
     const int lane = threadIdx.x & 31;
@@ -201,6 +232,7 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const u
     if (threadIdx.x < kRegions) {
         h[threadIdx.x] = st;
         seg[(uint64_t)threadIdx.x * tiles + t] = st | (sz << 16);
+        segt[t * kRegions + threadIdx.x] = st | (sz << 16);
     }
     __syncthreads();
     {
@@ -218,9 +250,9 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const u
             if (i < len) {
                 const bool range_bad = x[k] > n, sym_bad = cw[k] >= sigma;
                 flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                const uint64_t item = ((uint64_t)i << kIdxShift) |
-                                      (range_bad || sym_bad ? kBadItem : (x[k] | ((uint64_t)cw[k] << kSymShift)));
-                stage[h[region_of(x[k], shift)] + rank_in[i]] = item;
+                const uint32_t pos = h[region_of(x[k], shift)] + rank_in[i];
+                key_st[pos] = make_key(x[k], cw[k], range_bad || sym_bad, shift);
+                idx_st[pos] = make_idx(i, cw[k], range_bad || sym_bad);
             }
         }
     }
@@ -228,14 +260,17 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_sort(const u
 #pragma unroll
     for (int k = 0; k < kPer; k++) {
         const uint32_t p = threadIdx.x + k * kPassThreads;
-        if (p < len) work[base + p] = stage[p];
+        if (p < len) {
+            keys[base + p] = key_st[p];
+            idxs[base + p] = idx_st[p];
+        }
     }
     __syncthreads();  // the next tile reuses the shared arrays
     }
     if (flags) atomicOr(status, flags);
 }
 
-constexpr size_t kSortSmem = (size_t)kTile * 10 + (kRegions + 8) * 4;
+constexpr size_t kSortSmem = (size_t)kTile * 8 + (kRegions + 8) * 4;
 
 // ---------------------------------------------------------------- sort with TMA bulk copies
 // The same counting sort, with the tile moved by the TMA unit: each block
@@ -282,6 +317,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
     return false;
 }
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+    for (int k = 0; k < 8; k++)
+        if (mbar_wait_bounded(bar, parity)) return true;
+    return false;
+}
 __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(sdst)),
@@ -301,7 +341,10 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 constexpr int kTmaThreads = 1024;             // one block per SM: more warps hide the shared-memory latency
 constexpr int kTmaPer = kTile / kTmaThreads;
-constexpr size_t kSortTmaSmem = (size_t)kTile * 8 * 3 + (size_t)kTile * 2 + (size_t)kTile * 2 + (kRegions + 8) * 4 + 16;
+// queries (two buffers) + keys + indices + ranks inside the regions + symbols
+// (two buffers) + region sizes, the scan's scratch and two mbarriers
+constexpr size_t kSortTmaSmem = (size_t)kTile * 8 * 2 + (size_t)kTile * 4 + (size_t)kTile * 2 + (size_t)kTile * 2 +
+                                (size_t)kTile * 2 + (kRegions + 8) * 4 + 16;
 static_assert(kSortTmaSmem <= 227 * 1024 - 64, "sort pass: shared memory above the per-block limit");
 
 // Full tiles take a branch-free form of the region count that keeps each
@@ -312,14 +355,17 @@ template <bool VEC>
 __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t* __restrict__ q,
                                                                    const uint8_t* __restrict__ cv, uint32_t c0,
                                                                    uint32_t sigma, uint64_t m, uint64_t n, int shift,
-                                                                   uint64_t tiles, uint64_t* __restrict__ work,
-                                                                   uint32_t* __restrict__ seg, uint32_t* status,
+                                                                   uint64_t tiles, uint32_t* __restrict__ keys,
+                                                                   uint16_t* __restrict__ idxs,
+                                                                   uint32_t* __restrict__ seg,
+                                                                   uint32_t* __restrict__ segt, uint32_t* status,
                                                                    Gate gate, int withhold) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* raw0 = (uint64_t*)smem;                        // queries of the tile, in order (two buffers)
     uint64_t* raw1 = raw0 + kTile;
-    uint64_t* stage = raw1 + kTile;                          // items in region order
-    uint16_t* rank_in = (uint16_t*)(stage + kTile);          // rank of query i inside its region
+    uint32_t* key_st = (uint32_t*)(raw1 + kTile);            // keys in region order
+    uint16_t* idx_st = (uint16_t*)(key_st + kTile);          // their indices
+    uint16_t* rank_in = idx_st + kTile;                      // rank of query i inside its region
     uint8_t* csym0 = (uint8_t*)(rank_in + kTile);            // per-query symbols of the tile (VEC, two buffers)
     uint8_t* csym1 = csym0 + kTile;
     uint32_t* h = (uint32_t*)(csym1 + kTile);                // region sizes, then starts
@@ -347,6 +393,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
     }
     uint32_t flags = 0, j = 0;
     bool pending = false;  // thread 0: a load issued into the other buffer and not yet waited for
+    // thread 0: the load of the current tile's buffer was issued (only the
+    // test hook's first tile has none)
+    bool issued = full(t) && !(withhold && blockIdx.x == 0);
     for (; t < tiles; t += gridDim.x, j++) {
         const uint32_t b = j & 1;
         uint64_t* raw = b ? raw1 : raw0;
@@ -355,6 +404,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
         const uint64_t tn = t + gridDim.x;
         if (threadIdx.x == 0) {
+            if (j > 0) issued = pending;
             pending = false;
             if (full(tn)) {  // the other buffers were last read before the previous iteration's final barrier
                 fence_proxy_async();
@@ -425,8 +475,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         if (threadIdx.x < kRegions) {
             h[threadIdx.x] = st;
             seg[(uint64_t)threadIdx.x * tiles + t] = st | (sz << 16);
+            segt[t * kRegions + threadIdx.x] = st | (sz << 16);
         }
-        if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read `stage`
+        if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's stores have read the staging arrays
         __syncthreads();
         if (pipe) {
             uint32_t pos[kTmaPer], cc[kTmaPer];
@@ -443,8 +494,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
                 const uint32_t i = threadIdx.x + k * kTmaThreads;
                 const bool range_bad = x[k] > n, sym_bad = cc[k] >= sigma;
                 flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                stage[pos[k]] = ((uint64_t)i << kIdxShift) |
-                                (range_bad || sym_bad ? kBadItem : (x[k] | ((uint64_t)cc[k] << kSymShift)));
+                key_st[pos[k]] = make_key(x[k], cc[k], range_bad || sym_bad, shift);
+                idx_st[pos[k]] = make_idx(i, cc[k], range_bad || sym_bad);
             }
         }
         if (!pipe) {
@@ -456,27 +507,37 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
                     const uint32_t c = VEC ? (uint32_t)csym[i] : c0;
                     const bool range_bad = x > n, sym_bad = c >= sigma;
                     flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                    const uint64_t item = ((uint64_t)i << kIdxShift) |
-                                          (range_bad || sym_bad ? kBadItem : (x | ((uint64_t)c << kSymShift)));
-                    stage[h[region_of(x, shift)] + rank_in[i]] = item;
+                    const uint32_t pos = h[region_of(x, shift)] + rank_in[i];
+                    key_st[pos] = make_key(x, c, range_bad || sym_bad, shift);
+                    idx_st[pos] = make_idx(i, c, range_bad || sym_bad);
                 }
             }
         }
-        fence_proxy_async();  // this thread's writes to `stage` are visible to the bulk store
+        fence_proxy_async();  // this thread's writes to the staging arrays are visible to the bulk stores
         __syncthreads();
         if (len == kTile) {
-            if (threadIdx.x == 0) bulk_store(work + base, stage, kTile * 8);
+            if (threadIdx.x == 0) {
+                bulk_store(keys + base, key_st, kTile * 4);
+                bulk_store(idxs + base, idx_st, kTile * 2);
+            }
         } else {
-            for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) work[base + p] = stage[p];
-            __syncthreads();  // `stage` is rewritten by the next tile (none: this is the last one)
+            for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
+                keys[base + p] = key_st[p];
+                idxs[base + p] = idx_st[p];
+            }
+            __syncthreads();  // the staging arrays are rewritten by the next tile (none: this is the last one)
         }
     }
     if (threadIdx.x == 0) {
-        // copies in flight after a timed-out wait (this tile's, and the next
-        // one's if issued): wait for them, bounded
+        // copies still in flight after a timed-out wait (this tile's load if
+        // it was issued, and the next tile's if issued) write this block's
+        // shared memory: wait for them before the block exits, up to 8 more
+        // bounded waits (2 s) each.  A copy of valid global memory completes
+        // well within that; if one did not, the status already holds
+        // QR_ETIMEOUT and the context is to be treated as suspect.
         if (s_abort) {
-            mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1);
-            if (pending) mbar_wait_bounded(&bar[(j & 1) ^ 1], ((j + 1) >> 1) & 1);
+            if (issued) mbar_wait_drain(&bar[j & 1], (j >> 1) & 1);
+            if (pending) mbar_wait_drain(&bar[(j & 1) ^ 1], ((j + 1) >> 1) & 1);
         }
         bulk_wait_all();  // every store is complete before the block exits
     }
@@ -485,37 +546,193 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
 
 
 // ---------------------------------------------------------------- unsort
-__global__ void __launch_bounds__(kPassThreads, kPassBlocks) region_unsort(const uint64_t* __restrict__ work, uint64_t m,
-                                                                 uint64_t tiles, uint64_t* __restrict__ out,
-                                                                 Gate gate) {
+// Tile t's results back in query order.  The rank pass left the low 32 bits
+// of each result in place of its key; the result itself is
+// base + (low32 - low32(base)) mod 2^32, with base = the result at the first
+// position of the query's region for the query's symbol (bases[r * 4 + c]),
+// because results of one region exceed their base by less than 2^shift <=
+// 2^29.  The region of each sorted place comes from the tile's segment
+// entries: every warp writes the region number over the places of its
+// regions' runs (reg8), then every thread restores its results and puts
+// them at their index inside the tile, and the tile is written out in order.
+constexpr int kUnsortThreads = 512;
+constexpr int kUnsortPer = kTile / kUnsortThreads;
+constexpr int kUnsortChunks = kUnsortPer / 4;  // chunks of four consecutive sorted places per thread
+constexpr size_t kUnsortSmem = (size_t)kTile * 8 + (size_t)kRegions * kBaseSyms * 8 + (size_t)kRegions * 4 +
+                                (size_t)kTile;
+
+__global__ void __launch_bounds__(kUnsortThreads, 2) region_unsort(const uint32_t* __restrict__ keys,
+                                                                   const uint16_t* __restrict__ idxs,
+                                                                   const uint32_t* __restrict__ segt,
+                                                                   const uint64_t* __restrict__ bases, uint64_t m,
+                                                                   uint64_t tiles, uint64_t* __restrict__ out,
+                                                                   Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* res = (uint64_t*)smem;
+    uint64_t* res = (uint64_t*)smem;                        // the tile's results in query order
+    uint64_t* btab = res + kTile;                           // bases[kRegions * 4]
+    uint32_t* tseg = (uint32_t*)(btab + kRegions * kBaseSyms);  // the tile's segment entries
+    uint8_t* reg8 = (uint8_t*)(tseg + kRegions);             // region of every sorted place
     if (!regions_chosen(gate)) return;
+    for (uint32_t i = threadIdx.x; i < kRegions * kBaseSyms; i += blockDim.x) btab[i] = bases[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this thread's segment entry of the block's next tile, loaded a tile ahead
+    uint32_t e_next = 0;
+    if (threadIdx.x < kRegions && blockIdx.x < tiles) e_next = __ldg(segt + blockIdx.x * kRegions + threadIdx.x);
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const uint64_t base = t * kTile;
-    const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
-    uint64_t it[kPer];
+        const uint64_t base = t * kTile;
+        const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
+        // the tile's keys and indices first (their DRAM latency overlaps the
+        // region fill below), four consecutive places per load: chunk j of
+        // this thread holds places 4 (threadIdx.x + 512 j) .. + 3
+        uint4 kv[kUnsortChunks];
+        uint2 ix[kUnsortChunks];
 #pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        const uint32_t p = threadIdx.x + k * kPassThreads;
-        it[k] = p < len ? ld_stream_u64(work + base + p) : 0;
-    }
+        for (int j = 0; j < kUnsortChunks; j++) {
+            const uint32_t p = 4 * (threadIdx.x + j * kUnsortThreads);
+            if (p + 4 <= len) {
+                kv[j] = ld_stream_v4u32(keys + base + p);
+                ix[j] = ld_stream_v2u32((const uint32_t*)(idxs + base + p));
+            } else {
+                uint32_t k4[4] = {0, 0, 0, 0}, i4[4] = {0, 0, 0, 0};
+                for (uint32_t u = 0; u < 4; u++)
+                    if (p + u < len) {
+                        k4[u] = ld_stream_u32(keys + base + p + u);
+                        i4[u] = ld_stream_u16(idxs + base + p + u);
+                    }
+                kv[j] = make_uint4(k4[0], k4[1], k4[2], k4[3]);
+                ix[j] = make_uint2(i4[0] | (i4[1] << 16), i4[2] | (i4[3] << 16));
+            }
+        }
+        if (threadIdx.x < kRegions) {
+            tseg[threadIdx.x] = e_next;
+            const uint64_t tn = t + gridDim.x;
+            if (tn < tiles) e_next = __ldg(segt + tn * kRegions + threadIdx.x);
+        }
+        __syncthreads();
+        for (uint32_t r = warp; r < kRegions; r += kUnsortThreads / 32) {
+            const uint32_t e = tseg[r];
+            const uint32_t st = e & 0xFFFFu, ln = e >> 16;
+            for (uint32_t k = lane; k < ln; k += 32) reg8[st + k] = (uint8_t)r;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        const uint32_t p = threadIdx.x + k * kPassThreads;
-        if (p < len) res[(it[k] & kIdxBits) >> kIdxShift] = (it[k] & kBadItem) ? ~0ull : (it[k] & kValMask);
-    }
-    __syncthreads();
+        for (int j = 0; j < kUnsortChunks; j++) {
+            const uint32_t p = 4 * (threadIdx.x + j * kUnsortThreads);
+            const uint32_t rg = *(const uint32_t*)(reg8 + p);   // the regions of the four places
+            const uint32_t k4[4] = {kv[j].x, kv[j].y, kv[j].z, kv[j].w};
+            const uint32_t i4[4] = {ix[j].x & 0xFFFFu, ix[j].x >> 16, ix[j].y & 0xFFFFu, ix[j].y >> 16};
 #pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        const uint32_t i = threadIdx.x + k * kPassThreads;
-        if (i < len) st_stream_u64(out + base + i, res[i]);
-    }
-    __syncthreads();  // the next tile reuses res
+            for (int u = 0; u < 4; u++) {
+                if (p + u < len) {
+                    const uint32_t r = (rg >> (8 * u)) & 0xFFu;
+                    const uint64_t b = btab[r * kBaseSyms + ((i4[u] >> kIdxSymShift) & 3u)];
+                    const uint64_t v = b + (uint32_t)(k4[u] - (uint32_t)b);
+                    res[i4[u] & (kTile - 1)] = (i4[u] & kIdxBad) ? ~0ull : v;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kUnsortPer; k++) {
+            const uint32_t i = threadIdx.x + k * kUnsortThreads;
+            if (i < len) st_stream_u64(out + base + i, res[i]);
+        }
+        // the next tile writes tseg and reg8 before its first barrier and res
+        // only after its second: every read of this tile is done by then
     }
 }
 
-constexpr size_t kUnsortSmem = (size_t)kTile * 8;
+// rank_4: tile t's rows back in query order.  The rank pass left the low 32
+// bits of the four counts of every sorted place (16 bytes, res16); each count
+// is restored from its region's base for that symbol as in region_unsort.
+// The tile's 16-byte rows and their regions are first put at their query
+// index in shared memory (128 KiB + 16 KiB: one block of 1024 threads per
+// SM), then every thread writes whole 32-byte output rows in order.
+constexpr int kUnsort4Threads = 1024;
+constexpr int kUnsort4Per = kTile / kUnsort4Threads;
+constexpr uint16_t kRowBad = 0x100;  // (qreg) a bad query: a row of UINT64_MAX
+constexpr size_t kUnsort4Smem = (size_t)kTile * 16 + (size_t)kTile * 2 + (size_t)kRegions * kBaseSyms * 8 +
+                                (size_t)kRegions * 4 + (size_t)kTile;
+static_assert(kUnsort4Smem <= 227 * 1024, "rank_4 unsort: shared memory above the per-block limit");
+
+__global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint32_t* __restrict__ res16,
+                                                                     const uint16_t* __restrict__ idxs,
+                                                                     const uint32_t* __restrict__ segt,
+                                                                     const uint64_t* __restrict__ bases, uint64_t m,
+                                                                     uint64_t tiles, uint64_t* __restrict__ out4,
+                                                                     int out4_32, Gate gate) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4* rel = (uint4*)smem;                               // the tile's low 32 bits of the counts, query order
+    uint64_t* btab = (uint64_t*)(rel + kTile);               // bases[kRegions * 4]
+    uint16_t* qreg = (uint16_t*)(btab + kRegions * kBaseSyms);  // region of every query (kRowBad: bad)
+    uint32_t* tseg = (uint32_t*)(qreg + kTile);              // the tile's segment entries
+    uint8_t* reg8 = (uint8_t*)(tseg + kRegions);             // region of every sorted place
+    if (!regions_chosen(gate)) return;
+    for (uint32_t i = threadIdx.x; i < kRegions * kBaseSyms; i += blockDim.x) btab[i] = bases[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t e_next = 0;
+    if (threadIdx.x < kRegions && blockIdx.x < tiles) e_next = __ldg(segt + blockIdx.x * kRegions + threadIdx.x);
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t base = t * kTile;
+        const uint32_t len = (uint32_t)(m - base < kTile ? m - base : kTile);
+        uint4 rv[kUnsort4Per];
+        uint16_t ix[kUnsort4Per];
+#pragma unroll
+        for (int k = 0; k < kUnsort4Per; k++) {
+            const uint32_t p = threadIdx.x + k * kUnsort4Threads;
+            rv[k] = p < len ? ld_stream_v4u32(res16 + 4 * (base + p)) : make_uint4(0, 0, 0, 0);
+            ix[k] = p < len ? ld_stream_u16(idxs + base + p) : (uint16_t)0;
+        }
+        if (threadIdx.x < kRegions) {
+            tseg[threadIdx.x] = e_next;
+            const uint64_t tn = t + gridDim.x;
+            if (tn < tiles) e_next = __ldg(segt + tn * kRegions + threadIdx.x);
+        }
+        __syncthreads();
+        for (uint32_t r = warp; r < kRegions; r += kUnsort4Threads / 32) {
+            const uint32_t e = tseg[r];
+            const uint32_t st = e & 0xFFFFu, ln = e >> 16;
+            for (uint32_t k = lane; k < ln; k += 32) reg8[st + k] = (uint8_t)r;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kUnsort4Per; k++) {
+            const uint32_t p = threadIdx.x + k * kUnsort4Threads;
+            if (p < len) {
+                const uint32_t i = ix[k] & (kTile - 1);
+                rel[i] = rv[k];
+                qreg[i] = (ix[k] & kIdxBad) ? kRowBad : (uint16_t)reg8[p];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kUnsort4Per; k++) {
+            const uint32_t i = threadIdx.x + k * kUnsort4Threads;
+            if (i < len) {
+                const uint16_t r = qreg[i];
+                uint64_t v[4];
+                if (r & kRowBad) {
+                    v[0] = v[1] = v[2] = v[3] = ~0ull;
+                } else {
+                    const uint4 x = rel[i];
+                    const uint32_t lo[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const uint64_t b = btab[r * kBaseSyms + c];
+                        v[c] = b + (uint32_t)(lo[c] - (uint32_t)b);
+                    }
+                }
+                uint64_t* o = out4 + 4 * (base + i);
+                if (out4_32) {
+                    st_stream_v4u64(o, v[0], v[1], v[2], v[3]);
+                } else {
+                    st_stream_v2u64(o, v[0], v[1]);
+                    st_stream_v2u64(o + 2, v[2], v[3]);
+                }
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------- rank
 // Paper layout (BiRank16 / QuadRank16): the 32-byte half of the line that
@@ -649,25 +866,47 @@ __device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD,
     return quad_finish1(L.s, quad_delta(w0, w1, (int)c), x, L.pos, (int)c);
 }
 
+// rank_4: the four counts of a query from the loads of the prefix form (all
+// four superblock offsets).
+template <bool SECTOR>
+__device__ __forceinline__ void region_finish4(const RegionLoad<SECTOR, true, true>& L, uint64_t r[4]) {
+    const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
+    if (SECTOR) {
+        quad_sector_finish4(s4, L.X, L.pos, r);
+    } else {
+        const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
+        const bool upper = L.pos >= 128;
+        quad_finish4(s4, upper ? L.w0 : L.X.a, upper ? L.w1 : L.X.b, x, L.pos, r);
+    }
+}
+
+// Modes of the rank pass: rank(q, c) (scalar or per-query symbol), rank_4,
+// prefix_rank(q, c).
+constexpr int kModeRank = 0;
+constexpr int kModeRank4 = 1;
+constexpr int kModePrefix = 2;
+
 // The rank pass.  Every warp walks its own runs of SEGS consecutive
 // segments of the region-major table, taking its steps in table order from a
 // device work queue (QUEUE) or by a stride: the lengths are scanned with
-// shuffles, the runs' items are laid end to end and each lane answers items
-// lane, lane + 32, ..., K of them per round; the run holding an item is found
-// by a log2(SEGS)-step search over the starts held in the lanes.  The items
+// shuffles, the runs' keys are laid end to end and each lane answers keys
+// lane, lane + 32, ..., K of them per round; the run holding a key is found
+// by a log2(SEGS)-step search over the starts held in the lanes.  The keys
 // of round t + P are loaded while round t fetches its lines and counts, and
 // the table entries of the next step while this step runs.  No shared
 // memory, no block barrier.  With the queue the steps in flight stay close
 // together in the table, so the regions they touch stay in L2.
 template <int K>
 struct ItemSlot {
-    uint64_t it[K];
-    uint32_t at[K];  // place in the work array (m < 2^32)
+    uint32_t key[K];
+    uint32_t at[K];   // place in the key array (m < 2^32)
+    uint32_t reg[K];  // region of the key's run
 };
 
 template <int K, int SEGS>
-__device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint64_t* __restrict__ work, uint32_t j0,
-                                            uint32_t total, uint32_t start, uint32_t sbase, int lane) {
+__device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint32_t* __restrict__ keys, uint32_t j0,
+                                            uint32_t total, uint32_t start, uint32_t sbase, uint32_t sreg,
+                                            int lane) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const uint32_t j = j0 + lane + 32 * k;
@@ -680,33 +919,39 @@ __device__ __forceinline__ void fetch_items(ItemSlot<K>& S, const uint64_t* __re
         }
         const uint32_t sb = __shfl_sync(kAll, sbase, sidx);
         const uint32_t s0 = __shfl_sync(kAll, start, sidx);
+        S.reg[k] = __shfl_sync(kAll, sreg, sidx);
         S.at[k] = sb + (j - s0);
-        S.it[k] = j < total ? ld_stream_u64(work + S.at[k]) : kBadItem;
+        S.key[k] = j < total ? ld_stream_u32(keys + S.at[k]) : kKeyBad;
     }
 }
 
 struct RankPassArgs {
-    uint64_t* work;
+    uint32_t* keys;
+    uint32_t* res16;  // rank_4: 4 x 32 bits per sorted place
     const uint32_t* seg;
     uint64_t nseg, tiles;
     const uint4* lines;
     const void* supers;
     uint32_t c0;
+    int shift;
     unsigned long long* queue;  // step counter (QUEUE variants), zero at launch
     Gate gate;
 };
 
-template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, bool PREFIX = false,
+template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, int MODE = kModeRank,
           bool EL = false, bool N32 = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
+    constexpr bool kS4 = MODE != kModeRank;  // loads of all four superblock offsets
+    constexpr bool kR4 = MODE == kModeRank4;
     if (!regions_chosen(a.gate)) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (kRankThreads / 32);
     constexpr int kWarpSegs = SEGS;
     const uint64_t nsteps = (a.nseg + kWarpSegs - 1) / kWarpSegs;
     constexpr uint32_t kRound = 32 * K;
-    uint64_t* __restrict__ work = a.work;
+    uint32_t* __restrict__ keys = a.keys;
     const uint64_t pol = EL ? l2_policy_evict_last() : 0;
+    const uint64_t qmask = (1ull << a.shift) - 1;
     // the warp's next step: a strided sequence, or (QUEUE) taken in table order
     // from a device counter, so that the steps in flight stay close together
     auto next_step = [&](uint64_t cur) -> uint64_t {
@@ -716,70 +961,104 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
         return __shfl_sync(kAll, v, 0);
     };
     uint64_t g = QUEUE ? next_step(0) : (uint64_t)blockIdx.x * (kRankThreads / 32) + (threadIdx.x >> 5);
-    // this lane's segment of the warp's current step: length and first item
-    // (nseg = 256 tiles < 2^27 and m < 2^32: 32-bit arithmetic)
-    auto seg_of = [&](uint64_t step, uint32_t& len, uint32_t& sbase) {
+    // this lane's segment of the warp's current step: length, first key and
+    // region (nseg = 256 tiles < 2^27 and m < 2^32: 32-bit arithmetic)
+    auto seg_of = [&](uint64_t step, uint32_t& len, uint32_t& sbase, uint32_t& sreg) {
         len = 0;
         sbase = 0;
+        sreg = 0;
         const uint64_t w = step * kWarpSegs + lane;
         if (lane < kWarpSegs && step < nsteps && w < a.nseg) {
             const uint32_t e = __ldg(a.seg + w);
             len = e >> 16;
-            sbase = ((uint32_t)w % (uint32_t)a.tiles) * kTile + (e & 0xFFFFu);
+            sreg = (uint32_t)w / (uint32_t)a.tiles;
+            sbase = ((uint32_t)w - sreg * (uint32_t)a.tiles) * kTile + (e & 0xFFFFu);
         }
     };
-    uint32_t len;
-    uint32_t sbase;
-    seg_of(g, len, sbase);
+    uint32_t len, sbase, sreg;
+    seg_of(g, len, sbase, sreg);
     while (g < nsteps) {
         const uint64_t gn = next_step(g);
-        uint32_t nlen;
-        uint32_t nbase;
-        seg_of(gn, nlen, nbase);  // the next step's table entries, loaded early
+        uint32_t nlen, nbase, nreg;
+        seg_of(gn, nlen, nbase, nreg);  // the next step's table entries, loaded early
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < kWarpSegs; o <<= 1) {
             const uint32_t u = __shfl_up_sync(kAll, incl, o);
             if (lane >= o) incl += u;
         }
-        const uint32_t start = incl - len;  // first item of this lane's segment
+        const uint32_t start = incl - len;  // first key of this lane's segment
         const uint32_t total = __shfl_sync(kAll, incl, kWarpSegs - 1);
         constexpr int PS = P > 0 ? P : 1;
         ItemSlot<K> S[PS];
 #pragma unroll
-        for (int p = 0; p < P; p++) fetch_items<K, SEGS>(S[p], work, p * kRound, total, start, sbase, lane);
+        for (int p = 0; p < P; p++)
+            fetch_items<K, SEGS>(S[p], keys, p * kRound, total, start, sbase, sreg, lane);
         for (uint32_t j0 = 0; j0 < total; j0 += kRound) {
             ItemSlot<K> cur;
             if (P == 0) {
-                fetch_items<K, SEGS>(cur, work, j0, total, start, sbase, lane);
+                fetch_items<K, SEGS>(cur, keys, j0, total, start, sbase, sreg, lane);
             } else {
                 cur = S[0];
 #pragma unroll
                 for (int p = 0; p + 1 < P; p++) S[p] = S[p + 1];
                 if (j0 + P * kRound < total)
-                    fetch_items<K, SEGS>(S[PS - 1], work, j0 + P * kRound, total, start, sbase, lane);
+                    fetch_items<K, SEGS>(S[PS - 1], keys, j0 + P * kRound, total, start, sbase, sreg, lane);
             }
-            RegionLoad<SECTOR, QUAD, PREFIX> L[K];
+            RegionLoad<SECTOR, QUAD, kS4> L[K];
+            uint64_t qk[K];
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                const bool bad = cur.it[k] & kBadItem;
-                const uint64_t qq = bad ? 0 : cur.it[k] & kValMask;  // bad items (and idle lanes) read line 0
-                const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                region_issue<SECTOR, QUAD, PREFIX, EL, N32>(L[k], a.lines, a.supers, qq, c, pol);
+                const bool bad = cur.key[k] & kKeyBad;
+                // bad keys (and idle lanes) read line 0
+                qk[k] = bad ? 0 : ((uint64_t)cur.reg[k] << a.shift) | (cur.key[k] & qmask);
+                const uint32_t c = VEC ? cur.key[k] >> kKeySymShift : a.c0;
+                region_issue<SECTOR, QUAD, kS4, EL, N32>(L[k], a.lines, a.supers, qk[k], c, pol);
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
-                if (cur.it[k] & kBadItem) continue;
-                const uint64_t qq = cur.it[k] & kValMask;
-                const uint32_t c = VEC ? (uint32_t)(cur.it[k] >> kSymShift) & 3u : a.c0;
-                const uint64_t r = region_finish<SECTOR, QUAD, PREFIX>(L[k], qq, c);
-                st_stream_u64(work + cur.at[k], r | (cur.it[k] & kIdxBits));
+                if (kR4) {
+                    if constexpr (kR4) {
+                        if (cur.key[k] & kKeyBad) continue;
+                        uint64_t r[4];
+                        region_finish4<SECTOR>(L[k], r);
+                        st_stream_v4u32(a.res16 + 4 * (uint64_t)cur.at[k], (uint32_t)r[0], (uint32_t)r[1],
+                                        (uint32_t)r[2], (uint32_t)r[3]);
+                    }
+                } else {
+                    if (cur.key[k] & kKeyBad) continue;
+                    const uint32_t c = VEC ? cur.key[k] >> kKeySymShift : a.c0;
+                    const uint64_t r = region_finish<SECTOR, QUAD, kS4>(L[k], qk[k], c);
+                    st_stream_u32(keys + cur.at[k], (uint32_t)r);
+                }
             }
         }
         len = nlen;
         sbase = nbase;
+        sreg = nreg;
         g = gn;
     }
+}
+
+// The base table of rank and prefix_rank: bases[r * 4 + c] = the result at
+// the first position of region r (r << shift) for symbol c (prefix_rank: up
+// to c), by the same query arithmetic as the rank pass; 0 for regions that
+// start beyond n (no query falls there) and for c >= sigma.
+template <bool SECTOR, bool QUAD, bool PREFIX, bool N32>
+__global__ void __launch_bounds__(256) region_base(const uint4* __restrict__ lines, const void* __restrict__ supers,
+                                                  uint64_t n, int shift, uint64_t* __restrict__ bases, Gate gate) {
+    if (!regions_chosen(gate)) return;
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= kRegions * kBaseSyms) return;
+    const uint32_t r = id / kBaseSyms, c = id % kBaseSyms;
+    const uint64_t q = (uint64_t)r << shift;
+    uint64_t v = 0;
+    if (q <= n && (QUAD || c < 2)) {
+        RegionLoad<SECTOR, QUAD, PREFIX> L;
+        region_issue<SECTOR, QUAD, PREFIX, false, N32>(L, lines, supers, q, c, 0);
+        v = region_finish<SECTOR, QUAD, PREFIX>(L, q, c);
+    }
+    bases[id] = v;
 }
 
 // ---------------------------------------------------------------- scratch pool
@@ -820,29 +1099,39 @@ int set_smem(F fn, size_t bytes) {
 }
 
 using RankFn = void (*)(RankPassArgs);
+using BaseFn = void (*)(const uint4*, const void*, uint64_t, int, uint64_t*, Gate);
 
 // Rank-pass variants (items per lane and round, resident blocks per SM,
 // rounds of items loaded ahead, segments per warp-step, steps from a device
-// queue, evict-last index loads).  Measured on GB300 (2^28 uniform queries,
-// sector layout): 0 1.78 ms, 1 2.11 ms, 2 1.78 ms, 3 1.91 ms.
+// queue, evict-last index loads).  Measured on GB300 with 8-byte work items
+// (2^28 uniform queries, sector layout): 0 1.78 ms, 1 2.11 ms, 2 1.78 ms,
+// 3 1.91 ms.
 template <bool SECTOR, bool QUAD, bool VEC, bool N32 = false>
 RankFn pick_variant(int v) {
     switch (v) {
-        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, false, N32>;
-        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true, false, false, N32>;
-        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, false, true, N32>;
-        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true, false, false, N32>;
+        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, false, N32>;
+        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true, kModeRank, false, N32>;
+        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, true, N32>;
+        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true, kModeRank, false, N32>;
         default: return nullptr;
     }
 }
 
-// n32: sector layout with n < 2^37 (the 32-bit line-index division)
-RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix, bool n32) {
-    if (prefix) {  // sigma 4, one symbol, default variant
+// mode: kModeRank / kModeRank4 / kModePrefix (the last two sigma 4, one
+// symbol or none, default variant); n32: sector layout with n < 2^37 (the
+// 32-bit line-index division)
+RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, int mode, bool n32) {
+    if (mode == kModeRank4) {
         if (sector)
-            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, true, false, true>
-                       : region_rank<true, true, false, 2, 4, 1, 16, true, true>;
-        return region_rank<false, true, false, 2, 4, 1, 16, true, true>;
+            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, kModeRank4, false, true>
+                       : region_rank<true, true, false, 2, 4, 1, 16, true, kModeRank4>;
+        return region_rank<false, true, false, 2, 4, 1, 16, true, kModeRank4>;
+    }
+    if (mode == kModePrefix) {
+        if (sector)
+            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, kModePrefix, false, true>
+                       : region_rank<true, true, false, 2, 4, 1, 16, true, kModePrefix>;
+        return region_rank<false, true, false, 2, 4, 1, 16, true, kModePrefix>;
     }
     if (sector && n32) {
         if (quad) return vec ? pick_variant<true, true, true, true>(v) : pick_variant<true, true, false, true>(v);
@@ -856,13 +1145,33 @@ RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, bool prefix, bo
     return vec ? pick_variant<false, false, true>(v) : pick_variant<false, false, false>(v);
 }
 
+BaseFn pick_region_base(bool sector, bool quad, bool prefix, bool n32) {
+    if (prefix) {
+        if (sector) return n32 ? region_base<true, true, true, true> : region_base<true, true, true, false>;
+        return region_base<false, true, true, false>;
+    }
+    if (sector) {
+        if (quad) return n32 ? region_base<true, true, false, true> : region_base<true, true, false, false>;
+        return n32 ? region_base<true, false, false, true> : region_base<true, false, false, false>;
+    }
+    return quad ? region_base<false, true, false, false> : region_base<false, false, false, false>;
+}
+
+int region_shift(uint64_t n) {
+    int shift = 0;
+    while ((n >> shift) >= kRegions) shift++;
+    return shift;
+}
+
 }  // namespace
 
 bool region_supported(const qr_index* idx, int rank4) {
-    // rank_4 stays direct: its four 8-byte results would be moved three times
-    // (about 129 bytes per query in all), no less than the direct kernel's
-    // 168 bytes at the random-fill rate
-    return (rank4 == 0 || (rank4 == 2 && idx->sigma == 4)) && idx->layout != QR_LAYOUT_LINE128;
+    // rank, rank_c, prefix_rank (sigma 4) and rank_4 (sigma 4) on the paper
+    // and sector layouts, for texts whose regions fit the 29-bit key
+    // (n < 2^37); chains and the 128-byte line layout run direct
+    if (idx->layout == QR_LAYOUT_LINE128) return false;
+    if (region_shift(idx->n) > kMaxShift) return false;
+    return rank4 == 0 || idx->sigma == 4;
 }
 
 bool region_auto(const qr_index* idx, uint64_t m) {
@@ -875,37 +1184,45 @@ bool region_auto(const qr_index* idx, uint64_t m) {
     return bytes > l2 / 2 && m * 64 >= bytes;
 }
 
-
-
 int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, int c, uint64_t m, uint64_t* out,
                         int rank4, cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct) {
     if (m == 0) return QR_OK;
     if (m >= (1ull << 32)) return fail(QR_EINVAL, "region batch: m must be below 2^32");
+    const int shift = region_shift(idx->n);
+    if (shift > kMaxShift) return fail(QR_EINVAL, "region batch: n must be below 2^37");
+    const int mode = rank4 == 1 ? kModeRank4 : rank4 == 2 ? kModePrefix : kModeRank;
     const uint64_t tiles = (m + kTile - 1) / kTile;
     const uint64_t nseg = (uint64_t)kRegions * tiles;
-    int shift = 0;
-    while ((idx->n >> shift) >= kRegions) shift++;
     cudaMemPool_t pool;
     int rc = region_pool(&pool);
     if (rc) return rc;
-    const size_t work_bytes = (m * 8 + 255) & ~(size_t)255;
-    const size_t seg_bytes = (nseg * 4 + 255) & ~(size_t)255;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    // the segment table twice: region-major (the rank pass walks it) and
+    // tile-major (the unsort reads one tile's entries in one coalesced load)
+    const size_t key_bytes = up(m * 4), idx_bytes = up(m * 2), seg_bytes = up(nseg * 4);
+    const size_t res_bytes = mode == kModeRank4 ? up(m * 16) : 0;  // rank_4: the four counts' low 32 bits
+    const size_t base_bytes = (size_t)kRegions * kBaseSyms * 8;
     void* buf = nullptr;
     // under stream capture the scratch becomes a graph memory node
     // (cudaMallocAsync); otherwise it comes from the library's pool
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(e, "region batch: capture status");
-    const size_t scratch = work_bytes + seg_bytes + 32;
+    const size_t scratch = key_bytes + idx_bytes + 2 * seg_bytes + base_bytes + res_bytes + 32;
     e = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&buf, scratch, s)
                                              : cudaMallocFromPoolAsync(&buf, scratch, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(QR_ENOMEM, "region batch: no scratch memory");
     }
-    uint64_t* work = (uint64_t*)buf;
-    uint32_t* seg = (uint32_t*)((char*)buf + work_bytes);
-    unsigned long long* counters = (unsigned long long*)((char*)buf + work_bytes + seg_bytes);  // queue, probe, abort
+    char* cur = (char*)buf;
+    uint32_t* keys = (uint32_t*)cur;
+    uint16_t* idxs = (uint16_t*)(cur += key_bytes);
+    uint32_t* seg = (uint32_t*)(cur += idx_bytes);
+    uint32_t* segt = (uint32_t*)(cur += seg_bytes);
+    uint64_t* bases = (uint64_t*)(cur += seg_bytes);
+    uint32_t* res16 = (uint32_t*)(cur += base_bytes);
+    unsigned long long* counters = (unsigned long long*)(cur + res_bytes);  // queue, probe, abort
     static std::once_flag once[64];
     static int once_rc[64];
     const int dev = device_props().device & 63;
@@ -915,9 +1232,11 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort_tma<false>, kSortTmaSmem);
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_sort_tma<true>, kSortTmaSmem);
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_unsort, kUnsortSmem);
+        if (!once_rc[dev]) once_rc[dev] = set_smem(region_unsort4, kUnsort4Smem);
     });
     rc = once_rc[dev];
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR, vec = cvec != nullptr;
+    const bool n32 = sector && idx->n < (1ull << 37);
     const int sms = device_props().sms;
     Gate gate{nullptr, 0, counters + 2};
     if (!rc) {
@@ -933,31 +1252,38 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         gate = Gate{counters + 1, (unsigned long long)probes * kClusterMax, counters + 2};
         if (!rc) rc = (*direct)(gate.count, gate.limit);
     }
+    if (!rc) {
+        // the bases the unsort pass restores the results from
+        BaseFn bf = pick_region_base(sector, quad, mode == kModePrefix, n32);
+        bf<<<kRegions * kBaseSyms / 256, 256, 0, s>>>(idx->lines, idx->supers, idx->n, shift, bases, gate);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_base");
+    }
     if (!rc && marks) cudaEventRecord(marks[0], s);
     if (!rc) {
         const uint64_t grid = tiles < (uint64_t)sms * kPassBlocks ? tiles : (uint64_t)sms * kPassBlocks;
-        // the bulk copies need 16-byte aligned query and work arrays
-        const bool tma = (((uintptr_t)q | (uintptr_t)work | (uintptr_t)cvec) & 15) == 0;
+        // the bulk copies need 16-byte aligned query and symbol arrays (the
+        // key and index arrays are)
+        const bool tma = (((uintptr_t)q | (uintptr_t)cvec) & 15) == 0;
         if (tma) {
             const uint64_t g1 = tiles < (uint64_t)sms ? tiles : (uint64_t)sms;
             auto sort_fn = vec ? region_sort_tma<true> : region_sort_tma<false>;
             sort_fn<<<(unsigned)g1, kTmaThreads, kSortTmaSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
                                                                      (uint32_t)idx->sigma, m, idx->n, shift, tiles,
-                                                                     work, seg, idx->status, gate,
+                                                                     keys, idxs, seg, segt, idx->status, gate,
                                                                      idx->region_withhold);
         } else {
             auto sort_fn = vec ? region_sort<true> : region_sort<false>;
             sort_fn<<<(unsigned)grid, kPassThreads, kSortSmem, s>>>(q, vec ? cvec : nullptr, (uint32_t)c,
                                                                     (uint32_t)idx->sigma, m, idx->n, shift, tiles,
-                                                                    work, seg, idx->status, gate);
+                                                                    keys, idxs, seg, segt, idx->status, gate);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_sort");
     }
     if (!rc && marks) cudaEventRecord(marks[1], s);
     if (!rc) {
-        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, rank4 == 2,
-                                     sector && idx->n < (1ull << 37));
+        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, mode, n32);
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;
@@ -966,13 +1292,15 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         uint64_t grid = (uint64_t)per_sm * sms;
         if (grid > need) grid = need;
         RankPassArgs ra;
-        ra.work = work;
+        ra.keys = keys;
+        ra.res16 = res16;
         ra.seg = seg;
         ra.nseg = nseg;
         ra.tiles = tiles;
         ra.lines = idx->lines;
         ra.supers = idx->supers;
         ra.c0 = (uint32_t)c;
+        ra.shift = shift;
         ra.queue = counters;
         ra.gate = gate;
         fn<<<(unsigned)grid, kRankThreads, 0, s>>>(ra);
@@ -980,11 +1308,19 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         if (e != cudaSuccess) rc = cuda_fail(e, "region_rank");
     }
     if (!rc && marks) cudaEventRecord(marks[2], s);
-    if (!rc) {
-        const uint64_t grid = tiles < (uint64_t)sms * kPassBlocks ? tiles : (uint64_t)sms * kPassBlocks;
-        region_unsort<<<(unsigned)grid, kPassThreads, kUnsortSmem, s>>>(work, m, tiles, out, gate);
+    if (!rc && mode != kModeRank4) {
+        const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
+        region_unsort<<<(unsigned)grid, kUnsortThreads, kUnsortSmem, s>>>(keys, idxs, segt, bases, m, tiles, out,
+                                                                          gate);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort");
+    }
+    if (!rc && mode == kModeRank4) {
+        const uint64_t grid = tiles < (uint64_t)sms ? tiles : (uint64_t)sms;
+        region_unsort4<<<(unsigned)grid, kUnsort4Threads, kUnsort4Smem, s>>>(
+            res16, idxs, segt, bases, m, tiles, out, ((uintptr_t)out & 31) == 0, gate);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort4");
     }
     if (!rc && marks) cudaEventRecord(marks[3], s);
     cudaFreeAsync(buf, s);

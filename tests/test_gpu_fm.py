@@ -118,6 +118,29 @@ def test_counts_mid_size(stepwise):
     assert np.array_equal(got[sample], oracle.count_brute_batch(t, sub, sub_off))
 
 
+@pytest.mark.parametrize("policy", [0, 1, 2])
+def test_counts_every_l2_policy(policy):
+    """The count kernel's L2 policies (plain loads; index evict-last with the
+    pattern stream evict-first; index evict-last alone) give the oracle's
+    counts, both strands included."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 19
+    t = synth.fm_text(24, n)
+    idx = build_fm(t, keep_sa=False)
+    capi.qfm_set_policy(idx, policy)
+    pats, off = synth.patterns(25, t, 50_001, 1, 150, sub_rate=0.01)
+    want = oracle.count_sa(t, oracle.suffix_array(t), pats, off)
+    assert np.array_equal(counts(idx, pats, off), want)
+    both = torch.empty(2 * (off.size - 1), dtype=torch.int64, device="cuda")
+    capi.qfm_count_ex(idx, dev_u8(pats), dev_u64(off), both, capi.QFM_BOTH_STRANDS)
+    assert np.array_equal(host_u64(both)[: off.size - 1], want)
+    assert capi.qfm_status(idx) == 0
+    with pytest.raises(capi.QRError):
+        capi.qfm_set_policy(idx, 3)
+    idx.free()
+
+
 def test_counts_edge_patterns():
     from paper_2602_04103_gb300 import capi
     n = 5000

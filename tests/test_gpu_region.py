@@ -3,7 +3,7 @@ against the oracle, bit-exact.
 
 Region batching sorts every tile of 8192 queries by text region (256
 regions), answers the sorted runs region after region and puts the results
-back in query order.  The cases cover several tiles with a ragged last tile, every region,
+back in query order (rank_4 too, with its four counts per query).  The cases cover several tiles with a ragged last tile, every region,
 out-of-range positions and symbols inside the batch, degenerate orders (all
 queries equal, sorted, reversed, everything in the first or last region),
 tiny texts where regions are single positions, batch sizes around the tile
@@ -287,7 +287,11 @@ def test_auto_rule_small_index_stays_direct():
     assert capi.qr_rank_plan(idx, 1 << 26, 1) == capi.QR_BATCH_DIRECT
     capi.qr_set_batch_mode(idx, capi.QR_BATCH_REGIONS)
     assert capi.qr_rank_plan(idx, 1 << 26) == capi.QR_BATCH_REGIONS
-    assert capi.qr_rank_plan(idx, 1 << 26, 1) == capi.QR_BATCH_DIRECT   # rank_4 always direct
+    assert capi.qr_rank_plan(idx, 1 << 26, 1) == capi.QR_BATCH_DIRECT   # rank_4 is sigma 4 only
+    idx4 = build(synth.dna_uniform(6, n), n, 4, 1)
+    capi.qr_set_batch_mode(idx4, capi.QR_BATCH_REGIONS)
+    assert capi.qr_rank_plan(idx4, 1 << 26, 1) == capi.QR_BATCH_REGIONS
+    assert capi.qr_rank_plan(idx4, 1 << 26, 2) == capi.QR_BATCH_REGIONS
     idx128 = build(synth.bits(5, n, 0.5), n, 2, 2)
     capi.qr_set_batch_mode(idx128, capi.QR_BATCH_REGIONS)
     assert capi.qr_rank_plan(idx128, 1 << 26) == capi.QR_BATCH_DIRECT   # 128-byte lines always direct
@@ -347,4 +351,149 @@ def test_sort_wait_runs_out_and_reports_timeout():
     capi.qr_set_region_fault(idx, False)
     capi.qr_rank(idx, dq, 1, out)
     assert np.array_equal(host_u64(out), expect(words, n, 2, q, 1))
+    assert capi.qr_status(idx) == 0
+
+
+def rank4_regions(idx, q):
+    """qr_rank4 through region batching."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    assert capi.qr_rank_plan(idx, q.size, 1) == (capi.QR_BATCH_REGIONS if q.size else capi.QR_BATCH_DIRECT)
+    dq = dev_u64(q)
+    out = torch.full((q.size, 4), -7, dtype=torch.int64, device="cuda")
+    capi.qr_rank4(idx, dq, out)
+    return host_u64(out).reshape(-1, 4)
+
+
+def expect4(words, n, q):
+    ok = q <= n
+    want = np.full((q.size, 4), U64MAX, dtype=np.uint64)
+    if ok.any():
+        w, rc = oracle.rank4(words, n, q[ok])
+        assert rc == 0
+        want[ok] = w
+    return want
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_rank4_tiles_ragged(layout):
+    """rank_4 through region batching: every query's row of four counts;
+    out-of-range positions give rows of UINT64_MAX and QR_ERANGE.  An output
+    not 16-byte aligned is refused."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S4 + 777
+    words = synth.dna_gc_runs(synth.base_seed(70), n, 0.4, 0.05, 10, 1000)
+    idx = regions_index(words, n, 4, layout)
+    m = 2 * TILE + 4099
+    q = synth.queries(synth.base_seed(71), n, m)
+    got = rank4_regions(idx, q)
+    assert np.array_equal(got, expect4(words, n, q))
+    assert capi.qr_status(idx) == 0
+    q[::101] = n + 3
+    q[7] = U64MAX
+    q[8] = n
+    got = rank4_regions(idx, q)
+    assert np.array_equal(got, expect4(words, n, q))
+    assert capi.qr_status(idx) == capi.QR_ERANGE
+    flat = torch.full((4 * m + 2,), -7, dtype=torch.int64, device="cuda")
+    with pytest.raises(capi.QRError):
+        capi.qr_rank4(idx, dev_u64(q), flat[1:-1].view(m, 4))
+    # 16 bytes past a 32-byte boundary: rows written as two 16-byte stores
+    out = flat[2:].view(m, 4)
+    assert out.data_ptr() % 32 == 16
+    capi.qr_rank4(idx, dev_u64(q), out)
+    assert np.array_equal(host_u64(out).reshape(-1, 4), expect4(words, n, q))
+    assert capi.qr_status(idx) == capi.QR_ERANGE
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("order", ["equal", "sorted", "reversed", "last_region", "zero"])
+def test_rank4_degenerate_orders_and_unaligned_queries(layout, order):
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 4 * S4 + 31
+    words = synth.dna_uniform(synth.base_seed(72), n)
+    idx = regions_index(words, n, 4, layout)
+    m = 2 * TILE + 5
+    q = synth.queries(synth.base_seed(73), n, m)
+    if order == "equal":
+        q[:] = q[0]
+    elif order == "sorted":
+        q.sort()
+    elif order == "reversed":
+        q = np.sort(q)[::-1].copy()
+    elif order == "last_region":
+        q = np.uint64(n) - q % np.uint64(max(1, n >> 9))
+    else:
+        q[:] = 0
+    assert np.array_equal(rank4_regions(idx, q), expect4(words, n, q))
+    # queries 8 bytes past a 16-byte boundary: the plain sort pass
+    qq = np.concatenate([[np.uint64(0)], q]).astype(np.uint64)
+    dq = dev_u64(qq)[1:]
+    assert dq.data_ptr() % 16 == 8
+    out = torch.empty((m, 4), dtype=torch.int64, device="cuda")
+    capi.qr_rank4(idx, dq, out)
+    assert np.array_equal(host_u64(out).reshape(-1, 4), expect4(words, n, q))
+    assert capi.qr_status(idx) == 0
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("n", [0, 1, 2, 223, 224, 225, 255, 256, 1000])
+def test_rank4_tiny_texts_and_sizes(layout, n):
+    words = synth.dna_uniform(n + 21, n)
+    idx = regions_index(words, n, 4, layout)
+    q = np.concatenate([np.arange(n + 1, dtype=np.uint64), synth.queries(n + 22, n, 3000)])
+    assert np.array_equal(rank4_regions(idx, q), expect4(words, n, q))
+    for m in (1, 31, TILE - 1, TILE + 1):
+        qm = synth.queries(n + 23 + m, n, m)
+        assert np.array_equal(rank4_regions(idx, qm), expect4(words, n, qm))
+
+
+def test_rank4_agrees_with_direct_large_batch():
+    """2^22 rank_4 queries over 2^29 chars (a 153-179 MB index, larger than
+    half of L2, with more than two queries per 128 bytes of it): the
+    automatic rule takes region batching, and it agrees with the direct
+    kernels on every output; a sample matches the oracle."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 29
+    words = synth.dna_uniform(synth.base_seed(74), n)
+    q = synth.queries(synth.base_seed(75), n, 1 << 22)
+    dq = dev_u64(q)
+    for layout in LAYOUTS:
+        idx = build(words, n, 4, layout)
+        assert capi.qr_rank_plan(idx, q.size, 1) == capi.QR_BATCH_REGIONS
+        a = torch.empty((q.size, 4), dtype=torch.int64, device="cuda")
+        b = torch.empty_like(a)
+        capi.qr_rank4(idx, dq, a)
+        capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
+        capi.qr_rank4(idx, dq, b)
+        assert torch.equal(a, b), layout
+        sample = np.arange(0, q.size, 991)
+        want, rc = oracle.rank4(words, n, q[sample])
+        assert rc == 0 and np.array_equal(host_u64(a).reshape(-1, 4)[sample], want)
+        assert capi.qr_status(idx) == 0
+        idx.free()
+
+
+def test_region_rank4_timeout_leaves_output_untouched():
+    """The sort pass's bounded wait running out (test hook) stops the rank_4
+    passes too: QR_ETIMEOUT, the output untouched, the next call right."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S4 + 7
+    words = synth.dna_uniform(synth.base_seed(76), n)
+    idx = regions_index(words, n, 4, 1)
+    m = 4 * TILE
+    q = synth.queries(synth.base_seed(77), n, m)
+    dq = dev_u64(q)
+    out = torch.full((m, 4), -7, dtype=torch.int64, device="cuda")
+    capi.qr_set_region_fault(idx, True)
+    capi.qr_rank4(idx, dq, out)
+    assert capi.qr_status(idx) == capi.QR_ETIMEOUT
+    assert (out == -7).all()
+    capi.qr_set_region_fault(idx, False)
+    capi.qr_rank4(idx, dq, out)
+    assert np.array_equal(host_u64(out).reshape(-1, 4), expect4(words, n, q))
     assert capi.qr_status(idx) == 0

@@ -27,8 +27,9 @@ def test_noalloc_matches_qfm_count_two_calls_in_a_row():
         capi.qfm_count(idx, dp, doff, want)
         for _ in range(2):                               # two calls in a row
             got = torch.full((m,), -1, dtype=torch.int64, device="cuda")
-            capi.lib.qfm_count_noalloc(idx, capi.ptr(dp), capi.ptr(doff), m, capi.ptr(got),
-                                       capi.stream_ptr())
+            rc = capi.lib.qfm_count_noalloc(idx, capi.ptr(dp), capi.ptr(doff), m, capi.ptr(got),
+                                            capi.stream_ptr())
+            assert rc == capi.QR_OK, capi.lib.qr_last_error()
             torch.cuda.synchronize()
             assert np.array_equal(host_u64(got), host_u64(want))
     assert capi.qfm_status(idx) == 0

@@ -172,12 +172,18 @@ def traffic_record(kernel: str):
     return d if h.hexdigest() == d["sha256"] else None
 
 
+LAYOUT_NAMES_BI = {0: "BiRank16 (3.28% overhead)", 1: "BiRank16x2 sector layout (6.72% overhead)",
+                   2: "BiRank16 on 128-byte lines (1.69% overhead)", 3: "BiRank32 (6.67% overhead)",
+                   4: "BiRank32x2 (14.3% overhead)"}
+
+
 def bytes_per_query(sigma: int, layout: int, load_mode: int, rank4: bool = False, per_query_c: bool = False):
     """Algorithmic bytes of one query: the index bytes it must read (the
-    32-byte half-line of the sector layout, the 64-byte line of the paper
-    layout, the 128-byte line of the line layout) + the 8-byte query + the
-    result (8, or 32 for rank_4) + 1 byte of symbol when symbols are per query."""
-    index = {0: 64, 1: 32, 2: 128}[layout]
+    32-byte half-line of the sector layout and of BiRank32x2, the 64-byte line
+    of the paper layout and of BiRank32 / QuadRank32, the 128-byte line of the
+    line layout) + the 8-byte query + the result (8, or 32 for rank_4) + 1 byte
+    of symbol when symbols are per query."""
+    index = {0: 64, 1: 32, 2: 128, 3: 64, 4: 32}[layout]
     return index + 8 + (32 if rank4 else 8) + (1 if per_query_c else 0)
 
 
@@ -187,7 +193,7 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
     query, and so does the paper layout's pair-cooperative load mode 4 (the two
     lanes' halves of a line in one instruction); load modes 1 and 3 read one
     sector below the block middle and two above it, modes 0 and 2 two."""
-    if layout in (1, 2) or load_mode == 4:
+    if layout in (1, 2, 3, 4) or load_mode == 4:
         return 1.0
     if load_mode in (0, 2):
         return 2.0
@@ -353,14 +359,16 @@ def run_ours(args):
         launches = 1
         bpq = bytes_per_query(2, layout, tuning["load_mode"])
         achieved = bpq * m / (avg_ms * 1e-3) / 1e9
-        kname = {0: "birank_rank_paper", 1: "birank_rank_sector", 2: "birank_rank_line128"}[layout]
+        kname = {0: "birank_rank_paper", 1: "birank_rank_sector", 2: "birank_rank_line128", 3: "birank_rank_in32",
+                 4: "birank_rank_in32x2"}[layout]
         tr = traffic_record(kname)
         gq_launch = m / (avg_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": round(tr["bytes_per_query"] * m) if tr else None,
                     "peak_kind": f"of {peak_kind} (copy bandwidth)",
                     "kernel": {0: "rank_kernel<K,LOAD,kBiScalar>", 1: "rank_sector_kernel<K,kBiScalar>",
-                               2: "rank_line_kernel<K,kBiScalar>"}[layout],
+                               2: "rank_line_kernel<K,kBiScalar>", 3: "rank_in32_kernel<K,kBiScalar,false>",
+                               4: "rank_in32_kernel<K,kBiScalar,true>"}[layout],
                     "algorithmic_bytes_per_query": bpq, "queries_per_launch": m,
                     "random_requests_per_query": round(rpq, 3),
                     "random_request_ceiling_G_per_s": round(ceiling, 2) if ceiling == ceiling else None,
@@ -400,8 +408,7 @@ def run_ours(args):
         "config": {"workload": f"BiRank sigma=2 rank(q), n=2^{args.log_n} i.i.d. bits p=0.5, 2^{args.log_m} "
                                f"uniform uint64 queries per GPU",
                    "n_bits": n, "queries_per_gpu": m,
-                   "layout": {0: "BiRank16 (3.28% overhead)", 1: "BiRank16x2 sector layout (6.72% overhead)",
-                              2: "BiRank16 on 128-byte lines (1.69% overhead)"}[layout],
+                   "layout": LAYOUT_NAMES_BI[layout],
                    "index_bytes": index_bytes, "tuning": tuning,
                    "batch_path": "region batching (tiles of 8192 queries sorted by 256 text regions, answered "
                                  "region after region from L2, results put back in query order)"
@@ -473,14 +480,15 @@ def run_layouts(args, stream):
     import torch
     from paper_2602_04103_gb300 import capi, workloads
     m = 1 << args.log_m
-    names = {0: "paper (BiRank16 / QuadRank16)", 1: "sector (BiRank16x2 / 4-delta sectors)", 2: "128-byte lines"}
+    names = {0: "paper (BiRank16 / QuadRank16)", 1: "sector (BiRank16x2 / 4-delta sectors)", 2: "128-byte lines",
+             3: "32-bit inline (BiRank32 / QuadRank32)", 4: "32-bit inline x2 (BiRank32x2)"}
     res = {"birank": {}, "quadrank": {}}
     text, q = workloads.birank_inputs(args.log_n, args.log_m)
     dq, o = dev_u64(q), None
     o = torch.empty_like(dq)
     dt = dev_u64(text)
     del text
-    for layout in (0, 1, 2):
+    for layout in (0, 1, 2, 3, 4):
         idx = capi.qr_build(dt, 1 << args.log_n, 2, layout=layout)
         t = capi.qr_autotune(idx, dq[: 1 << 24], o, c=1)
         ms = best_ms(lambda: capi.qr_rank(idx, dq, 1, o), stream)
@@ -498,7 +506,7 @@ def run_layouts(args, stream):
     o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
     d4 = dev_u64(t4)
     del t4
-    for layout in (0, 1, 2):
+    for layout in (0, 1, 2, 3):
         idx = capi.qr_build(d4, 1 << args.log_n4, 4, layout=layout)
         t1 = capi.qr_autotune(idx, dq[: 1 << 24], o, c=dc[: 1 << 24])
         ms1 = best_ms(lambda: capi.qr_rank_c(idx, dq, dc, o), stream)
@@ -928,7 +936,7 @@ def main():
                     help="log2 of the queries per step of --impl reference")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--layout", type=int, choices=[0, 1, 2], default=None,
+    ap.add_argument("--layout", type=int, choices=[0, 1, 2, 3, 4], default=None,
                     help="fixed layout for the headline (skips the tuned build and the probe)")
     ap.add_argument("--tuning", type=int, nargs=3, default=[1, 512, 0], metavar=("K", "THREADS", "LOAD"))
     ap.add_argument("--serve-requests", type=int, default=8000)

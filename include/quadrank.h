@@ -58,6 +58,20 @@ extern "C" {
                             /* at 1/4 and 3/4 of a 480-bit block, 6.72%), each     */
                             /* delta at the head of its 32-byte half; sigma 4 =    */
                             /* four deltas + 96 transposed chars per sector (33%)  */
+#define QR_LAYOUT_INLINE32 3    /* 32-bit inline values (paper Sec. 3.1 BiRank32,   */
+                                /* Sec. 4.1 QuadRank32): sigma 2 = one 32-bit value */
+                                /* + 480 data bits per line (6.67%), the value to   */
+                                /* data offset 240; sigma 4 = four 32-bit values +  */
+                                /* 192 transposed chars (33.3%), values to char 96; */
+                                /* a query reads the whole 64-byte line              */
+#define QR_LAYOUT_INLINE32X2 4  /* sigma 2 only: the paper's BiRank32x2 (Sec. 3.1),  */
+                                /* two 32-bit values, each at the head of its        */
+                                /* 32-byte half with 224 data bits, pointing to the  */
+                                /* half's middle (14.3%); one sector per query       */
+/* The two inline-32 layouts have no superblock array of 32-bit offsets: their
+ * values are relative to an L0 table of one 64-bit rank per 2^22 lines (four
+ * for sigma 4), which shrinks it by a factor 2^15 against the 16-bit layouts
+ * (a few KB at n = 2^43), as the paper's variants intend. */
 
 typedef struct qr_index qr_index;
 
@@ -67,14 +81,17 @@ typedef struct {
     int32_t sigma;          /* 2 or 4                                                */
     int32_t layout;         /* QR_LAYOUT_*                                           */
     uint64_t block_chars;   /* chars per line: 496 / 224 (paper layout), 480 / 192   */
-                            /* (sector), 1008 / 480 (128-byte lines) for sigma 2 / 4 */
+                            /* (sector), 1008 / 480 (128-byte lines), 480 / 192      */
+                            /* (inline 32), 448 (inline 32 x2) for sigma 2 / 4       */
     uint64_t super_blocks;  /* lines per superblock: 128 / 256 (paper, sector),      */
-                            /* 32 / 64 (128-byte lines) for sigma 2 / 4              */
+                            /* 32 / 64 (128-byte lines) for sigma 2 / 4; 2^22 lines  */
+                            /* per L0 entry (inline layouts)                         */
     uint64_t line_bytes;    /* 64, or 128 for QR_LAYOUT_LINE128                      */
     uint64_t nblocks;       /* floor(n / B) + 1 lines                                */
     uint64_t nsuper;        /* ceil(nblocks / super_blocks) superblock entries        */
     uint64_t bytes_blocks;  /* line_bytes * nblocks                                  */
-    uint64_t bytes_super;   /* 4 * nsuper (sigma 2) or 16 * nsuper (sigma 4)          */
+    uint64_t bytes_super;   /* 4 * nsuper (sigma 2) or 16 * nsuper (sigma 4); inline */
+                            /* layouts 8 * nsuper or 32 * nsuper                     */
 } qr_info_t;
 
 /* Per-handle launch tuning of the rank kernels (chosen by the autotuner). */
@@ -88,7 +105,8 @@ typedef struct {
                                  /*    sectors, 32-byte loads; 4: whole line, the two    */
                                  /*    lanes of a pair load its two sectors in one       */
                                  /*    instruction (one request per line)                */
-                                 /* The sector layout ignores it (one 32-byte load).    */
+                                 /* The sector and inline layouts ignore it (one      */
+                                 /* 32-byte load; whole lines by lane pairs).          */
     int32_t grid_blocks;         /* 0: SM count x resident blocks per SM                */
 } qr_tuning_t;
 
@@ -124,7 +142,9 @@ int qr_build(const uint64_t* text, uint64_t n, int sigma, int text_on_device, vo
  * the block, so only a quarter of the line is popcounted); the sigma 4 form
  * applies the same idea to QuadRank (Sec. 4.1 variants: larger inline values
  * so that fewer characters are counted).  Every query reads one 32-byte
- * sector of its line. */
+ * sector of its line.  QR_LAYOUT_INLINE32 and QR_LAYOUT_INLINE32X2 are the
+ * paper's 32-bit inline variants (Sec. 3.1 BiRank32 and BiRank32x2, Sec. 4.1
+ * QuadRank32).  QR_LAYOUT_INLINE32X2 with sigma 4 gives QR_EINVAL. */
 int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device, int layout, void* stream,
                 qr_index** out);
 

@@ -603,6 +603,220 @@ __global__ void layout4l_kernel(const uint64_t* __restrict__ text, uint64_t n, u
     }
 }
 
+// ---------------------------------------------------------------- 32-bit inline layouts
+// Built in chunks of 128 lines, independent of the 2^22-line L0 blocks: the
+// counts of every chunk, an exclusive scan of them, then every chunk's lines,
+// their values relative to the rank at the start of their L0 block (that
+// rank is the scanned base of the block's first chunk, which also writes it
+// to the L0 table).
+constexpr uint64_t kChunkLines = 128;
+constexpr uint64_t kChunksPerL0 = kL0Lines / kChunkLines;
+
+// sigma 2, VAR 0 = BiRank32 (one value + 480 data bits), VAR 1 = BiRank32x2
+// (per 32-byte half: one value + 224 data bits): the line's words with their
+// value bits still 0, its count, and the counts before each value's position
+// (mid[h]; half0 = the count of half 0 for VAR 1).
+struct LineIn2 {
+    uint64_t w[8];
+    uint32_t cnt, half0, mid[2];
+};
+
+template <int VAR>
+__device__ __forceinline__ LineIn2 make_line_in2(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    LineIn2 L;
+    L.half0 = 0;
+    if (VAR == 0) {
+        const uint64_t base = j * kB2w;  // data bit d at line bit 32 + d
+        L.w[0] = bits64(t, n, base) << 32;
+#pragma unroll
+        for (int k = 1; k < 8; k++) L.w[k] = bits64(t, n, base + 64 * k - 32);
+        // data bits [0, 240) = line bits [32, 272)
+        L.mid[0] = popc64(L.w[0]) + popc64(L.w[1]) + popc64(L.w[2]) + popc64(L.w[3]) + popc64(L.w[4] & 0xFFFFull);
+        L.mid[1] = 0;
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) c += popc64(L.w[k]);
+        L.cnt = c;
+    } else {
+        uint32_t total = 0;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint64_t base = j * kB2x + h * kHalf2x;  // data bit d of the half at half bit 32 + d
+            L.w[4 * h] = bits64(t, n, base) << 32;
+#pragma unroll
+            for (int k = 1; k < 4; k++) L.w[4 * h + k] = bits64(t, n, base + 64 * k - 32);
+            // data bits [0, 112) of the half = half bits [32, 144)
+            L.mid[h] = popc64(L.w[4 * h]) + popc64(L.w[4 * h + 1]) + popc64(L.w[4 * h + 2] & 0xFFFFull);
+            const uint32_t hc = popc64(L.w[4 * h]) + popc64(L.w[4 * h + 1]) + popc64(L.w[4 * h + 2]) +
+                                popc64(L.w[4 * h + 3]);
+            if (h == 0) L.half0 = hc;
+            total += hc;
+        }
+        L.cnt = total;
+    }
+    return L;
+}
+
+template <int VAR>
+__global__ void count_in2_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
+                                 uint64_t* __restrict__ chunk_cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nchunks; i += nwarps) {
+        uint64_t sum = 0;
+        for (int r = 0; r < (int)(kChunkLines / 32); r++) {
+            const uint64_t j = i * kChunkLines + r * 32 + lane;
+            if (j < nblocks) sum += make_line_in2<VAR>(text, n, j).cnt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) chunk_cnt[i] = sum;
+    }
+}
+
+template <int VAR>
+__global__ void layout_in2_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
+                                  const uint64_t* __restrict__ chunk_base, uint4* __restrict__ lines,
+                                  uint64_t* __restrict__ l0tab) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nchunks; i += nwarps) {
+        const uint64_t base = chunk_base[i];
+        const uint64_t l0 = chunk_base[i & ~(kChunksPerL0 - 1)];  // rank at the start of the L0 block
+        if (lane == 0 && (i & (kChunksPerL0 - 1)) == 0) l0tab[i / kChunksPerL0] = base;
+        uint64_t running = base - l0;  // < 2^22 * 480
+        for (int r = 0; r < (int)(kChunkLines / 32); r++) {
+            const uint64_t j = i * kChunkLines + r * 32 + lane;
+            LineIn2 L;
+            const bool live = j < nblocks;
+            if (live) L = make_line_in2<VAR>(text, n, j);
+            const uint32_t v = live ? L.cnt : 0;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const uint64_t before = running + (incl - v);  // rank(line start) - rank(L0 start)
+            if (live) {
+                L.w[0] |= before + L.mid[0];                      // < 2^32
+                if (VAR == 1) L.w[4] |= before + L.half0 + L.mid[1];
+                uint4* dst = lines + 4 * j;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                        (uint32_t)(L.w[2 * k + 1] >> 32));
+            }
+            running += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+// sigma 4, QuadRank32: 192 chars as three transposed groups of 64 (words
+// 2 + 2g, 3 + 2g), the per-symbol counts of the line and of its first 96 chars.
+struct LineIn4 {
+    uint64_t w[8];
+    uint32_t cnt[4], mid[4];
+};
+
+__device__ __forceinline__ LineIn4 make_line_in4(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
+    LineIn4 R;
+    const uint64_t nbits = 2 * n;
+    const uint64_t c0 = j * kB4w;
+    uint32_t cnt[4] = {0, 0, 0, 0}, mid[4] = {0, 0, 0, 0};
+    R.w[0] = R.w[1] = 0;
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+        const uint64_t first = c0 + 64 * g;
+        const uint64_t x0 = bits64(t, nbits, 2 * first), x1 = bits64(t, nbits, 2 * first + 64);
+        const uint64_t L = (uint64_t)even_bits(x0) | ((uint64_t)even_bits(x1) << 32);
+        const uint64_t H = (uint64_t)even_bits(x0 >> 1) | ((uint64_t)even_bits(x1 >> 1) << 32);
+        count_group(L, H, ~0ull, cnt);
+        if (g == 0) count_group(L, H, ~0ull, mid);
+        if (g == 1) count_group(L, H, 0xFFFFFFFFull, mid);  // chars 64 .. 95
+        R.w[2 + 2 * g] = ~L;
+        R.w[3 + 2 * g] = ~H;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        R.cnt[c] = cnt[c];
+        R.mid[c] = mid[c];
+    }
+    return R;
+}
+
+__global__ void count_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
+                                 uint64_t* __restrict__ chunk_cnt /* [4][nchunks] */) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nchunks; i += nwarps) {
+        uint64_t sum[4] = {0, 0, 0, 0};
+        for (int r = 0; r < (int)(kChunkLines / 32); r++) {
+            const uint64_t j = i * kChunkLines + r * 32 + lane;
+            if (j < nblocks) {
+                const LineIn4 L = make_line_in4(text, n, j);
+#pragma unroll
+                for (int c = 0; c < 4; c++) sum[c] += L.cnt[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+            if (lane == 0) chunk_cnt[c * nchunks + i] = sum[c];
+        }
+    }
+}
+
+__global__ void layout_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
+                                  const uint64_t* __restrict__ chunk_base /* [4][nchunks] */,
+                                  uint4* __restrict__ lines, uint64_t* __restrict__ l0tab /* [nl0][4] */) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < nchunks; i += nwarps) {
+        uint64_t running[4];
+        const uint64_t first = i & ~(kChunksPerL0 - 1);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint64_t base = chunk_base[c * nchunks + i];
+            running[c] = base - chunk_base[c * nchunks + first];
+            if (lane == 0 && i == first) l0tab[4 * (i / kChunksPerL0) + c] = base;
+        }
+        for (int r = 0; r < (int)(kChunkLines / 32); r++) {
+            const uint64_t j = i * kChunkLines + r * 32 + lane;
+            const bool live = j < nblocks;
+            LineIn4 L;
+            if (live) L = make_line_in4(text, n, j);
+            uint64_t val[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const uint32_t v = live ? L.cnt[c] : 0;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                val[c] = running[c] + (incl - v) + (live ? L.mid[c] : 0);  // rank(192 j + 96, c) - L0
+                running[c] += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (live) {
+                L.w[0] = val[0] | (val[1] << 32);
+                L.w[1] = val[2] | (val[3] << 32);
+                uint4* dst = lines + 4 * j;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    dst[k] = make_uint4((uint32_t)L.w[2 * k], (uint32_t)(L.w[2 * k] >> 32), (uint32_t)L.w[2 * k + 1],
+                                        (uint32_t)(L.w[2 * k + 1] >> 32));
+            }
+        }
+    }
+}
+
 unsigned grid_for_warps(uint64_t nwarps) {
     uint64_t blocks = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const uint64_t cap = (uint64_t)device_props().sms * 64;
@@ -613,7 +827,48 @@ unsigned grid_for_warps(uint64_t nwarps) {
 
 }  // namespace
 
+// The two inline-32 layouts: chunk counts, scans, lines and the L0 table.
+int build_inline_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
+    const uint64_t nchunks = (idx->nblocks + kChunkLines - 1) / kChunkLines;
+    const int nsym = idx->sigma == 2 ? 1 : 4;
+    uint64_t* cnt = nullptr;
+    uint64_t* base = nullptr;
+    QR_CUDA_TRY(cudaMallocAsync((void**)&cnt, sizeof(uint64_t) * nchunks * nsym, s));
+    cudaError_t e = cudaMallocAsync((void**)&base, sizeof(uint64_t) * nchunks * nsym, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(cnt, s);
+        return cuda_fail(e, "cudaMallocAsync(scan)");
+    }
+    const unsigned grid = grid_for_warps(nchunks);
+    const unsigned threads = 32 * kWarpsPerBlock;
+    int rc = QR_OK;
+    uint64_t* l0 = (uint64_t*)idx->supers;
+    if (idx->sigma == 2) {
+        const bool x2 = idx->layout == QR_LAYOUT_INLINE32X2;
+        if (x2) count_in2_kernel<1><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
+        else count_in2_kernel<0><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
+        rc = exclusive_scan_u64(cnt, base, nchunks, s);
+        if (rc == QR_OK && x2)
+            layout_in2_kernel<1><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines, l0);
+        else if (rc == QR_OK)
+            layout_in2_kernel<0><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines, l0);
+    } else {
+        count_in4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
+        for (int c = 0; c < 4 && rc == QR_OK; c++)
+            rc = exclusive_scan_u64(cnt + c * nchunks, base + c * nchunks, nchunks, s);
+        if (rc == QR_OK)
+            layout_in4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines, l0);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(base, s);
+    if (rc != QR_OK) return rc;
+    if (le != cudaSuccess) return cuda_fail(le, "inline layout kernels");
+    return QR_OK;
+}
+
 int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
+    if (inline_layout(idx->layout)) return build_inline_index(idx, d_text, s);
     const uint64_t nsuper = idx->nsuper;
     const int nsym = idx->sigma == 2 ? 1 : 4;
     uint64_t* cnt = nullptr;

@@ -41,13 +41,20 @@ const DeviceProps& device_props() {
 uint64_t block_chars(int sigma, int layout) {
     if (layout == QR_LAYOUT_SECTOR) return sigma == 2 ? kB2s : kB4s;
     if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kB2L : kB4L;
+    if (layout == QR_LAYOUT_INLINE32) return sigma == 2 ? kB2w : kB4w;
+    if (layout == QR_LAYOUT_INLINE32X2) return kB2x;
     return sigma == 2 ? kB2 : kB4;
 }
 uint64_t super_lines(int sigma, int layout) {
     if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kSuper2L : kSuper4L;
+    if (inline_layout(layout)) return kL0Lines;
     return sigma == 2 ? kSuper2 : kSuper4;
 }
 uint64_t line_bytes(int layout) { return layout == QR_LAYOUT_LINE128 ? 128 : 64; }
+uint64_t super_entry_bytes(int sigma, int layout) {
+    if (inline_layout(layout)) return sigma == 2 ? 8 : 32;
+    return sigma == 2 ? 4 : 16;
+}
 
 static int tuning_ok(const qr_tuning_t& t) {
     const int k = t.queries_per_thread;
@@ -88,8 +95,11 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     if (!out) return fail(QR_EINVAL, "qr_build: out is NULL");
     *out = nullptr;
     if (sigma != 2 && sigma != 4) return fail(QR_EINVAL, "qr_build: sigma must be 2 or 4");
-    if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR && layout != QR_LAYOUT_LINE128)
+    if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR && layout != QR_LAYOUT_LINE128 &&
+        layout != QR_LAYOUT_INLINE32 && layout != QR_LAYOUT_INLINE32X2)
         return fail(QR_EINVAL, "qr_build: unknown layout");
+    if (layout == QR_LAYOUT_INLINE32X2 && sigma != 2)
+        return fail(QR_EINVAL, "qr_build: QR_LAYOUT_INLINE32X2 is sigma 2 only");
     if (sigma == 2 && n >= (1ull << 43)) return fail(QR_EINVAL, "qr_build: sigma 2 needs n < 2^43");
     if (sigma == 4 && n >= (1ull << 45)) return fail(QR_EINVAL, "qr_build: sigma 4 needs n < 2^45");
     if (!text && n > 0) return fail(QR_EINVAL, "qr_build: text is NULL");
@@ -107,7 +117,7 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     idx->nblocks = n / B + 1;
     idx->nsuper = (idx->nblocks + per - 1) / per;
     cudaError_t e = cudaMalloc((void**)&idx->lines, line_bytes(layout) * idx->nblocks);
-    if (e == cudaSuccess) e = cudaMalloc(&idx->supers, (sigma == 2 ? 4 : 16) * idx->nsuper);
+    if (e == cudaSuccess) e = cudaMalloc(&idx->supers, super_entry_bytes(sigma, layout) * idx->nsuper);
     if (e == cudaSuccess) e = cudaMalloc((void**)&idx->status, 64);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx->status, 0, 64, s);
     if (e != cudaSuccess) {
@@ -269,7 +279,7 @@ int qr_info(const qr_index* idx, qr_info_t* info) {
     info->nblocks = idx->nblocks;
     info->nsuper = idx->nsuper;
     info->bytes_blocks = info->line_bytes * idx->nblocks;
-    info->bytes_super = (idx->sigma == 2 ? 4 : 16) * idx->nsuper;
+    info->bytes_super = super_entry_bytes(idx->sigma, idx->layout) * idx->nsuper;
     return QR_OK;
 }
 
@@ -286,7 +296,7 @@ int qr_copy_layout(const qr_index* idx, void* lines_dst, void* supers_dst, void*
     if (lines_dst)
         QR_CUDA_TRY(cudaMemcpyAsync(lines_dst, idx->lines, line_bytes(idx->layout) * idx->nblocks, cudaMemcpyDefault, s));
     if (supers_dst)
-        QR_CUDA_TRY(cudaMemcpyAsync(supers_dst, idx->supers, (idx->sigma == 2 ? 4 : 16) * idx->nsuper,
+        QR_CUDA_TRY(cudaMemcpyAsync(supers_dst, idx->supers, super_entry_bytes(idx->sigma, idx->layout) * idx->nsuper,
                                     cudaMemcpyDefault, s));
     QR_CUDA_TRY(cudaStreamSynchronize(s));
     return QR_OK;
@@ -370,7 +380,7 @@ static constexpr uint64_t kTuneSample = 1ull << 24;  // queries timed per autotu
 static double layout_overhead(int sigma, int layout, uint64_t n) {
     const uint64_t B = block_chars(sigma, layout), per = super_lines(sigma, layout);
     const uint64_t nb = n / B + 1, ns = (nb + per - 1) / per;
-    const double bytes = (double)line_bytes(layout) * nb + (sigma == 2 ? 4.0 : 16.0) * ns;
+    const double bytes = (double)line_bytes(layout) * nb + (double)super_entry_bytes(sigma, layout) * ns;
     const double text = sigma == 2 ? n / 8.0 : n / 4.0;
     return n ? bytes / text - 1.0 : 0.0;
 }
@@ -384,7 +394,9 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
     int best_layout = -1;
     float best_ms = 1e30f;
     cudaStream_t s = (cudaStream_t)stream;
-    for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128}) {
+    for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128, QR_LAYOUT_INLINE32,
+                       QR_LAYOUT_INLINE32X2}) {
+        if (layout == QR_LAYOUT_INLINE32X2 && sigma != 2) continue;
         if (sigma == 2 || sigma == 4) {
             if (layout_overhead(sigma, layout, n < 4096 ? 1u << 30 : n) > max_overhead) continue;
         }

@@ -68,6 +68,30 @@ constexpr uint64_t kB4L = 480;
 constexpr uint64_t kMid4L = 240;
 constexpr uint64_t kSuper4L = 64;
 
+// 32-bit inline layouts (QR_LAYOUT_INLINE32, QR_LAYOUT_INLINE32X2; paper
+// Sec. 3.1 BiRank32 and BiRank32x2, Sec. 4.1 QuadRank32).  A 32-bit value per
+// line (per half-line for BiRank32x2, per symbol for QuadRank32) holds the
+// rank at the line's middle minus the rank at the start of its L0 block of
+// 2^22 lines; the L0 table keeps one 64-bit rank per block (four for sigma
+// 4), a few KB even at n = 2^43.  The values stay below 2^22 * 480 < 2^31.
+//   BiRank32:   word 0 low 32 bits = value, data bit d (d < 480) at line bit
+//               32 + d, the value counts data bits before offset 240.
+//   BiRank32x2: each 32-byte half h: low 32 bits = value, data bit d (d < 224)
+//               of the half at half bit 32 + d, the value counts the data bits
+//               before offset 112 of the half.
+//   QuadRank32: word 0 = v0 | v1 << 32, word 1 = v2 | v3 << 32; words 2 + 2g
+//               / 3 + 2g = ~low / ~high bits of chars 64g .. 64g + 63 (g < 3);
+//               v_c counts symbol c among chars 0 .. 95 of the line.
+constexpr uint64_t kB2w = 480;
+constexpr uint64_t kMid2w = 240;
+constexpr uint64_t kB2x = 448;
+constexpr uint64_t kHalf2x = 224;
+constexpr uint64_t kMid2x = 112;
+constexpr uint64_t kB4w = 192;
+constexpr uint64_t kMid4w = 96;
+constexpr int kL0Shift = 22;
+constexpr uint64_t kL0Lines = 1ull << kL0Shift;
+
 // Status bits written by kernels (same values as the QR_E* status codes).
 constexpr uint32_t kStatusRange = QR_ERANGE;
 constexpr uint32_t kStatusBadSym = QR_EBADSYM;
@@ -99,6 +123,8 @@ __host__ __device__ __forceinline__ uint64_t div480(uint64_t q) { return mulhi64
 constexpr uint64_t kMagic63 = 0x8208208208208209ull;  // ceil(2^69 / 63)
 __host__ __device__ __forceinline__ uint64_t div1008(uint64_t q) { return mulhi64(q >> 4, kMagic63) >> 5; }
 __host__ __device__ __forceinline__ uint64_t div192(uint64_t q) { return mulhi64(q >> 6, kMagic3) >> 1; }
+// 448 = 64 * 7 (the magic of div224, error term 6).
+__host__ __device__ __forceinline__ uint64_t div448(uint64_t q) { return mulhi64(q >> 6, kMagic7) >> 2; }
 // floor(q / 224) for q < 2^32 with one 32-bit high multiply: x = q >> 5 and
 // M = ceil(2^32 / 7) = (2^32 + 3) / 7 give x M / 2^32 = x / 7 + 3x / (7 2^32),
 // which floors to floor(x / 7) while 3x < 2^32 (here x < 2^27).
@@ -377,6 +403,88 @@ __device__ __forceinline__ void quad_sector_finish4(const uint32_t s[4], const u
     }
 }
 
+// ---------------------------------------------------------------- 32-bit inline layout queries
+// A count over 32-bit words w[lo..hi) of the bits between bit position x and
+// the fixed middle M (both measured in the words' bit coordinates): the mask
+// of word i is low(x - 32 i) XOR low(M - 32 i).
+template <int N, int FIRST, int M>
+__device__ __forceinline__ uint32_t count_to_mid(const uint32_t (&w)[N], int32_t x) {
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = FIRST; i < N; i++) cnt += __popc(w[i] & (low32(x - 32 * i) ^ cmask32(M - 32 * i)));
+    return cnt;
+}
+// BiRank32: the line's two sectors S0, S1, data offset d (< 480); l0 = the
+// rank at the start of the line's L0 block.
+__device__ __forceinline__ uint64_t in32_bi_finish(uint64_t l0, const u64x4& S0, const u64x4& S1, uint32_t d) {
+    const uint32_t w[16] = {lo32(S0.a), hi32(S0.a), lo32(S0.b), hi32(S0.b), lo32(S0.c), hi32(S0.c),
+                            lo32(S0.d), hi32(S0.d), lo32(S1.a), hi32(S1.a), lo32(S1.b), hi32(S1.b),
+                            lo32(S1.c), hi32(S1.c), lo32(S1.d), hi32(S1.d)};
+    const uint32_t cnt = count_to_mid<16, 1, 32 + (int)kMid2w>(w, 32 + (int32_t)d);
+    const uint64_t mid = l0 + lo32(S0.a);
+    return d >= kMid2w ? mid + cnt : mid - cnt;
+}
+// BiRank32x2: the query's 32-byte half W, data offset r inside the half (< 224).
+__device__ __forceinline__ uint64_t in32x2_finish(uint64_t l0, const u64x4& W, uint32_t r) {
+    const uint32_t w[8] = {lo32(W.a), hi32(W.a), lo32(W.b), hi32(W.b), lo32(W.c), hi32(W.c), lo32(W.d), hi32(W.d)};
+    const uint32_t cnt = count_to_mid<8, 1, 32 + (int)kMid2x>(w, 32 + (int32_t)r);
+    const uint64_t mid = l0 + lo32(W.a);
+    return r >= kMid2x ? mid + cnt : mid - cnt;
+}
+// QuadRank32: chars 32 i .. 32 i + 31 (i < 6) are the low (i even) or high
+// (i odd) 32 bits of words 2 + 2 (i / 2) (~low bits) and 3 + 2 (i / 2)
+// (~high bits); the mask of each is the chars between d and 96.
+struct Quad32Words {
+    uint32_t nl[6], nh[6], m[6];
+};
+__device__ __forceinline__ Quad32Words quad32_words(const u64x4& S0, const u64x4& S1, uint32_t d) {
+    const uint64_t L[3] = {S0.c, S1.a, S1.c}, H[3] = {S0.d, S1.b, S1.d};
+    Quad32Words q;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        q.nl[i] = (i & 1) ? hi32(L[i >> 1]) : lo32(L[i >> 1]);
+        q.nh[i] = (i & 1) ? hi32(H[i >> 1]) : lo32(H[i >> 1]);
+        q.m[i] = low32((int32_t)d - 32 * i) ^ cmask32((int)kMid4w - 32 * i);
+    }
+    return q;
+}
+__device__ __forceinline__ uint32_t quad32_value(const u64x4& S0, int c) {
+    const uint64_t w = (c & 2) ? S0.b : S0.a;
+    return (c & 1) ? hi32(w) : lo32(w);
+}
+__device__ __forceinline__ uint64_t quad32_finish1(uint64_t l0_c, const u64x4& S0, const u64x4& S1, uint32_t d,
+                                                   int c) {
+    const Quad32Words q = quad32_words(S0, S1, d);
+    const uint32_t cl = 0u - (uint32_t)(c & 1), ch = 0u - (uint32_t)(c >> 1);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) cnt += __popc((q.nl[i] ^ cl) & (q.nh[i] ^ ch) & q.m[i]);
+    const uint64_t mid = l0_c + quad32_value(S0, c);
+    return d >= kMid4w ? mid + cnt : mid - cnt;
+}
+// All four counts: n3 = |L & H|, n1 = |L| - n3, n2 = |H| - n3,
+// n0 = |mask| - n1 - n2 - n3 over the masked chars (L, H = raw bits).
+__device__ __forceinline__ void quad32_finish4(const uint64_t l0[4], const u64x4& S0, const u64x4& S1, uint32_t d,
+                                               uint64_t r[4]) {
+    const Quad32Words q = quad32_words(S0, S1, d);
+    uint32_t nl = 0, nh = 0, n3 = 0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const uint32_t L = ~q.nl[i] & q.m[i], H = ~q.nh[i] & q.m[i];
+        nl += __popc(L);
+        nh += __popc(H);
+        n3 += __popc(L & H);
+    }
+    const bool upper = d >= kMid4w;
+    const uint32_t nm = upper ? d - (uint32_t)kMid4w : (uint32_t)kMid4w - d;
+    const uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const uint64_t mid = l0[c] + quad32_value(S0, c);
+        r[c] = upper ? mid + n[c] : mid - n[c];
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct DeviceProps {
     int device = -1;
@@ -415,6 +523,8 @@ namespace qr {
 uint64_t block_chars(int sigma, int layout);
 uint64_t super_lines(int sigma, int layout);
 uint64_t line_bytes(int layout);
+uint64_t super_entry_bytes(int sigma, int layout);
+inline bool inline_layout(int layout) { return layout == QR_LAYOUT_INLINE32 || layout == QR_LAYOUT_INLINE32X2; }
 // Build the layout into an already sized index from a device text.
 int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
 // Launch the rank kernels (no argument checks beyond the mode); rank4 = 0:

@@ -396,8 +396,10 @@ KernelFn pick_sector(int k) {
     }
 }
 
-KernelFn pick_kind(int kind, int k, int load, bool sector, bool line128 = false) {
-    if (line128) return pick_line_kind(kind, k);
+KernelFn pick_kind(int kind, int k, int load, int layout) {
+    if (layout == QR_LAYOUT_LINE128) return pick_line_kind(kind, k);
+    if (inline_layout(layout)) return pick_in32_kind(kind, k, layout == QR_LAYOUT_INLINE32X2);
+    const bool sector = layout == QR_LAYOUT_SECTOR;
     if (sector) {
         switch (kind) {
             case kBiScalar: return pick_sector<kBiScalar>(k);
@@ -556,8 +558,7 @@ int launch_direct(const qr_index* idx, const uint64_t* q, const uint8_t* cvec, i
     // more (measured on sorted 2^28-query batches: K = 2 191 Gq/s, K = 4 156,
     // K = 8 83), so the tuning found on the uniform batch is not reused
     if (gate && t.queries_per_thread > 2) t.queries_per_thread = 2;
-    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout == QR_LAYOUT_SECTOR,
-                            idx->layout == QR_LAYOUT_LINE128);
+    KernelFn fn = pick_kind(kind, t.queries_per_thread, t.load_mode, idx->layout);
     if (!fn) return fail(QR_EINVAL, "no rank kernel for this tuning");
     RankArgs a{idx->lines, idx->supers, idx->n, q, cvec, c, m, out, idx->status, gate, gate_limit};
     const uint64_t tiles = (m + (uint64_t)t.block_threads * t.queries_per_thread - 1) /
@@ -574,8 +575,9 @@ int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint
     if (nchains == 0) return QR_OK;
     RankArgs a{idx->lines, idx->supers, idx->n, q0, nullptr, c, nchains, out, idx->status, nullptr, 0};
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR;
-    ChainFn fn = idx->layout == QR_LAYOUT_LINE128
-                     ? pick_chain_line(quad)
+    ChainFn fn = idx->layout == QR_LAYOUT_LINE128 ? pick_chain_line(quad)
+                 : inline_layout(idx->layout)
+                     ? pick_chain_in32(quad, idx->layout == QR_LAYOUT_INLINE32X2)
                      : quad ? (sector ? rank_chain_kernel<true, true> : rank_chain_kernel<true, false>)
                             : (sector ? rank_chain_kernel<false, true> : rank_chain_kernel<false, false>);
     uint64_t grid = (nchains + 255) / 256;

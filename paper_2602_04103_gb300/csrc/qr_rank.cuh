@@ -1,6 +1,6 @@
-// Declarations shared by the batched rank kernels of the three layouts
+// Declarations shared by the batched rank kernels of the layouts
 // (qr_rank.cu: paper and sector layouts, chains, probe; qr_rank_line.cu:
-// 128-byte line layout).
+// 128-byte line layout; qr_rank_in32.cu: the 32-bit inline layouts).
 #pragma once
 
 #include "qr_common.cuh"
@@ -46,5 +46,10 @@ __device__ __forceinline__ uint64_t chain_next(uint64_t q, uint64_t r, uint64_t 
 // a.out = 2 values per chain (see qr_rank_chain).  Launched with whole warps.
 using ChainFn = void (*)(RankArgs, uint64_t);
 ChainFn pick_chain_line(bool quad);
+
+// Kernels of the 32-bit inline layouts (qr_rank_in32.cu): x2 = BiRank32x2
+// (QR_LAYOUT_INLINE32X2), else BiRank32 / QuadRank32 (QR_LAYOUT_INLINE32).
+KernelFn pick_in32_kind(int kind, int k, bool x2);
+ChainFn pick_chain_in32(bool quad, bool x2);
 
 }  // namespace qr

@@ -740,12 +740,15 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
 // is the upper half.  Sector layout: the one self-contained half.
 // PREFIX (sigma 4): prefix_rank(q, c), the sum of the four counts up to c,
 // from all four superblock offsets.
-template <bool SECTOR, bool QUAD, bool PREFIX = false>
+// LAY: the index layout (QR_LAYOUT_PAPER, _SECTOR, _INLINE32, _INLINE32X2).
+template <int LAY, bool QUAD, bool PREFIX = false>
 struct RegionLoad {
-    u64x4 X;
+    u64x4 X, X2;     // the sector(s) the query needs (X2: the second sector of an INLINE32 line)
     uint64_t w0, w1;
     uint32_t s;
     uint4 s4;
+    uint64_t l0;     // inline layouts: the L0 entry (of the query's symbol)
+    uint4 l4a, l4b;  // QuadRank32 with all four symbols: the four L0 entries
     uint32_t pos;
 };
 
@@ -765,14 +768,54 @@ __device__ __forceinline__ uint32_t ix_ld_u32(const uint32_t* p, uint64_t pol) {
     return EL ? ld_u32_hint(p, pol) : __ldg(p);
 }
 
-// N32 (sector layouts, n < 2^37): the line index from a 32-bit high multiply,
-// x = q >> 5 (or q >> 6) < 2^32 and the usual magic numbers for 15 and 3,
-// ceil(2^35 / 15) and ceil(2^33 / 3), exact for every 32-bit x.
-template <bool SECTOR, bool QUAD, bool PREFIX = false, bool EL = false, bool N32 = false>
-__device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L, const uint4* __restrict__ lines,
+// N32 (sector and inline layouts, n < 2^37): the line index from a 32-bit
+// high multiply, x = q >> 5 (or q >> 6) < 2^32 and the usual magic numbers for
+// 15, 3 and 7: ceil(2^35 / 15), ceil(2^33 / 3), ceil(2^34 / 7), exact for every
+// 32-bit x.
+template <int LAY, bool QUAD, bool PREFIX = false, bool EL = false, bool N32 = false>
+__device__ __forceinline__ void region_issue(RegionLoad<LAY, QUAD, PREFIX>& L, const uint4* __restrict__ lines,
                                              const void* __restrict__ supers, uint64_t q, uint32_t c,
                                              uint64_t pol = 0) {
-    if (SECTOR) {
+    if (LAY == QR_LAYOUT_INLINE32X2) {  // sigma 2 only
+        uint64_t j;
+        uint32_t p;
+        if (N32) {
+            const uint32_t j32 = __umulhi((uint32_t)(q >> 6), 0x92492493u) >> 2;
+            j = j32;
+            p = (uint32_t)q - j32 * (uint32_t)kB2x;
+        } else {
+            j = div448(q);
+            p = (uint32_t)(q - j * kB2x);
+        }
+        const uint32_t h = p >= kHalf2x;
+        L.pos = p - h * (uint32_t)kHalf2x;
+        L.l0 = __ldg((const uint64_t*)supers + (j >> kL0Shift));
+        L.X = ix_ld32<EL>(lines + 4 * j + 2 * h, pol);
+        L.w0 = L.w1 = 0;
+    } else if (LAY == QR_LAYOUT_INLINE32) {
+        uint64_t j;
+        if (N32) {
+            const uint32_t j32 = QUAD ? __umulhi((uint32_t)(q >> 6), 0xAAAAAAABu) >> 1
+                                      : __umulhi((uint32_t)(q >> 5), 0x88888889u) >> 3;
+            j = j32;
+            L.pos = (uint32_t)q - j32 * (uint32_t)(QUAD ? kB4w : kB2w);
+        } else {
+            j = QUAD ? div192(q) : div480(q);
+            L.pos = (uint32_t)(q - j * (QUAD ? kB4w : kB2w));
+        }
+        const uint64_t* l0 = (const uint64_t*)supers;
+        if (!QUAD) {
+            L.l0 = __ldg(l0 + (j >> kL0Shift));
+        } else if (PREFIX) {
+            L.l4a = __ldg((const uint4*)(l0 + 4 * (j >> kL0Shift)));
+            L.l4b = __ldg((const uint4*)(l0 + 4 * (j >> kL0Shift)) + 1);
+        } else {
+            L.l0 = __ldg(l0 + 4 * (j >> kL0Shift) + c);
+        }
+        L.X = ix_ld32<EL>(lines + 4 * j, pol);
+        L.X2 = ix_ld32<EL>(lines + 4 * j + 2, pol);
+        L.w0 = L.w1 = 0;
+    } else if (LAY == QR_LAYOUT_SECTOR) {
         uint64_t j;
         uint32_t h;
         if (!QUAD) {
@@ -831,24 +874,47 @@ __device__ __forceinline__ void region_issue(RegionLoad<SECTOR, QUAD, PREFIX>& L
     }
 }
 
-template <bool SECTOR, bool QUAD, bool PREFIX = false>
-__device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD, PREFIX>& L, uint64_t q, uint32_t c) {
-    if (PREFIX) {
-        const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
+// rank_4: the four counts of a query from the loads of the prefix form (all
+// four superblock offsets).
+template <int LAY>
+__device__ __forceinline__ void region_finish4(const RegionLoad<LAY, true, true>& L, uint64_t r[4]) {
+    if (LAY == QR_LAYOUT_INLINE32) {
+        const uint64_t b[4] = {lo64(L.l4a), hi64(L.l4a), lo64(L.l4b), hi64(L.l4b)};
+        quad32_finish4(b, L.X, L.X2, L.pos, r);
+        return;
+    }
+    const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
+    if (LAY == QR_LAYOUT_SECTOR) {
+        quad_sector_finish4(s4, L.X, L.pos, r);
+    } else {
+        const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
+        const bool upper = L.pos >= 128;
+        quad_finish4(s4, upper ? L.w0 : L.X.a, upper ? L.w1 : L.X.b, x, L.pos, r);
+    }
+}
+
+template <int LAY, bool QUAD, bool PREFIX = false>
+__device__ __forceinline__ uint64_t region_finish(const RegionLoad<LAY, QUAD, PREFIX>& L, uint64_t q, uint32_t c) {
+    if constexpr (PREFIX) {
         uint64_t r[4];
-        if (SECTOR) {
-            quad_sector_finish4(s4, L.X, L.pos, r);
-        } else {
-            const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
-            const bool upper = L.pos >= 128;
-            quad_finish4(s4, upper ? L.w0 : L.X.a, upper ? L.w1 : L.X.b, x, L.pos, r);
-        }
+        region_finish4<LAY>(L, r);
         uint64_t sum = 0;
 #pragma unroll
         for (uint32_t k = 0; k < 4; k++) sum += k <= c ? r[k] : 0;
         return sum;
     }
-    if (SECTOR) {
+    if (LAY == QR_LAYOUT_INLINE32X2) {
+        const uint64_t r1 = in32x2_finish(L.l0, L.X, L.pos);
+        return c == 1 ? r1 : q - r1;
+    }
+    if (LAY == QR_LAYOUT_INLINE32) {
+        if (!QUAD) {
+            const uint64_t r1 = in32_bi_finish(L.l0, L.X, L.X2, L.pos);
+            return c == 1 ? r1 : q - r1;
+        }
+        return quad32_finish1(L.l0, L.X, L.X2, L.pos, (int)c);
+    }
+    if (LAY == QR_LAYOUT_SECTOR) {
         if (!QUAD) {
             const uint64_t r1 = birank_sector_finish(L.s, L.X, L.pos);
             return c == 1 ? r1 : q - r1;
@@ -864,20 +930,6 @@ __device__ __forceinline__ uint64_t region_finish(const RegionLoad<SECTOR, QUAD,
     const bool upper = L.pos >= 128;
     const uint64_t w0 = upper ? L.w0 : L.X.a, w1 = upper ? L.w1 : L.X.b;
     return quad_finish1(L.s, quad_delta(w0, w1, (int)c), x, L.pos, (int)c);
-}
-
-// rank_4: the four counts of a query from the loads of the prefix form (all
-// four superblock offsets).
-template <bool SECTOR>
-__device__ __forceinline__ void region_finish4(const RegionLoad<SECTOR, true, true>& L, uint64_t r[4]) {
-    const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
-    if (SECTOR) {
-        quad_sector_finish4(s4, L.X, L.pos, r);
-    } else {
-        const uint64_t x[4] = {L.X.a, L.X.b, L.X.c, L.X.d};
-        const bool upper = L.pos >= 128;
-        quad_finish4(s4, upper ? L.w0 : L.X.a, upper ? L.w1 : L.X.b, x, L.pos, r);
-    }
 }
 
 // Modes of the rank pass: rank(q, c) (scalar or per-query symbol), rank_4,
@@ -938,7 +990,7 @@ struct RankPassArgs {
     Gate gate;
 };
 
-template <bool SECTOR, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, int MODE = kModeRank,
+template <int LAY, bool QUAD, bool VEC, int K, int MINB, int P, int SEGS, bool QUEUE, int MODE = kModeRank,
           bool EL = false, bool N32 = false>
 __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a) {
     constexpr bool kS4 = MODE != kModeRank;  // loads of all four superblock offsets
@@ -1005,7 +1057,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                 if (j0 + P * kRound < total)
                     fetch_items<K, SEGS>(S[PS - 1], keys, j0 + P * kRound, total, start, sbase, sreg, lane);
             }
-            RegionLoad<SECTOR, QUAD, kS4> L[K];
+            RegionLoad<LAY, QUAD, kS4> L[K];
             uint64_t qk[K];
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -1013,7 +1065,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                 // bad keys (and idle lanes) read line 0
                 qk[k] = bad ? 0 : ((uint64_t)cur.reg[k] << a.shift) | (cur.key[k] & qmask);
                 const uint32_t c = VEC ? cur.key[k] >> kKeySymShift : a.c0;
-                region_issue<SECTOR, QUAD, kS4, EL, N32>(L[k], a.lines, a.supers, qk[k], c, pol);
+                region_issue<LAY, QUAD, kS4, EL, N32>(L[k], a.lines, a.supers, qk[k], c, pol);
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -1021,14 +1073,14 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
                     if constexpr (kR4) {
                         if (cur.key[k] & kKeyBad) continue;
                         uint64_t r[4];
-                        region_finish4<SECTOR>(L[k], r);
+                        region_finish4<LAY>(L[k], r);
                         st_stream_v4u32(a.res16 + 4 * (uint64_t)cur.at[k], (uint32_t)r[0], (uint32_t)r[1],
                                         (uint32_t)r[2], (uint32_t)r[3]);
                     }
                 } else {
                     if (cur.key[k] & kKeyBad) continue;
                     const uint32_t c = VEC ? cur.key[k] >> kKeySymShift : a.c0;
-                    const uint64_t r = region_finish<SECTOR, QUAD, kS4>(L[k], qk[k], c);
+                    const uint64_t r = region_finish<LAY, QUAD, kS4>(L[k], qk[k], c);
                     st_stream_u32(keys + cur.at[k], (uint32_t)r);
                 }
             }
@@ -1044,7 +1096,7 @@ __global__ void __launch_bounds__(kRankThreads, MINB) region_rank(RankPassArgs a
 // the first position of region r (r << shift) for symbol c (prefix_rank: up
 // to c), by the same query arithmetic as the rank pass; 0 for regions that
 // start beyond n (no query falls there) and for c >= sigma.
-template <bool SECTOR, bool QUAD, bool PREFIX, bool N32>
+template <int LAY, bool QUAD, bool PREFIX, bool N32>
 __global__ void __launch_bounds__(256) region_base(const uint4* __restrict__ lines, const void* __restrict__ supers,
                                                   uint64_t n, int shift, uint64_t* __restrict__ bases, Gate gate) {
     if (!regions_chosen(gate)) return;
@@ -1054,9 +1106,9 @@ __global__ void __launch_bounds__(256) region_base(const uint4* __restrict__ lin
     const uint64_t q = (uint64_t)r << shift;
     uint64_t v = 0;
     if (q <= n && (QUAD || c < 2)) {
-        RegionLoad<SECTOR, QUAD, PREFIX> L;
-        region_issue<SECTOR, QUAD, PREFIX, false, N32>(L, lines, supers, q, c, 0);
-        v = region_finish<SECTOR, QUAD, PREFIX>(L, q, c);
+        RegionLoad<LAY, QUAD, PREFIX> L;
+        region_issue<LAY, QUAD, PREFIX, false, N32>(L, lines, supers, q, c, 0);
+        v = region_finish<LAY, QUAD, PREFIX>(L, q, c);
     }
     bases[id] = v;
 }
@@ -1106,55 +1158,76 @@ using BaseFn = void (*)(const uint4*, const void*, uint64_t, int, uint64_t*, Gat
 // queue, evict-last index loads).  Measured on GB300 with 8-byte work items
 // (2^28 uniform queries, sector layout): 0 1.78 ms, 1 2.11 ms, 2 1.78 ms,
 // 3 1.91 ms.
-template <bool SECTOR, bool QUAD, bool VEC, bool N32 = false>
+template <int LAY, bool QUAD, bool VEC, bool N32 = false>
 RankFn pick_variant(int v) {
     switch (v) {
-        case 0: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, false, N32>;
-        case 1: return region_rank<SECTOR, QUAD, VEC, 1, 6, 2, 16, true, kModeRank, false, N32>;
-        case 2: return region_rank<SECTOR, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, true, N32>;
-        case 3: return region_rank<SECTOR, QUAD, VEC, 4, 3, 1, 16, true, kModeRank, false, N32>;
+        case 0: return region_rank<LAY, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, false, N32>;
+        case 1: return region_rank<LAY, QUAD, VEC, 1, 6, 2, 16, true, kModeRank, false, N32>;
+        case 2: return region_rank<LAY, QUAD, VEC, 2, 4, 1, 16, true, kModeRank, true, N32>;
+        case 3: return region_rank<LAY, QUAD, VEC, 4, 3, 1, 16, true, kModeRank, false, N32>;
         default: return nullptr;
     }
 }
 
-// mode: kModeRank / kModeRank4 / kModePrefix (the last two sigma 4, one
-// symbol or none, default variant); n32: sector layout with n < 2^37 (the
-// 32-bit line-index division)
-RankFn pick_region_rank(bool sector, bool quad, bool vec, int v, int mode, bool n32) {
-    if (mode == kModeRank4) {
-        if (sector)
-            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, kModeRank4, false, true>
-                       : region_rank<true, true, false, 2, 4, 1, 16, true, kModeRank4>;
-        return region_rank<false, true, false, 2, 4, 1, 16, true, kModeRank4>;
+// The rank pass of one layout: mode kModeRank4 / kModePrefix are sigma 4,
+// one symbol or none, default variant; n32: n < 2^37 on a layout with a
+// 32-bit line-index division (sector and inline layouts).
+template <int LAY>
+RankFn pick_rank_lay(bool quad, bool vec, int v, int mode, bool n32) {
+    constexpr bool kN32 = LAY != QR_LAYOUT_PAPER;
+    if (mode == kModeRank4 || mode == kModePrefix) {
+        if constexpr (LAY == QR_LAYOUT_INLINE32X2) {
+            return nullptr;  // sigma 2 only
+        } else {
+            if (mode == kModeRank4)
+                return n32 && kN32 ? region_rank<LAY, true, false, 2, 4, 1, 16, true, kModeRank4, false, kN32>
+                                   : region_rank<LAY, true, false, 2, 4, 1, 16, true, kModeRank4>;
+            return n32 && kN32 ? region_rank<LAY, true, false, 2, 4, 1, 16, true, kModePrefix, false, kN32>
+                               : region_rank<LAY, true, false, 2, 4, 1, 16, true, kModePrefix>;
+        }
     }
-    if (mode == kModePrefix) {
-        if (sector)
-            return n32 ? region_rank<true, true, false, 2, 4, 1, 16, true, kModePrefix, false, true>
-                       : region_rank<true, true, false, 2, 4, 1, 16, true, kModePrefix>;
-        return region_rank<false, true, false, 2, 4, 1, 16, true, kModePrefix>;
+    if (quad) {
+        if constexpr (LAY == QR_LAYOUT_INLINE32X2) {
+            return nullptr;
+        } else {
+            if (n32 && kN32) return vec ? pick_variant<LAY, true, true, kN32>(v) : pick_variant<LAY, true, false, kN32>(v);
+            return vec ? pick_variant<LAY, true, true>(v) : pick_variant<LAY, true, false>(v);
+        }
     }
-    if (sector && n32) {
-        if (quad) return vec ? pick_variant<true, true, true, true>(v) : pick_variant<true, true, false, true>(v);
-        return vec ? pick_variant<true, false, true, true>(v) : pick_variant<true, false, false, true>(v);
-    }
-    if (sector) {
-        if (quad) return vec ? pick_variant<true, true, true>(v) : pick_variant<true, true, false>(v);
-        return vec ? pick_variant<true, false, true>(v) : pick_variant<true, false, false>(v);
-    }
-    if (quad) return vec ? pick_variant<false, true, true>(v) : pick_variant<false, true, false>(v);
-    return vec ? pick_variant<false, false, true>(v) : pick_variant<false, false, false>(v);
+    if (n32 && kN32) return vec ? pick_variant<LAY, false, true, kN32>(v) : pick_variant<LAY, false, false, kN32>(v);
+    return vec ? pick_variant<LAY, false, true>(v) : pick_variant<LAY, false, false>(v);
 }
 
-BaseFn pick_region_base(bool sector, bool quad, bool prefix, bool n32) {
-    if (prefix) {
-        if (sector) return n32 ? region_base<true, true, true, true> : region_base<true, true, true, false>;
-        return region_base<false, true, true, false>;
+RankFn pick_region_rank(int layout, bool quad, bool vec, int v, int mode, bool n32) {
+    switch (layout) {
+        case QR_LAYOUT_PAPER: return pick_rank_lay<QR_LAYOUT_PAPER>(quad, vec, v, mode, false);
+        case QR_LAYOUT_SECTOR: return pick_rank_lay<QR_LAYOUT_SECTOR>(quad, vec, v, mode, n32);
+        case QR_LAYOUT_INLINE32: return pick_rank_lay<QR_LAYOUT_INLINE32>(quad, vec, v, mode, n32);
+        case QR_LAYOUT_INLINE32X2: return pick_rank_lay<QR_LAYOUT_INLINE32X2>(quad, vec, v, mode, n32);
+        default: return nullptr;
     }
-    if (sector) {
-        if (quad) return n32 ? region_base<true, true, false, true> : region_base<true, true, false, false>;
-        return n32 ? region_base<true, false, false, true> : region_base<true, false, false, false>;
+}
+
+template <int LAY>
+BaseFn pick_base_lay(bool quad, bool prefix, bool n32) {
+    constexpr bool kN32 = LAY != QR_LAYOUT_PAPER;
+    if constexpr (LAY == QR_LAYOUT_INLINE32X2) {
+        if (quad || prefix) return nullptr;
+    } else {
+        if (prefix) return n32 && kN32 ? region_base<LAY, true, true, kN32> : region_base<LAY, true, true, false>;
+        if (quad) return n32 && kN32 ? region_base<LAY, true, false, kN32> : region_base<LAY, true, false, false>;
     }
-    return quad ? region_base<false, true, false, false> : region_base<false, false, false, false>;
+    return n32 && kN32 ? region_base<LAY, false, false, kN32> : region_base<LAY, false, false, false>;
+}
+
+BaseFn pick_region_base(int layout, bool quad, bool prefix, bool n32) {
+    switch (layout) {
+        case QR_LAYOUT_PAPER: return pick_base_lay<QR_LAYOUT_PAPER>(quad, prefix, false);
+        case QR_LAYOUT_SECTOR: return pick_base_lay<QR_LAYOUT_SECTOR>(quad, prefix, n32);
+        case QR_LAYOUT_INLINE32: return pick_base_lay<QR_LAYOUT_INLINE32>(quad, prefix, n32);
+        case QR_LAYOUT_INLINE32X2: return pick_base_lay<QR_LAYOUT_INLINE32X2>(quad, prefix, n32);
+        default: return nullptr;
+    }
 }
 
 int region_shift(uint64_t n) {
@@ -1235,8 +1308,8 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         if (!once_rc[dev]) once_rc[dev] = set_smem(region_unsort4, kUnsort4Smem);
     });
     rc = once_rc[dev];
-    const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR, vec = cvec != nullptr;
-    const bool n32 = sector && idx->n < (1ull << 37);
+    const bool quad = idx->sigma == 4, vec = cvec != nullptr;
+    const bool n32 = idx->layout != QR_LAYOUT_PAPER && idx->n < (1ull << 37);
     const int sms = device_props().sms;
     Gate gate{nullptr, 0, counters + 2};
     if (!rc) {
@@ -1254,10 +1327,14 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc) {
         // the bases the unsort pass restores the results from
-        BaseFn bf = pick_region_base(sector, quad, mode == kModePrefix, n32);
-        bf<<<kRegions * kBaseSyms / 256, 256, 0, s>>>(idx->lines, idx->supers, idx->n, shift, bases, gate);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) rc = cuda_fail(e, "region_base");
+        BaseFn bf = pick_region_base(idx->layout, quad, mode == kModePrefix, n32);
+        if (!bf) {
+            rc = fail(QR_EINVAL, "region batch: no base kernel for this layout and call");
+        } else {
+            bf<<<kRegions * kBaseSyms / 256, 256, 0, s>>>(idx->lines, idx->supers, idx->n, shift, bases, gate);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_fail(e, "region_base");
+        }
     }
     if (!rc && marks) cudaEventRecord(marks[0], s);
     if (!rc) {
@@ -1283,7 +1360,11 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     }
     if (!rc && marks) cudaEventRecord(marks[1], s);
     if (!rc) {
-        RankFn fn = pick_region_rank(sector, quad, vec, idx->region_variant, mode, n32);
+        RankFn fn = pick_region_rank(idx->layout, quad, vec, idx->region_variant, mode, n32);
+        if (!fn) {
+            cudaFreeAsync(buf, s);
+            return fail(QR_EINVAL, "region batch: no rank pass for this layout and call");
+        }
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;

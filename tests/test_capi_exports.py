@@ -94,6 +94,18 @@ def test_division_constants_sector_and_32bit():
             assert ((q >> 6) * m3 >> 32) >> 1 == q // 192
         if q < (1 << 32):
             assert (q >> 5) * m7 >> 32 == q // 224
+    # 448 = 64 * 7 (the 32-bit inline layout BiRank32x2): the 64-bit form with the magic of
+    # div224, and the 32-bit form for q < 2^37 with M = ceil(2^34 / 7), exact for x < 2^32
+    # while x (7 M - 2^34) < 2^34
+    m7_34, M7 = 0x92492493, 0x924924924924924A
+    assert m7_34 == -(-(1 << 34) // 7) and (7 * m7_34 - (1 << 34)) * ((1 << 32) - 1) < (1 << 34) * 7
+    for q in qs + [(1 << 37) - 1, (1 << 37) - 448, 447, 448, 449]:
+        assert ((q >> 6) * M7 >> 64) >> 2 == q // 448
+        if q < (1 << 37):
+            assert ((q >> 6) * m7_34 >> 32) >> 2 == q // 448
+    for r in range(7):
+        x = (1 << 31) - 1 - r
+        assert (x * m7_34 >> 32) >> 2 == x // 7
     for d, M in ((15, m15), (3, m3)):   # the largest dividend below 2^32 of each residue
         for r in range(d):
             x = (1 << 32) - 1 - r
@@ -101,7 +113,7 @@ def test_division_constants_sector_and_32bit():
     src = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_common.cuh").read_text()
     assert all(h in src for h in ("0x8888888888888889", "0xAAAAAAAAAAAAAAAB", "0x8208208208208209", "0x24924925"))
     reg = (ROOT / "paper_2602_04103_gb300" / "csrc" / "qr_region.cu").read_text()
-    assert "0x88888889u" in reg and "0xAAAAAAABu" in reg
+    assert "0x88888889u" in reg and "0xAAAAAAABu" in reg and "0x92492493u" in reg
 
 
 def test_handle_classes():

@@ -21,7 +21,11 @@ pytestmark = pytest.mark.gpu
 B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
 B2S, S2S, B4S, S4S = 480, 480 * 128, 192, 192 * 256
 B2L, S2L, B4L, S4L = 1008, 1008 * 32, 480, 480 * 64
-LAYOUTS = [0, 1, 2]   # QR_LAYOUT_PAPER (BiRank16 / QuadRank16), QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128
+B2W, B2X, B4W, L0 = 480, 448, 192, 1 << 22   # inline-32 layouts: data per line, lines per L0 entry
+# QR_LAYOUT_PAPER (BiRank16 / QuadRank16), _SECTOR, _LINE128, _INLINE32 (BiRank32 /
+# QuadRank32), _INLINE32X2 (BiRank32x2, sigma 2 only)
+BI_LAYOUTS = [0, 1, 2, 3, 4]
+DNA_LAYOUTS = [0, 1, 2, 3]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,21 +59,21 @@ def check_dna(words, n, q=None, layout=0):
     return idx
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", BI_LAYOUTS)
 def test_tiny_exhaustive_bits(layout):
     for L in range(0, 11):
         for bits in itertools.product([0, 1], repeat=L):
             check_bits(synth.pack_bits(np.array(bits, dtype=np.uint8)), L, layout=layout)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", DNA_LAYOUTS)
 def test_tiny_exhaustive_dna(layout):
     for L in range(0, 6):
         for codes in itertools.product(range(4), repeat=L):
             check_dna(synth.pack2(np.array(codes, dtype=np.uint8)), L, layout=layout)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", BI_LAYOUTS)
 @pytest.mark.parametrize("p", [0.5, 0.01, 0.99])
 def test_multi_superblock_bits_every_q(p, layout):
     n = 3 * S2 + 1234
@@ -77,7 +81,7 @@ def test_multi_superblock_bits_every_q(p, layout):
     check_bits(words, n, layout=layout)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", DNA_LAYOUTS)
 @pytest.mark.parametrize("kind", ["uniform", "gc_runs"])
 def test_multi_superblock_dna_every_q(kind, layout):
     n = 3 * S4 + 777
@@ -85,12 +89,13 @@ def test_multi_superblock_dna_every_q(kind, layout):
     check_dna(words, n, layout=layout)
 
 
-@pytest.mark.parametrize("n", [0, 1, 63, 64, 119, 120, 121, 239, 240, 241, 255, 256, 359, 360, 361, 479, 480,
-                               481, 495, 496, 497, 503, 504, 505, 991, 992, 993, 1007, 1008, 1009, 2016,
+@pytest.mark.parametrize("n", [0, 1, 63, 64, 111, 112, 113, 119, 120, 121, 223, 224, 225, 239, 240, 241, 255, 256,
+                               335, 336, 337, 359, 360, 361, 447, 448, 449, 479, 480, 481, 495, 496, 497, 503,
+                               504, 505, 895, 896, 897, 991, 992, 993, 1007, 1008, 1009, 2016,
                                S2L - 1, S2L, S2L + 1, S2S - 1, S2S, S2S + 1, S2 - 1, S2, S2 + 1,
                                2 * S2, 2 * S2 + 240])
 def test_edge_lengths_bits(n):
-    for layout in LAYOUTS:
+    for layout in BI_LAYOUTS:
         check_bits(synth.bits(n + 3, n, 0.5), n, layout=layout)
 
 
@@ -98,7 +103,7 @@ def test_edge_lengths_bits(n):
                                223, 224, 225, 239, 240, 241, 447, 448, 449, 479, 480, 481, S4L - 1, S4L, S4L + 1,
                                S4S - 1, S4S, S4S + 1, S4 - 1, S4, S4 + 1, 2 * S4 + 96])
 def test_edge_lengths_dna(n):
-    for layout in LAYOUTS:
+    for layout in DNA_LAYOUTS:
         check_dna(synth.dna_uniform(n + 5, n), n, layout=layout)
 
 
@@ -245,7 +250,7 @@ def test_out_of_range_and_bad_symbols():
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
-@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1), (0, 2)])
+@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1), (0, 2), (0, 3), (0, 4)])
 @pytest.mark.parametrize("threads", [64, 256, 512])
 def test_every_tuning(k, load, layout, threads):
     from paper_2602_04103_gb300 import capi
@@ -256,17 +261,19 @@ def test_every_tuning(k, load, layout, threads):
     q = synth.queries(19, n, 100_003)
     q4 = synth.queries(20, n4, 100_003)
     cv = synth.symbols(21, q4.size, 4)
-    idx, idx4 = build(words, n, 2, layout), build(w4, n4, 4, layout)
-    for i in (idx, idx4):
-        capi.qr_set_tuning(i, k, threads, load, 0)
+    idx = build(words, n, 2, layout)
+    capi.qr_set_tuning(idx, k, threads, load, 0)
     assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
-    assert np.array_equal(rank(idx4, q4, cv), oracle.rank_c(w4, n4, 4, q4, cv)[0])
-    assert np.array_equal(rank4(idx4, q4), oracle.rank4(w4, n4, q4)[0])
+    if layout in DNA_LAYOUTS:
+        idx4 = build(w4, n4, 4, layout)
+        capi.qr_set_tuning(idx4, k, threads, load, 0)
+        assert np.array_equal(rank(idx4, q4, cv), oracle.rank_c(w4, n4, 4, q4, cv)[0])
+        assert np.array_equal(rank4(idx4, q4), oracle.rank4(w4, n4, q4)[0])
     capi.qr_set_tuning(idx, k, threads, load, 7)    # explicit small grid: grid-stride loop
     assert np.array_equal(rank(idx, q, 0), oracle.rank(words, n, 2, q, 0)[0])
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", DNA_LAYOUTS)
 def test_host_pipeline_matches_device(layout):
     import torch
     from paper_2602_04103_gb300 import capi
@@ -496,7 +503,7 @@ def test_line128_max_deltas_and_overheads():
         capi.qr_set_tuning(idx, 4, 256, 0, 0)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", DNA_LAYOUTS)
 def test_prefix_rank(layout):
     import torch
     from paper_2602_04103_gb300 import capi
@@ -517,11 +524,13 @@ def test_prefix_rank(layout):
         capi.qr_prefix_rank(build(synth.bits(1, 100, 0.5), 100, 2), dq, 0, out)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", BI_LAYOUTS)
 @pytest.mark.parametrize("sigma", [2, 4])
 def test_rank_chain(layout, sigma):
     import torch
     from paper_2602_04103_gb300 import capi
+    if sigma == 4 and layout not in DNA_LAYOUTS:
+        pytest.skip("BiRank32x2 is sigma 2 only")
     n = 4 * S2 + 99 if sigma == 2 else 4 * S4 + 99
     words = synth.bits(91, n, 0.5) if sigma == 2 else synth.dna_uniform(92, n)
     idx = build(words, n, sigma, layout)
@@ -587,7 +596,7 @@ def test_small_configuration_every_output():
     want0 = q - want1
     dq = dev_u64(q)
     out = torch.empty_like(dq)
-    for layout in LAYOUTS:
+    for layout in BI_LAYOUTS:
         idx = build(words, n, 2, layout)
         for c, want in ((1, want1), (0, want0)):
             capi.qr_rank(idx, dq, c, out)
@@ -598,3 +607,175 @@ def test_small_configuration_every_output():
     capi.qr_rank(idx, dq, 1, out)
     assert np.array_equal(host_u64(out), want1), layout
     idx.free()
+
+
+# ---------------------------------------------------------------- 32-bit inline layouts
+def read_inline(idx):
+    """(info, lines as uint64 words [nb, 8], L0 table as uint64)."""
+    from paper_2602_04103_gb300 import capi
+    info = capi.qr_info(idx)
+    lines = np.empty(info["bytes_blocks"] // 8, dtype=np.uint64)
+    l0 = np.empty(info["bytes_super"] // 8, dtype=np.uint64)
+    capi.qr_copy_layout(idx, lines, l0)
+    return info, lines.reshape(-1, 8), l0
+
+
+@pytest.mark.parametrize("layout", [3, 4])
+def test_inline_layout_matches_definitions_bits(layout):
+    """BiRank32 (Sec. 3.1): one 32-bit value per line = rank(480 j + 240) minus
+    the rank at the start of the line's L0 block (2^22 lines), data bit d at
+    line bit 32 + d.  BiRank32x2: per 32-byte half h, the value = rank(448 j +
+    224 h + 112) minus the same L0 rank, data bit d of the half at half bit
+    32 + d.  The L0 table holds rank(L0 block start)."""
+    n = 9 * S2 + 4321
+    words = synth.bits(199, n, 0.37)
+    idx = build(words, n, 2, layout)
+    info, lines, l0 = read_inline(idx)
+    per = B2W if layout == 3 else B2X
+    nb = n // per + 1
+    assert info["nblocks"] == nb and info["super_blocks"] == L0 and info["nsuper"] == 1
+    assert l0.tolist() == [0]                       # one L0 block: rank 0 at its start
+    js = np.arange(nb, dtype=np.uint64)
+    tb = np.unpackbits(words.view(np.uint8), bitorder="little")
+    lb = np.unpackbits(lines.view(np.uint8), bitorder="little").reshape(nb, 512)
+    if layout == 3:
+        mids = np.minimum(js * np.uint64(B2W) + np.uint64(240), np.uint64(n))
+        r_mid, _ = oracle.rank(words, n, 2, mids, 1)   # padding bits are 0
+        assert np.array_equal(lines[:, 0] & np.uint64(0xFFFFFFFF), r_mid)
+        for j in [0, 1, 2, nb - 1]:
+            lo, hi = j * B2W, min(j * B2W + B2W, n)
+            assert np.array_equal(lb[j, 32:32 + hi - lo], tb[lo:hi])
+            assert lb[j, 32 + hi - lo:].sum() == 0
+    else:
+        for h in (0, 1):
+            mids = np.minimum(js * np.uint64(B2X) + np.uint64(224 * h + 112), np.uint64(n))
+            r_mid, _ = oracle.rank(words, n, 2, mids, 1)
+            assert np.array_equal(lines[:, 4 * h] & np.uint64(0xFFFFFFFF), r_mid), h
+        for j in [0, 1, 2, nb - 1]:
+            for h in (0, 1):
+                lo, hi = j * B2X + 224 * h, min(j * B2X + 224 * h + 224, n)
+                if hi <= lo:
+                    assert lb[j, 256 * h + 32:256 * h + 256].sum() == 0
+                    continue
+                assert np.array_equal(lb[j, 256 * h + 32:256 * h + 32 + hi - lo], tb[lo:hi])
+                assert lb[j, 256 * h + 32 + hi - lo:256 * h + 256].sum() == 0
+
+
+def test_inline_layout_matches_definitions_dna():
+    """QuadRank32 (Sec. 4.1): four 32-bit values per line, v_c = rank(192 j + 96,
+    c) minus the L0 rank of c (word 0 = v0 | v1 << 32, word 1 = v2 | v3 << 32);
+    words 2 + 2g / 3 + 2g = ~low / ~high bits of chars 64 g .. 64 g + 63."""
+    n = 7 * S4 + 999
+    words = synth.dna_uniform(223, n)
+    idx = build(words, n, 4, 3)
+    info, lines, l0 = read_inline(idx)
+    nb = n // B4W + 1
+    assert info["nblocks"] == nb and l0.tolist() == [0, 0, 0, 0]
+    js = np.arange(nb, dtype=np.uint64)
+    mids = np.minimum(js * np.uint64(B4W) + np.uint64(96), np.uint64(n))
+    r4, _ = oracle.rank4(words, n, mids)
+    r4[:, 0] += (js * np.uint64(B4W) + np.uint64(96)) - mids     # padding chars are A (code 0)
+    w0, w1 = lines[:, 0], lines[:, 1]
+    got = np.stack([w0 & np.uint64(0xFFFFFFFF), w0 >> np.uint64(32), w1 & np.uint64(0xFFFFFFFF),
+                    w1 >> np.uint64(32)], axis=1)
+    assert np.array_equal(got, r4)
+    codes = synth.unpack2(words, n)
+    for j in [0, 1, 2, nb - 1]:
+        for d in range(B4W):
+            g, b = d // 64, d % 64
+            lo = (~int(lines[j, 2 + 2 * g]) >> b) & 1
+            hi = (~int(lines[j, 3 + 2 * g]) >> b) & 1
+            c = j * B4W + d
+            assert lo | (hi << 1) == (int(codes[c]) if c < n else 0), (j, d)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("layout,sigma", [(3, 2), (4, 2), (3, 4)])
+def test_inline_l0_blocks(layout, sigma):
+    """Texts spanning several L0 blocks (2^22 lines each: 2^33 bits for
+    BiRank32 / BiRank32x2, 2^31 chars for QuadRank32): the L0 table against
+    the oracle's rank at every block start, and every query within 600
+    positions of each block boundary plus 2^20 uniform ones against the
+    oracle (rank, rank_4, both symbols), direct and region-batched."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 1 << 33 if sigma == 2 else 1 << 31
+    words = synth.bits(synth.base_seed(301), n, 0.5) if sigma == 2 else synth.dna_uniform(synth.base_seed(302), n)
+    per = {(3, 2): B2W, (4, 2): B2X, (3, 4): B4W}[(layout, sigma)]
+    idx = build(words, n, sigma, layout)
+    info, _, l0 = read_inline(idx)
+    nl0 = (n // per + 1 + L0 - 1) // L0
+    assert info["nsuper"] == nl0 >= 3
+    starts = np.minimum(np.arange(nl0, dtype=np.uint64) * np.uint64(L0 * per), np.uint64(n))
+    if sigma == 2:
+        want_l0, _ = oracle.rank(words, n, 2, starts, 1)
+        assert np.array_equal(l0, want_l0)
+    else:
+        want_l0, _ = oracle.rank4(words, n, starts)
+        assert np.array_equal(l0.reshape(-1, 4), want_l0)
+    edges = np.concatenate([np.arange(int(b) - 600, int(b) + 600) for b in starts[1:]])
+    q = np.concatenate([edges, synth.queries(synth.base_seed(303), n, 1 << 20), [0, n]]).astype(np.uint64)
+    dq = dev_u64(q)
+    for mode in (capi.QR_BATCH_DIRECT, capi.QR_BATCH_REGIONS):
+        capi.qr_set_batch_mode(idx, mode)
+        if sigma == 2:
+            out = torch.empty_like(dq)
+            for c in (0, 1):
+                capi.qr_rank(idx, dq, c, out)
+                want, rc = oracle.rank(words, n, 2, q, c)
+                assert rc == 0 and np.array_equal(host_u64(out), want), (mode, c)
+        else:
+            out4 = torch.empty((q.size, 4), dtype=torch.int64, device="cuda")
+            capi.qr_rank4(idx, dq, out4)
+            want4, rc = oracle.rank4(words, n, q)
+            assert rc == 0 and np.array_equal(host_u64(out4).reshape(-1, 4), want4), mode
+            cv = synth.symbols(synth.base_seed(304), q.size, 4)
+            out = torch.empty_like(dq)
+            capi.qr_rank_c(idx, dq, dev_u8(cv), out)
+            assert np.array_equal(host_u64(out), want4[np.arange(q.size), cv]), mode
+    assert capi.qr_status(idx) == 0
+    idx.free()
+
+
+@pytest.mark.slow
+def test_inline_values_near_their_bound():
+    """An all-ones text over a whole L0 block: the last lines' values reach
+    2^22 * 448 - 112 (BiRank32x2), the largest a 32-bit value holds here."""
+    n = L0 * B2X + 5000
+    words = np.full((n + 63) // 64 + 1, np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    words[n // 64] = np.uint64((1 << (n % 64)) - 1)            # no bits at or beyond n
+    words[n // 64 + 1:] = 0
+    idx = build(words, n, 2, 4)
+    info, lines, l0 = read_inline(idx)
+    assert l0.tolist() == [0, L0 * B2X]
+    assert int(lines[L0 - 1, 4] & np.uint64(0xFFFFFFFF)) == L0 * B2X - 112
+    q = np.concatenate([np.arange(L0 * B2X - 1000, L0 * B2X + 1000), [n]]).astype(np.uint64)
+    got = rank(idx, q, 1)
+    assert np.array_equal(got, q)                              # rank of all ones is q
+    assert np.array_equal(rank(idx, q, 0), np.zeros(q.size, dtype=np.uint64))
+    idx.free()
+
+
+def test_inline_sizes_and_overheads():
+    """Overheads from the closed forms: BiRank32 6.67%, BiRank32x2 14.3%
+    (Sec. 3.1), QuadRank32 33.3% (Sec. 4.1), with an L0 table of one 8-byte
+    (sigma 2) or 32-byte (sigma 4) entry per 2^22 lines."""
+    from paper_2602_04103_gb300 import capi
+    for layout, per in ((3, B2W), (4, B2X)):
+        n = 3 * S2 + 5
+        idx = build(synth.bits(1, n, 0.5), n, 2, layout)
+        info = capi.qr_info(idx)
+        nb = n // per + 1
+        assert info["bytes_blocks"] == 64 * nb and info["bytes_super"] == 8
+        n2 = 1 << 34
+        nb = n2 // per + 1
+        over = (64 * nb + 8 * ((nb + L0 - 1) // L0)) * 8 / n2 - 1
+        assert abs(over * 100 - {3: 6.67, 4: 14.29}[layout]) < 0.01
+    idx4 = build(synth.dna_uniform(2, 1000), 1000, 4, 3)
+    assert capi.qr_info(idx4)["bytes_super"] == 32
+    n4 = 1 << 32
+    nb4 = n4 // B4W + 1
+    over4 = (64 * nb4 + 32 * ((nb4 + L0 - 1) // L0)) * 8 / (2 * n4) - 1
+    assert abs(over4 * 100 - 33.33) < 0.01
+    with pytest.raises(capi.QRError):
+        build(synth.dna_uniform(2, 1000), 1000, 4, 4)              # BiRank32x2 is sigma 2 only

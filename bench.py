@@ -780,10 +780,14 @@ def fm_approx_row(dt, n, dp, doff, ref, stream):
 
 
 def run_serving(args):
-    """QuadFm serving over a 2^28-char index: closed-loop capacity of the
-    continuous-batching server, then Poisson arrivals at fractions of that
-    capacity, for the batching server and the plain per-request path (one
-    request per launch, one at a time)."""
+    """QuadFm serving over a 2^28-char index.  Arms: the continuous-batching
+    server (4 slots, requests packed into shared batches); the same server with
+    one request per batch on 4 slots (overlap without batching) and on 1 slot
+    (serialised), the latter also with a spinning completion poll instead of
+    the 20 us sleep; and a plain loop of qfm_count calls (copy in, count, copy
+    out, wait) timed with CUDA events.  Each arm: closed-loop capacity, then
+    Poisson arrivals at fractions of its own capacity (p50 / p99 latency at
+    loads it sustains); the batching server also at 0.5..1.2x of its capacity."""
     import torch
     from paper_2602_04103_gb300 import capi, workloads
     text, pats, off, first = workloads.serving_inputs(args.serve_requests, args.serve_log_n)
@@ -791,43 +795,116 @@ def run_serving(args):
     npat = int(first[-1])
     # the request trace lives in page-locked host memory (as an input reader
     # would keep it), so batches of back-to-back requests copy straight from it
-    pats = torch.from_numpy(pats).pin_memory().numpy()
+    pats_t = torch.from_numpy(pats).pin_memory()
+    pats = pats_t.numpy()
     off = torch.from_numpy(off.view(np.int64)).pin_memory().numpy().view(np.uint64)
     fidx = capi.qfm_build(torch.from_numpy(text).cuda(), text.size)
     del text
     res = {"serving_index_chars": 1 << args.serve_log_n, "serving_requests": nreq, "serving_patterns": npat,
            "serving_mean_patterns_per_request": round(npat / nreq, 1)}
-    modes = {"batched": dict(slots=4), "per_request": dict(slots=1, max_requests_per_batch=1)}
+    modes = {"batched": dict(slots=4), "per_request_4_slots": dict(slots=4, max_requests_per_batch=1),
+             "per_request": dict(slots=1, max_requests_per_batch=1),
+             "per_request_spin_poll": dict(slots=1, max_requests_per_batch=1, poll_us=0)}
     if args.serve_stream_calls:
         modes["batched_stream_calls"] = dict(slots=4, use_graph=0)
     ref = None
+    rng = np.random.default_rng(55)
+
+    def summary(mk, lat_us, st=None, gpu_us=None):
+        d = {"patterns_per_s": round(npat / mk), "makespan_s": round(mk, 4),
+             "p50_ms": round(float(np.percentile(lat_us, 50)) / 1e3, 3),
+             "p99_ms": round(float(np.percentile(lat_us, 99)) / 1e3, 3)}
+        if st is not None:
+            d["mean_requests_per_batch"] = round(st["mean_requests_per_batch"], 2)
+        if gpu_us is not None:
+            d["gpu_p50_ms"] = round(float(np.percentile(gpu_us, 50)) / 1e3, 3)
+            d["gpu_p99_ms"] = round(float(np.percentile(gpu_us, 99)) / 1e3, 3)
+        return d
+
+    def check(out):
+        nonlocal ref
+        if ref is None:
+            ref = out.copy()
+        assert np.array_equal(out, ref), "serving results differ between runs"
 
     def replay(mode, arrival):
-        nonlocal ref
         sv = capi.QFMServer(fidx, **modes[mode])
         out = torch.zeros(npat, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
         lat = np.zeros(nreq)
         mk = sv.replay(pats, off, first, arrival, out, lat)
         st = sv.stats()
         sv.close()
-        if ref is None:
-            ref = out.copy()
-        assert np.array_equal(out, ref), "serving results differ between runs"
-        return {"patterns_per_s": round(npat / mk), "makespan_s": round(mk, 4),
-                "p50_ms": round(float(np.percentile(lat, 50)) / 1e3, 3),
-                "p99_ms": round(float(np.percentile(lat, 99)) / 1e3, 3),
-                "mean_requests_per_batch": round(st["mean_requests_per_batch"], 2)}
+        check(out)
+        return summary(mk, lat, st)
 
-    cap = {m: replay(m, np.zeros(nreq)) for m in modes}
-    res["serving_closed_loop"] = cap
+    # the plain path a caller writes without the server: for each request
+    # in arrival order, copy its patterns and offsets in, count, copy the
+    # counts out, wait; per-request GPU time from CUDA events
+    d_pat = torch.empty(int(off[-1]) + 16, dtype=torch.uint8, device="cuda")
+    d_off = torch.empty(nreq and int((first[1:] - first[:-1]).max()) + 1, dtype=torch.int64, device="cuda")
+    d_out = torch.empty_like(d_off)
+    h_off = torch.empty_like(d_off, device="cpu").pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def plain_loop(arrival):
+        out = torch.zeros(npat, dtype=torch.int64).pin_memory()
+        lat = np.zeros(nreq)
+        gpu = np.zeros(nreq)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tp = pats_t
+        t_start = time.perf_counter()
+        for r in range(nreq):
+            while time.perf_counter() - t_start < arrival[r]:
+                pass
+            a, b = int(first[r]), int(first[r + 1])
+            pa, pb = int(off[a]), int(off[b])
+            h_off[: b - a + 1].copy_(torch.from_numpy((off[a:b + 1] - off[a]).view(np.int64)))
+            e0.record(stream)
+            d_pat[: pb - pa].copy_(tp[pa:pb], non_blocking=True)
+            d_off[: b - a + 1].copy_(h_off[: b - a + 1], non_blocking=True)
+            capi.qfm_count(fidx, d_pat, d_off[: b - a + 1], d_out[: b - a])
+            out[a:b].copy_(d_out[: b - a], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            lat[r] = (time.perf_counter() - t_start - arrival[r]) * 1e6
+            gpu[r] = e0.elapsed_time(e1) * 1e3
+        mk = time.perf_counter() - t_start
+        check(out.numpy().view(np.uint64))
+        return summary(mk, lat, gpu_us=gpu)
+
+    arms = dict(modes)
+    arms["plain_qfm_count_loop"] = None
+    run = {m: (lambda arr, m=m: plain_loop(arr) if arms[m] is None else replay(m, arr)) for m in arms}
+    mean_req = npat / nreq
+    # the batching server first: an untimed warm-up replay (after seconds of
+    # light GPU load the first replay ran with a p99 of up to ~4 ms), its
+    # closed-loop capacity, then Poisson arrivals at 0.5 .. 1.2x of it
+    replay("batched", np.zeros(nreq))
+    cap = {"batched": replay("batched", np.zeros(nreq))}
     capacity = cap["batched"]["patterns_per_s"]
-    rng = np.random.default_rng(55)
     for f in (0.5, 0.8, 1.0, 1.2):
-        lam = f * capacity / (npat / nreq)                  # requests per second
+        lam = f * capacity / mean_req                                # requests per second
         arrival = np.cumsum(rng.exponential(1.0 / lam, nreq))
-        res[f"serving_poisson_{f}x"] = {m: replay(m, arrival) for m in modes}
-        log(f"[bench] serving {f}x: " + ", ".join(f"{m} {v['patterns_per_s'] / 1e6:.1f} M/s p99 {v['p99_ms']} ms"
-                                                  for m, v in res[f"serving_poisson_{f}x"].items()))
+        res[f"serving_poisson_{f}x"] = {"batched": replay("batched", arrival)}
+        log(f"[bench] serving {f}x batched capacity: batched "
+            f"{res[f'serving_poisson_{f}x']['batched']['patterns_per_s'] / 1e6:.1f} M/s p99 "
+            f"{res[f'serving_poisson_{f}x']['batched']['p99_ms']} ms")
+    # the other arms: closed-loop capacity, then Poisson arrivals at
+    # fractions of each arm's own capacity (loads it sustains)
+    for m in arms:
+        if m != "batched":
+            cap[m] = run[m](np.zeros(nreq))
+    res["serving_closed_loop"] = cap
+    for f in (0.5, 0.8):
+        row = {}
+        for m in arms:
+            if m == "batched":
+                continue
+            lam = f * cap[m]["patterns_per_s"] / mean_req
+            row[m] = run[m](np.cumsum(rng.exponential(1.0 / lam, nreq)))
+        res[f"serving_poisson_{f}x_own_capacity"] = row
+        log(f"[bench] serving {f}x own capacity: " + ", ".join(
+            f"{m} {v['patterns_per_s'] / 1e6:.1f} M/s p99 {v['p99_ms']} ms" for m, v in row.items()))
     fidx.free()
     return res
 

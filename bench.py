@@ -294,6 +294,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    host = bind_to_gpu_node(local)
     stream = torch.cuda.current_stream()
     n, m = 1 << args.log_n, 1 << args.log_m
     t0 = time.time()
@@ -343,6 +344,17 @@ def run_ours(args):
     rpq = requests_per_query(2, layout, tuning["load_mode"])
     if plan == capi.QR_BATCH_REGIONS:
         roofline, launches = region_roofline(idx, step, m, index_bytes, avg_ms, peak, peak_kind, stream)
+        # the rank pass against the L2: its read requests per query (ncu, the
+        # committed capture) at the pass's rate, over the random 32-byte
+        # request rate of an L2-resident buffer (qr_probe_l2: 64-byte records
+        # are two 32-byte loads)
+        tr = traffic_record("birank_region_rank")
+        if tr and "l2_read_requests_per_query" in tr:
+            rec_s, _ = l2_probe(20 << 20, stream)
+            rq = tr["l2_read_requests_per_query"] * m / (roofline["passes_ms"]["rank"] * 1e-3)
+            roofline["rank_pass_l2_requests"] = {
+                "requests_per_query": tr["l2_read_requests_per_query"], "G_requests_per_s": round(rq / 1e9, 1),
+                "l2_probe_G_requests_per_s": round(2 * rec_s / 1e9, 1), "frac": round(rq / (2 * rec_s), 4)}
         # the direct kernels on the same index and queries, for comparison
         capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
         ms_d = best_ms(step, stream)
@@ -415,7 +427,7 @@ def run_ours(args):
                    if plan == capi.QR_BATCH_REGIONS else "direct kernels (one line load per query)",
                    "tuned_build_s": round(t_tune, 2),
                    "l2": "inputs larger than L2 (2 GiB queries, 2.3 GB index; L2 129 MB)",
-                   "parallelism": f"independent replica per GPU x{ws}"},
+                   "parallelism": f"independent replica per GPU x{ws}", "host": host},
         "roofline": roofline,
         "e2e": {"value": round(e2e_val, 3), "unit": "Gqueries/s", "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 8 * m,
@@ -732,6 +744,30 @@ def fm_roofline(lf_steps_per_s, index_bytes, stream):
             "index_bytes": index_bytes}
 
 
+def fm_policies(args, stream):
+    """The count kernel under each L2 policy (1, 2, 0; two launches each, the
+    second timed with CUDA events) on the count workload: the measurement
+    behind the default policy."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    text, pats, off = workloads.fm_inputs(args.fm_log_n, args.fm_m)
+    m = off.size - 1
+    fidx = capi.qfm_build(torch.from_numpy(text).cuda(), text.size)
+    dp = torch.from_numpy(pats).cuda()
+    doff = torch.from_numpy(off.view(np.int64)).cuda()
+    o = torch.empty(m, dtype=torch.int64, device="cuda")
+    res, ref = {}, None
+    for pol in (1, 2, 0):
+        capi.qfm_set_policy(fidx, pol)
+        capi.qfm_count(fidx, dp, doff, o)
+        _, per = time_launches(lambda: capi.qfm_count(fidx, dp, doff, o), 1, stream)
+        ref = o.clone() if ref is None else ref
+        assert torch.equal(o, ref)
+        res[f"policy_{pol}"] = {"ms": round(per[0], 3), "patterns_per_s": round(m / (per[0] * 1e-3))}
+    fidx.free()
+    return res
+
+
 def fm_locate_row(dt, n, dp, doff, m, ref, ms_p, stream):
     """Locate every occurrence of all patterns on the same text indexed with
     suffix-array sampling factor 32 (count with intervals, scan, LF walks)."""
@@ -909,6 +945,41 @@ def run_serving(args):
     return res
 
 
+def parse_cpulist(text: str) -> set:
+    """'0-3,8,10-11' -> {0, 1, 2, 3, 8, 10, 11}."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        else:
+            cpus.add(int(part))
+    return cpus
+
+
+def bind_to_gpu_node(gpu_index: int) -> dict:
+    """Run on the host cores local to the GPU (its PCI device's local_cpulist)
+    when some of them are allowed, so that pinned host buffers live on the
+    GPU's own memory node; reports what was found and done."""
+    info = {"gpu_numa_node": None, "bound_cores": None}
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dev = Path("/sys/bus/pci/devices") / ("0000:" + bus.split(":", 1)[1].lower())
+        info["gpu_numa_node"] = int((dev / "numa_node").read_text().strip())
+        local = parse_cpulist((dev / "local_cpulist").read_text())
+        allowed = os.sched_getaffinity(0)
+        both = local & allowed
+        if both and both != allowed:
+            os.sched_setaffinity(0, both)
+        info["bound_cores"] = len(both) if both else None
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    return info
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -1020,7 +1091,8 @@ def main():
     ap.add_argument("--serve-log-n", type=int, default=28)
     ap.add_argument("--serve-stream-calls", action="store_true",
                     help="also run the batching server without CUDA graphs")
-    ap.add_argument("--only", choices=["fm", "fm_locate", "fm_approx", "quadrank", "serving", "probe", "layouts"],
+    ap.add_argument("--only", choices=["fm", "fm_locate", "fm_approx", "fm_policies", "quadrank", "serving", "probe",
+                                       "layouts"],
                     default=None, help="run one extra row alone and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
@@ -1029,6 +1101,8 @@ def main():
         stream = torch.cuda.current_stream()
         if args.only in ("fm", "fm_locate", "fm_approx"):
             res = run_fm(args, stream, part=args.only[3:] or "all")
+        elif args.only == "fm_policies":
+            res = fm_policies(args, stream)
         elif args.only == "serving":
             res = run_serving(args)
         elif args.only == "layouts":

@@ -49,3 +49,29 @@ def test_bytes_and_requests_per_query():
     assert bench.requests_per_query(2, 0, 2) == 2.0
     assert bench.requests_per_query(2, 0, 4) == 1.0 and bench.requests_per_query(4, 0, 4) == 1.0
     assert abs(bench.requests_per_query(2, 0, 3) - (240 / 496 + 2 * 256 / 496)) < 1e-12
+
+
+def test_region_pass_bytes():
+    """Algorithmic bytes per query of the region passes: 8 (q) + 4 (key) + 2
+    (index) + two segment tables in the sort; 4 + 4 + one table + the index
+    once per batch in the rank pass; 4 + 2 + one table + 8 in the unsort
+    (rank_4: 16-byte results and 32-byte rows)."""
+    import bench
+    seg = 4 * 256 / 8192
+    m, idx = 1 << 28, 2_291_767_764
+    b = bench.region_pass_bytes(m, idx)
+    assert b == {"sort": 14 + 2 * seg, "rank": 8 + seg + idx / m, "unsort": 14 + seg}
+    assert abs(sum(b.values()) - 45.0375) < 1e-3                  # the BiRank headline step
+    b4 = bench.region_pass_bytes(m, idx, rank4=True)
+    assert b4["rank"] == 20 + seg + idx / m and b4["unsort"] == 50 + seg
+    assert bench.region_pass_bytes(m, idx, per_query_c=True)["sort"] == 15 + 2 * seg
+    # the QuadFm step: two rank queries of a QuadRank16 line, lower half one sector,
+    # upper half the 16 delta bytes and one sector
+    assert abs(2 * bench.QFM_RANK_L2_BYTES - 82.2857) < 1e-3
+
+
+def test_parse_cpulist():
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("72-143") == set(range(72, 144))
+    assert bench.parse_cpulist("") == set()

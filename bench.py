@@ -180,10 +180,10 @@ LAYOUT_NAMES_BI = {0: "BiRank16 (3.28% overhead)", 1: "BiRank16x2 sector layout 
 def bytes_per_query(sigma: int, layout: int, load_mode: int, rank4: bool = False, per_query_c: bool = False):
     """Algorithmic bytes of one query: the index bytes it must read (the
     32-byte half-line of the sector layout and of BiRank32x2, the 64-byte line
-    of the paper layout and of BiRank32 / QuadRank32, the 128-byte line of the
-    line layout) + the 8-byte query + the result (8, or 32 for rank_4) + 1 byte
-    of symbol when symbols are per query."""
-    index = {0: 64, 1: 32, 2: 128, 3: 64, 4: 32}[layout]
+    of the paper layout and of BiRank32 / QuadRank32 / QuadRank24_8, the
+    128-byte line of the line layout) + the 8-byte query + the result (8, or 32
+    for rank_4) + 1 byte of symbol when symbols are per query."""
+    index = {0: 64, 1: 32, 2: 128, 3: 64, 4: 32, 5: 64}[layout]
     return index + 8 + (32 if rank4 else 8) + (1 if per_query_c else 0)
 
 
@@ -193,7 +193,7 @@ def requests_per_query(sigma: int, layout: int, load_mode: int) -> float:
     query, and so does the paper layout's pair-cooperative load mode 4 (the two
     lanes' halves of a line in one instruction); load modes 1 and 3 read one
     sector below the block middle and two above it, modes 0 and 2 two."""
-    if layout in (1, 2, 3, 4) or load_mode == 4:
+    if layout in (1, 2, 3, 4, 5) or load_mode == 4:
         return 1.0
     if load_mode in (0, 2):
         return 2.0
@@ -493,7 +493,8 @@ def run_layouts(args, stream):
     from paper_2602_04103_gb300 import capi, workloads
     m = 1 << args.log_m
     names = {0: "paper (BiRank16 / QuadRank16)", 1: "sector (BiRank16x2 / 4-delta sectors)", 2: "128-byte lines",
-             3: "32-bit inline (BiRank32 / QuadRank32)", 4: "32-bit inline x2 (BiRank32x2)"}
+             3: "32-bit inline (BiRank32 / QuadRank32)", 4: "32-bit inline x2 (BiRank32x2)",
+             5: "QuadRank24_8"}
     res = {"birank": {}, "quadrank": {}}
     text, q = workloads.birank_inputs(args.log_n, args.log_m)
     dq, o = dev_u64(q), None
@@ -518,7 +519,7 @@ def run_layouts(args, stream):
     o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
     d4 = dev_u64(t4)
     del t4
-    for layout in (0, 1, 2, 3):
+    for layout in (0, 1, 2, 3, 5):
         idx = capi.qr_build(d4, 1 << args.log_n4, 4, layout=layout)
         t1 = capi.qr_autotune(idx, dq[: 1 << 24], o, c=dc[: 1 << 24])
         ms1 = best_ms(lambda: capi.qr_rank_c(idx, dq, dc, o), stream)

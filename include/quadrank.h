@@ -68,10 +68,16 @@ extern "C" {
                                 /* two 32-bit values, each at the head of its        */
                                 /* 32-byte half with 224 data bits, pointing to the  */
                                 /* half's middle (14.3%); one sector per query       */
-/* The two inline-32 layouts have no superblock array of 32-bit offsets: their
- * values are relative to an L0 table of one 64-bit rank per 2^22 lines (four
- * for sigma 4), which shrinks it by a factor 2^15 against the 16-bit layouts
- * (a few KB at n = 2^43), as the paper's variants intend. */
+#define QR_LAYOUT_INLINE24_8 5  /* sigma 4 only: the paper's QuadRank24_8 (Sec.    */
+                                /* 4.1), 192 transposed chars in 3 groups of 64,   */
+                                /* per symbol a 24-bit value to the end of group 0 */
+                                /* and an 8-bit step from there to the end of      */
+                                /* group 2: a query counts at most 64 chars (33.3%) */
+/* The inline layouts have no superblock array of 32-bit offsets: their
+ * values are relative to an L0 table of one 64-bit rank per 2^22 lines (2^16
+ * for QR_LAYOUT_INLINE24_8; four ranks for sigma 4), which shrinks it by a
+ * factor 2^15 (2^9) against the 16-bit layouts (a few KB at n = 2^43), as the
+ * paper's variants intend. */
 
 typedef struct qr_index qr_index;
 
@@ -144,7 +150,9 @@ int qr_build(const uint64_t* text, uint64_t n, int sigma, int text_on_device, vo
  * so that fewer characters are counted).  Every query reads one 32-byte
  * sector of its line.  QR_LAYOUT_INLINE32 and QR_LAYOUT_INLINE32X2 are the
  * paper's 32-bit inline variants (Sec. 3.1 BiRank32 and BiRank32x2, Sec. 4.1
- * QuadRank32).  QR_LAYOUT_INLINE32X2 with sigma 4 gives QR_EINVAL. */
+ * QuadRank32) and QuadRank24_8 (Sec. 4.1, QR_LAYOUT_INLINE24_8).
+ * QR_LAYOUT_INLINE32X2 with sigma 4 and QR_LAYOUT_INLINE24_8 with sigma 2
+ * give QR_EINVAL. */
 int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device, int layout, void* stream,
                 qr_index** out);
 

@@ -20,6 +20,7 @@ lib = C.CDLL(str(_SO))
 QR_OK, QR_EINVAL, QR_ENOMEM, QR_ECUDA = 0, 1, 2, 3
 QR_ERANGE, QR_EBADSYM, QR_ETIMEOUT = 4, 8, 16
 QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128 = 0, 1, 2
+QR_LAYOUT_INLINE32, QR_LAYOUT_INLINE32X2, QR_LAYOUT_INLINE24_8 = 3, 4, 5
 QFM_KEEP_SA = 1
 QFM_BOTH_STRANDS = 2
 

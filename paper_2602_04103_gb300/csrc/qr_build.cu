@@ -603,14 +603,15 @@ __global__ void layout4l_kernel(const uint64_t* __restrict__ text, uint64_t n, u
     }
 }
 
-// ---------------------------------------------------------------- 32-bit inline layouts
-// Built in chunks of 128 lines, independent of the 2^22-line L0 blocks: the
-// counts of every chunk, an exclusive scan of them, then every chunk's lines,
-// their values relative to the rank at the start of their L0 block (that
-// rank is the scanned base of the block's first chunk, which also writes it
-// to the L0 table).
+// ---------------------------------------------------------------- inline layouts
+// Built in chunks of 128 lines, independent of the L0 blocks (2^22 lines, 2^16
+// for QuadRank24_8): the counts of every chunk, an exclusive scan of them,
+// then every chunk's lines, their values relative to the rank at the start of
+// their L0 block (that rank is the scanned base of the block's first chunk,
+// which also writes it to the L0 table).
 constexpr uint64_t kChunkLines = 128;
 constexpr uint64_t kChunksPerL0 = kL0Lines / kChunkLines;
+constexpr uint64_t kChunksPerL0_24 = kL0Lines24 / kChunkLines;
 
 // sigma 2, VAR 0 = BiRank32 (one value + 480 data bits), VAR 1 = BiRank32x2
 // (per 32-byte half: one value + 224 data bits): the line's words with their
@@ -714,13 +715,15 @@ __global__ void layout_in2_kernel(const uint64_t* __restrict__ text, uint64_t n,
     }
 }
 
-// sigma 4, QuadRank32: 192 chars as three transposed groups of 64 (words
-// 2 + 2g, 3 + 2g), the per-symbol counts of the line and of its first 96 chars.
+// sigma 4: 192 chars as three transposed groups of 64 (words 2 + 2g, 3 + 2g),
+// the per-symbol counts of the line and of its first 96 chars (QuadRank32,
+// Q24 false) or its first 64 chars (QuadRank24_8, Q24 true).
 struct LineIn4 {
     uint64_t w[8];
     uint32_t cnt[4], mid[4];
 };
 
+template <bool Q24>
 __device__ __forceinline__ LineIn4 make_line_in4(const uint64_t* __restrict__ t, uint64_t n, uint64_t j) {
     LineIn4 R;
     const uint64_t nbits = 2 * n;
@@ -735,7 +738,7 @@ __device__ __forceinline__ LineIn4 make_line_in4(const uint64_t* __restrict__ t,
         const uint64_t H = (uint64_t)even_bits(x0 >> 1) | ((uint64_t)even_bits(x1 >> 1) << 32);
         count_group(L, H, ~0ull, cnt);
         if (g == 0) count_group(L, H, ~0ull, mid);
-        if (g == 1) count_group(L, H, 0xFFFFFFFFull, mid);  // chars 64 .. 95
+        if (g == 1 && !Q24) count_group(L, H, 0xFFFFFFFFull, mid);  // chars 64 .. 95
         R.w[2 + 2 * g] = ~L;
         R.w[3 + 2 * g] = ~H;
     }
@@ -747,6 +750,7 @@ __device__ __forceinline__ LineIn4 make_line_in4(const uint64_t* __restrict__ t,
     return R;
 }
 
+template <bool Q24>
 __global__ void count_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
                                  uint64_t* __restrict__ chunk_cnt /* [4][nchunks] */) {
     const int lane = threadIdx.x & 31;
@@ -757,7 +761,7 @@ __global__ void count_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, 
         for (int r = 0; r < (int)(kChunkLines / 32); r++) {
             const uint64_t j = i * kChunkLines + r * 32 + lane;
             if (j < nblocks) {
-                const LineIn4 L = make_line_in4(text, n, j);
+                const LineIn4 L = make_line_in4<Q24>(text, n, j);
 #pragma unroll
                 for (int c = 0; c < 4; c++) sum[c] += L.cnt[c];
             }
@@ -771,26 +775,32 @@ __global__ void count_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, 
     }
 }
 
+// QuadRank32: value v_c = rank(192 j + 96, c) - L0_c in word c / 2, half c % 2.
+// QuadRank24_8: a_c = rank(192 j + 64, c) - L0_c (< 2^16 * 192 < 2^24) and
+// b_c = the count of c in chars 64 .. 191 (<= 128), as a_c | b_c << 24 in the
+// same place.
+template <bool Q24>
 __global__ void layout_in4_kernel(const uint64_t* __restrict__ text, uint64_t n, uint64_t nblocks, uint64_t nchunks,
                                   const uint64_t* __restrict__ chunk_base /* [4][nchunks] */,
                                   uint4* __restrict__ lines, uint64_t* __restrict__ l0tab /* [nl0][4] */) {
+    constexpr uint64_t kPer = Q24 ? kChunksPerL0_24 : kChunksPerL0;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t i = warp; i < nchunks; i += nwarps) {
         uint64_t running[4];
-        const uint64_t first = i & ~(kChunksPerL0 - 1);
+        const uint64_t first = i & ~(kPer - 1);
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const uint64_t base = chunk_base[c * nchunks + i];
             running[c] = base - chunk_base[c * nchunks + first];
-            if (lane == 0 && i == first) l0tab[4 * (i / kChunksPerL0) + c] = base;
+            if (lane == 0 && i == first) l0tab[4 * (i / kPer) + c] = base;
         }
         for (int r = 0; r < (int)(kChunkLines / 32); r++) {
             const uint64_t j = i * kChunkLines + r * 32 + lane;
             const bool live = j < nblocks;
             LineIn4 L;
-            if (live) L = make_line_in4(text, n, j);
+            if (live) L = make_line_in4<Q24>(text, n, j);
             uint64_t val[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) {
@@ -801,7 +811,8 @@ __global__ void layout_in4_kernel(const uint64_t* __restrict__ text, uint64_t n,
                     const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += u;
                 }
-                val[c] = running[c] + (incl - v) + (live ? L.mid[c] : 0);  // rank(192 j + 96, c) - L0
+                val[c] = running[c] + (incl - v) + (live ? L.mid[c] : 0);  // rank(192 j + 96 or 64, c) - L0
+                if (Q24 && live) val[c] |= (uint64_t)(L.cnt[c] - L.mid[c]) << 24;
                 running[c] += __shfl_sync(0xffffffffu, incl, 31);
             }
             if (live) {
@@ -827,7 +838,7 @@ unsigned grid_for_warps(uint64_t nwarps) {
 
 }  // namespace
 
-// The two inline-32 layouts: chunk counts, scans, lines and the L0 table.
+// The inline layouts: chunk counts, scans, lines and the L0 table.
 int build_inline_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
     const uint64_t nchunks = (idx->nblocks + kChunkLines - 1) / kChunkLines;
     const int nsym = idx->sigma == 2 ? 1 : 4;
@@ -853,11 +864,17 @@ int build_inline_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s) {
         else if (rc == QR_OK)
             layout_in2_kernel<0><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines, l0);
     } else {
-        count_in4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
+        const bool q24 = idx->layout == QR_LAYOUT_INLINE24_8;
+        if (q24) count_in4_kernel<true><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
+        else count_in4_kernel<false><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, cnt);
         for (int c = 0; c < 4 && rc == QR_OK; c++)
             rc = exclusive_scan_u64(cnt + c * nchunks, base + c * nchunks, nchunks, s);
-        if (rc == QR_OK)
-            layout_in4_kernel<<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines, l0);
+        if (rc == QR_OK && q24)
+            layout_in4_kernel<true><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines,
+                                                            l0);
+        else if (rc == QR_OK)
+            layout_in4_kernel<false><<<grid, threads, 0, s>>>(d_text, idx->n, idx->nblocks, nchunks, base, idx->lines,
+                                                             l0);
     }
     cudaError_t le = cudaGetLastError();
     cudaFreeAsync(cnt, s);

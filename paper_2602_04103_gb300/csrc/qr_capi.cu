@@ -43,11 +43,12 @@ uint64_t block_chars(int sigma, int layout) {
     if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kB2L : kB4L;
     if (layout == QR_LAYOUT_INLINE32) return sigma == 2 ? kB2w : kB4w;
     if (layout == QR_LAYOUT_INLINE32X2) return kB2x;
+    if (layout == QR_LAYOUT_INLINE24_8) return kB4w;
     return sigma == 2 ? kB2 : kB4;
 }
 uint64_t super_lines(int sigma, int layout) {
     if (layout == QR_LAYOUT_LINE128) return sigma == 2 ? kSuper2L : kSuper4L;
-    if (inline_layout(layout)) return kL0Lines;
+    if (inline_layout(layout)) return 1ull << l0_shift(layout);
     return sigma == 2 ? kSuper2 : kSuper4;
 }
 uint64_t line_bytes(int layout) { return layout == QR_LAYOUT_LINE128 ? 128 : 64; }
@@ -96,10 +97,12 @@ int qr_build_ex(const uint64_t* text, uint64_t n, int sigma, int text_on_device,
     *out = nullptr;
     if (sigma != 2 && sigma != 4) return fail(QR_EINVAL, "qr_build: sigma must be 2 or 4");
     if (layout != QR_LAYOUT_PAPER && layout != QR_LAYOUT_SECTOR && layout != QR_LAYOUT_LINE128 &&
-        layout != QR_LAYOUT_INLINE32 && layout != QR_LAYOUT_INLINE32X2)
+        layout != QR_LAYOUT_INLINE32 && layout != QR_LAYOUT_INLINE32X2 && layout != QR_LAYOUT_INLINE24_8)
         return fail(QR_EINVAL, "qr_build: unknown layout");
     if (layout == QR_LAYOUT_INLINE32X2 && sigma != 2)
         return fail(QR_EINVAL, "qr_build: QR_LAYOUT_INLINE32X2 is sigma 2 only");
+    if (layout == QR_LAYOUT_INLINE24_8 && sigma != 4)
+        return fail(QR_EINVAL, "qr_build: QR_LAYOUT_INLINE24_8 is sigma 4 only");
     if (sigma == 2 && n >= (1ull << 43)) return fail(QR_EINVAL, "qr_build: sigma 2 needs n < 2^43");
     if (sigma == 4 && n >= (1ull << 45)) return fail(QR_EINVAL, "qr_build: sigma 4 needs n < 2^45");
     if (!text && n > 0) return fail(QR_EINVAL, "qr_build: text is NULL");
@@ -395,8 +398,9 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
     float best_ms = 1e30f;
     cudaStream_t s = (cudaStream_t)stream;
     for (int layout : {QR_LAYOUT_PAPER, QR_LAYOUT_SECTOR, QR_LAYOUT_LINE128, QR_LAYOUT_INLINE32,
-                       QR_LAYOUT_INLINE32X2}) {
+                       QR_LAYOUT_INLINE32X2, QR_LAYOUT_INLINE24_8}) {
         if (layout == QR_LAYOUT_INLINE32X2 && sigma != 2) continue;
+        if (layout == QR_LAYOUT_INLINE24_8 && sigma != 4) continue;
         if (sigma == 2 || sigma == 4) {
             if (layout_overhead(sigma, layout, n < 4096 ? 1u << 30 : n) > max_overhead) continue;
         }

@@ -91,6 +91,16 @@ constexpr uint64_t kB4w = 192;
 constexpr uint64_t kMid4w = 96;
 constexpr int kL0Shift = 22;
 constexpr uint64_t kL0Lines = 1ull << kL0Shift;
+// QuadRank24_8 (QR_LAYOUT_INLINE24_8; paper Sec. 4.1): the chars and groups
+// of QuadRank32, and per symbol c one 32-bit word a_c | b_c << 24 in words 0
+// and 1 (as QuadRank32's values): a_c (24 bits) = rank at the end of group 0
+// (char 64 of the line) minus the line's L0 entry, b_c (8 bits, <= 128) = the
+// count of c in groups 1 and 2 (chars 64 .. 191), so that rank at the end of
+// group 2 (char 192) = a_c + b_c.  A query in group 0 or 2 counts back from
+// the end of its group, one in group 1 forward from its start: at most 64
+// chars.  The 24-bit values need L0 blocks of 2^16 lines (2^16 * 192 < 2^24).
+constexpr int kL0Shift24 = 16;
+constexpr uint64_t kL0Lines24 = 1ull << kL0Shift24;
 
 // Status bits written by kernels (same values as the QR_E* status codes).
 constexpr uint32_t kStatusRange = QR_ERANGE;
@@ -485,6 +495,51 @@ __device__ __forceinline__ void quad32_finish4(const uint64_t l0[4], const u64x4
     }
 }
 
+// QuadRank24_8: position d (< 192) of a line whose sectors are S0, S1.  The
+// group g = d / 64 holds the counted chars: [d, 64 g + 64) subtracted from
+// the rank at the group's end for g = 0 and 2, [64, d) added to the rank at
+// char 64 for g = 1.
+struct Quad24Words {
+    uint64_t nl, nh, m;  // the group's ~low / ~high words and the mask of the counted chars
+    uint32_t g;
+};
+__device__ __forceinline__ Quad24Words quad24_words(const u64x4& S0, const u64x4& S1, uint32_t d) {
+    Quad24Words q;
+    q.g = d >> 6;
+    const uint32_t t = d & 63;
+    q.nl = q.g == 0 ? S0.c : q.g == 1 ? S1.a : S1.c;
+    q.nh = q.g == 0 ? S0.d : q.g == 1 ? S1.b : S1.d;
+    const uint64_t below = low_mask(t);  // chars 64 g .. 64 g + t - 1
+    q.m = q.g == 1 ? below : ~below;
+    return q;
+}
+// The rank at the reference point of group g for symbol c: l0 + a_c, plus b_c
+// for group 2.
+__device__ __forceinline__ uint64_t quad24_mid(uint64_t l0_c, const u64x4& S0, int c, uint32_t g) {
+    const uint32_t v = quad32_value(S0, c);
+    return l0_c + (v & 0xFFFFFFu) + (g == 2 ? (v >> 24) : 0u);
+}
+__device__ __forceinline__ uint64_t quad24_finish1(uint64_t l0_c, const u64x4& S0, const u64x4& S1, uint32_t d,
+                                                   int c) {
+    const Quad24Words q = quad24_words(S0, S1, d);
+    const uint64_t cl = 0ull - (uint64_t)(c & 1), ch = 0ull - (uint64_t)(c >> 1);
+    const uint32_t cnt = popc64((q.nl ^ cl) & (q.nh ^ ch) & q.m);
+    const uint64_t mid = quad24_mid(l0_c, S0, c, q.g);
+    return q.g == 1 ? mid + cnt : mid - cnt;
+}
+__device__ __forceinline__ void quad24_finish4(const uint64_t l0[4], const u64x4& S0, const u64x4& S1, uint32_t d,
+                                               uint64_t r[4]) {
+    const Quad24Words q = quad24_words(S0, S1, d);
+    const uint64_t L = ~q.nl & q.m, H = ~q.nh & q.m;
+    const uint32_t n3 = popc64(L & H), nl = popc64(L), nh = popc64(H), nm = popc64(q.m);
+    const uint32_t n[4] = {nm - nl - nh + n3, nl - n3, nh - n3, n3};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const uint64_t mid = quad24_mid(l0[c], S0, c, q.g);
+        r[c] = q.g == 1 ? mid + n[c] : mid - n[c];
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct DeviceProps {
     int device = -1;
@@ -524,7 +579,11 @@ uint64_t block_chars(int sigma, int layout);
 uint64_t super_lines(int sigma, int layout);
 uint64_t line_bytes(int layout);
 uint64_t super_entry_bytes(int sigma, int layout);
-inline bool inline_layout(int layout) { return layout == QR_LAYOUT_INLINE32 || layout == QR_LAYOUT_INLINE32X2; }
+inline bool inline_layout(int layout) {
+    return layout == QR_LAYOUT_INLINE32 || layout == QR_LAYOUT_INLINE32X2 || layout == QR_LAYOUT_INLINE24_8;
+}
+// log2 of the lines per L0 entry of an inline layout
+inline int l0_shift(int layout) { return layout == QR_LAYOUT_INLINE24_8 ? kL0Shift24 : kL0Shift; }
 // Build the layout into an already sized index from a device text.
 int build_rank_index(qr_index* idx, const uint64_t* d_text, cudaStream_t s);
 // Launch the rank kernels (no argument checks beyond the mode); rank4 = 0:

@@ -398,7 +398,7 @@ KernelFn pick_sector(int k) {
 
 KernelFn pick_kind(int kind, int k, int load, int layout) {
     if (layout == QR_LAYOUT_LINE128) return pick_line_kind(kind, k);
-    if (inline_layout(layout)) return pick_in32_kind(kind, k, layout == QR_LAYOUT_INLINE32X2);
+    if (inline_layout(layout)) return pick_in32_kind(kind, k, layout);
     const bool sector = layout == QR_LAYOUT_SECTOR;
     if (sector) {
         switch (kind) {
@@ -577,7 +577,7 @@ int launch_chain(const qr_index* idx, const uint64_t* q0, uint64_t nchains, uint
     const bool quad = idx->sigma == 4, sector = idx->layout == QR_LAYOUT_SECTOR;
     ChainFn fn = idx->layout == QR_LAYOUT_LINE128 ? pick_chain_line(quad)
                  : inline_layout(idx->layout)
-                     ? pick_chain_in32(quad, idx->layout == QR_LAYOUT_INLINE32X2)
+                     ? pick_chain_in32(quad, idx->layout)
                      : quad ? (sector ? rank_chain_kernel<true, true> : rank_chain_kernel<true, false>)
                             : (sector ? rank_chain_kernel<false, true> : rank_chain_kernel<false, false>);
     uint64_t grid = (nchains + 255) / 256;

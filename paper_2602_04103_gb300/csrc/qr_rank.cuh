@@ -47,9 +47,10 @@ __device__ __forceinline__ uint64_t chain_next(uint64_t q, uint64_t r, uint64_t 
 using ChainFn = void (*)(RankArgs, uint64_t);
 ChainFn pick_chain_line(bool quad);
 
-// Kernels of the 32-bit inline layouts (qr_rank_in32.cu): x2 = BiRank32x2
-// (QR_LAYOUT_INLINE32X2), else BiRank32 / QuadRank32 (QR_LAYOUT_INLINE32).
-KernelFn pick_in32_kind(int kind, int k, bool x2);
-ChainFn pick_chain_in32(bool quad, bool x2);
+// Kernels of the inline layouts (qr_rank_in32.cu) for layout
+// QR_LAYOUT_INLINE32, _INLINE32X2 or _INLINE24_8; nullptr where the layout
+// has no such kernel (BiRank32x2 is sigma 2 only, QuadRank24_8 sigma 4 only).
+KernelFn pick_in32_kind(int kind, int k, int layout);
+ChainFn pick_chain_in32(bool quad, int layout);
 
 }  // namespace qr

@@ -740,15 +740,17 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
 // is the upper half.  Sector layout: the one self-contained half.
 // PREFIX (sigma 4): prefix_rank(q, c), the sum of the four counts up to c,
 // from all four superblock offsets.
-// LAY: the index layout (QR_LAYOUT_PAPER, _SECTOR, _INLINE32, _INLINE32X2).
+// LAY: the index layout (QR_LAYOUT_PAPER, _SECTOR, _INLINE32, _INLINE32X2,
+// _INLINE24_8).  QuadRank24_8 keeps its values and chars 0 .. 63 in the first
+// sector: a query there loads that sector alone, the others both.
 template <int LAY, bool QUAD, bool PREFIX = false>
 struct RegionLoad {
-    u64x4 X, X2;     // the sector(s) the query needs (X2: the second sector of an INLINE32 line)
+    u64x4 X, X2;     // the sector(s) the query needs (X2: the second sector of an inline line)
     uint64_t w0, w1;
     uint32_t s;
     uint4 s4;
     uint64_t l0;     // inline layouts: the L0 entry (of the query's symbol)
-    uint4 l4a, l4b;  // QuadRank32 with all four symbols: the four L0 entries
+    uint4 l4a, l4b;  // sigma-4 inline layouts, all four symbols: the four L0 entries
     uint32_t pos;
 };
 
@@ -791,6 +793,26 @@ __device__ __forceinline__ void region_issue(RegionLoad<LAY, QUAD, PREFIX>& L, c
         L.pos = p - h * (uint32_t)kHalf2x;
         L.l0 = __ldg((const uint64_t*)supers + (j >> kL0Shift));
         L.X = ix_ld32<EL>(lines + 4 * j + 2 * h, pol);
+        L.w0 = L.w1 = 0;
+    } else if (LAY == QR_LAYOUT_INLINE24_8) {  // sigma 4 only
+        uint64_t j;
+        if (N32) {
+            const uint32_t j32 = __umulhi((uint32_t)(q >> 6), 0xAAAAAAABu) >> 1;
+            j = j32;
+            L.pos = (uint32_t)q - j32 * (uint32_t)kB4w;
+        } else {
+            j = div192(q);
+            L.pos = (uint32_t)(q - j * kB4w);
+        }
+        const uint64_t* l0 = (const uint64_t*)supers + 4 * (j >> kL0Shift24);
+        if (PREFIX) {
+            L.l4a = __ldg((const uint4*)l0);
+            L.l4b = __ldg((const uint4*)l0 + 1);
+        } else {
+            L.l0 = __ldg(l0 + c);
+        }
+        L.X = ix_ld32<EL>(lines + 4 * j, pol);
+        L.X2 = L.pos >= 64 ? ix_ld32<EL>(lines + 4 * j + 2, pol) : u64x4{0, 0, 0, 0};
         L.w0 = L.w1 = 0;
     } else if (LAY == QR_LAYOUT_INLINE32) {
         uint64_t j;
@@ -878,9 +900,10 @@ __device__ __forceinline__ void region_issue(RegionLoad<LAY, QUAD, PREFIX>& L, c
 // four superblock offsets).
 template <int LAY>
 __device__ __forceinline__ void region_finish4(const RegionLoad<LAY, true, true>& L, uint64_t r[4]) {
-    if (LAY == QR_LAYOUT_INLINE32) {
+    if (LAY == QR_LAYOUT_INLINE32 || LAY == QR_LAYOUT_INLINE24_8) {
         const uint64_t b[4] = {lo64(L.l4a), hi64(L.l4a), lo64(L.l4b), hi64(L.l4b)};
-        quad32_finish4(b, L.X, L.X2, L.pos, r);
+        if (LAY == QR_LAYOUT_INLINE24_8) quad24_finish4(b, L.X, L.X2, L.pos, r);
+        else quad32_finish4(b, L.X, L.X2, L.pos, r);
         return;
     }
     const uint32_t s4[4] = {L.s4.x, L.s4.y, L.s4.z, L.s4.w};
@@ -907,6 +930,7 @@ __device__ __forceinline__ uint64_t region_finish(const RegionLoad<LAY, QUAD, PR
         const uint64_t r1 = in32x2_finish(L.l0, L.X, L.pos);
         return c == 1 ? r1 : q - r1;
     }
+    if (LAY == QR_LAYOUT_INLINE24_8) return quad24_finish1(L.l0, L.X, L.X2, L.pos, (int)c);
     if (LAY == QR_LAYOUT_INLINE32) {
         if (!QUAD) {
             const uint64_t r1 = in32_bi_finish(L.l0, L.X, L.X2, L.pos);
@@ -1194,8 +1218,13 @@ RankFn pick_rank_lay(bool quad, bool vec, int v, int mode, bool n32) {
             return vec ? pick_variant<LAY, true, true>(v) : pick_variant<LAY, true, false>(v);
         }
     }
-    if (n32 && kN32) return vec ? pick_variant<LAY, false, true, kN32>(v) : pick_variant<LAY, false, false, kN32>(v);
-    return vec ? pick_variant<LAY, false, true>(v) : pick_variant<LAY, false, false>(v);
+    if constexpr (LAY == QR_LAYOUT_INLINE24_8) {
+        return nullptr;  // sigma 4 only
+    } else {
+        if (n32 && kN32)
+            return vec ? pick_variant<LAY, false, true, kN32>(v) : pick_variant<LAY, false, false, kN32>(v);
+        return vec ? pick_variant<LAY, false, true>(v) : pick_variant<LAY, false, false>(v);
+    }
 }
 
 RankFn pick_region_rank(int layout, bool quad, bool vec, int v, int mode, bool n32) {
@@ -1204,6 +1233,7 @@ RankFn pick_region_rank(int layout, bool quad, bool vec, int v, int mode, bool n
         case QR_LAYOUT_SECTOR: return pick_rank_lay<QR_LAYOUT_SECTOR>(quad, vec, v, mode, n32);
         case QR_LAYOUT_INLINE32: return pick_rank_lay<QR_LAYOUT_INLINE32>(quad, vec, v, mode, n32);
         case QR_LAYOUT_INLINE32X2: return pick_rank_lay<QR_LAYOUT_INLINE32X2>(quad, vec, v, mode, n32);
+        case QR_LAYOUT_INLINE24_8: return pick_rank_lay<QR_LAYOUT_INLINE24_8>(quad, vec, v, mode, n32);
         default: return nullptr;
     }
 }
@@ -1217,7 +1247,11 @@ BaseFn pick_base_lay(bool quad, bool prefix, bool n32) {
         if (prefix) return n32 && kN32 ? region_base<LAY, true, true, kN32> : region_base<LAY, true, true, false>;
         if (quad) return n32 && kN32 ? region_base<LAY, true, false, kN32> : region_base<LAY, true, false, false>;
     }
-    return n32 && kN32 ? region_base<LAY, false, false, kN32> : region_base<LAY, false, false, false>;
+    if constexpr (LAY == QR_LAYOUT_INLINE24_8) {
+        return nullptr;  // sigma 4 only
+    } else {
+        return n32 && kN32 ? region_base<LAY, false, false, kN32> : region_base<LAY, false, false, false>;
+    }
 }
 
 BaseFn pick_region_base(int layout, bool quad, bool prefix, bool n32) {
@@ -1226,6 +1260,7 @@ BaseFn pick_region_base(int layout, bool quad, bool prefix, bool n32) {
         case QR_LAYOUT_SECTOR: return pick_base_lay<QR_LAYOUT_SECTOR>(quad, prefix, n32);
         case QR_LAYOUT_INLINE32: return pick_base_lay<QR_LAYOUT_INLINE32>(quad, prefix, n32);
         case QR_LAYOUT_INLINE32X2: return pick_base_lay<QR_LAYOUT_INLINE32X2>(quad, prefix, n32);
+        case QR_LAYOUT_INLINE24_8: return pick_base_lay<QR_LAYOUT_INLINE24_8>(quad, prefix, n32);
         default: return nullptr;
     }
 }

@@ -56,6 +56,32 @@ def test_binding_loads_and_reports_errors_without_gpu(so_path):
     assert capi.lib.qr_rank(None, None, 0, 1, None, None) == capi.QR_EINVAL
 
 
+def test_binding_constants_match_the_headers():
+    """Every QR_* / QFM_* constant the binding names has the header's value."""
+    from paper_2602_04103_gb300 import capi
+    defines = {}
+    for h in (ROOT / "include").glob("*.h"):
+        for m in re.finditer(r"^#define\s+((?:QR|QFM)_\w+)\s+\(?(-?\d+)", h.read_text(), flags=re.M):
+            defines[m.group(1)] = int(m.group(2))
+    named = [k for k in dir(capi) if re.fullmatch(r"(QR|QFM)_[A-Z0-9_]+", k)]
+    assert "QR_LAYOUT_INLINE24_8" in named
+    for k in named:
+        assert k in defines and defines[k] == getattr(capi, k), k
+
+
+def test_layout_rules_checked_on_the_host(so_path):
+    """qr_build_ex refuses a layout the alphabet does not have before any CUDA
+    call: BiRank32x2 is sigma 2 only, QuadRank24_8 sigma 4 only."""
+    from paper_2602_04103_gb300 import capi
+    h = ctypes.c_void_p()
+    word = (ctypes.c_uint64 * 1)(0)
+    for sigma, layout in ((4, capi.QR_LAYOUT_INLINE32X2), (2, capi.QR_LAYOUT_INLINE24_8), (2, 6), (4, -1)):
+        rc = capi.lib.qr_build_ex(word, 10, sigma, 0, layout, None, ctypes.byref(h))
+        assert rc == capi.QR_EINVAL and not h.value, (sigma, layout)
+    capi.lib.qr_build_ex(word, 10, 2, 0, capi.QR_LAYOUT_INLINE24_8, None, ctypes.byref(h))
+    assert b"sigma 4 only" in capi.lib.qr_last_error()
+
+
 def test_division_constants():
     # floor(q / 496) and floor(q / 224) by multiply-high, as the kernels compute them
     import random

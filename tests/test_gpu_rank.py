@@ -22,10 +22,12 @@ B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
 B2S, S2S, B4S, S4S = 480, 480 * 128, 192, 192 * 256
 B2L, S2L, B4L, S4L = 1008, 1008 * 32, 480, 480 * 64
 B2W, B2X, B4W, L0 = 480, 448, 192, 1 << 22   # inline-32 layouts: data per line, lines per L0 entry
+L0_24 = 1 << 16                                # QuadRank24_8: lines per L0 entry
 # QR_LAYOUT_PAPER (BiRank16 / QuadRank16), _SECTOR, _LINE128, _INLINE32 (BiRank32 /
-# QuadRank32), _INLINE32X2 (BiRank32x2, sigma 2 only)
+# QuadRank32), _INLINE32X2 (BiRank32x2, sigma 2 only), _INLINE24_8 (QuadRank24_8,
+# sigma 4 only)
 BI_LAYOUTS = [0, 1, 2, 3, 4]
-DNA_LAYOUTS = [0, 1, 2, 3]
+DNA_LAYOUTS = [0, 1, 2, 3, 5]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -99,7 +101,8 @@ def test_edge_lengths_bits(n):
         check_bits(synth.bits(n + 3, n, 0.5), n, layout=layout)
 
 
-@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 47, 48, 49, 95, 96, 97, 127, 128, 143, 144, 145, 191, 192, 193,
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129, 143, 144, 145,
+                               191, 192, 193, 255, 256, 257, 319, 320, 321,
                                223, 224, 225, 239, 240, 241, 447, 448, 449, 479, 480, 481, S4L - 1, S4L, S4L + 1,
                                S4S - 1, S4S, S4S + 1, S4 - 1, S4, S4 + 1, 2 * S4 + 96])
 def test_edge_lengths_dna(n):
@@ -250,7 +253,8 @@ def test_out_of_range_and_bad_symbols():
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
-@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1), (0, 2), (0, 3), (0, 4)])
+@pytest.mark.parametrize("load,layout", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 1), (0, 2), (0, 3), (0, 4),
+                                         (0, 5)])
 @pytest.mark.parametrize("threads", [64, 256, 512])
 def test_every_tuning(k, load, layout, threads):
     from paper_2602_04103_gb300 import capi
@@ -261,7 +265,7 @@ def test_every_tuning(k, load, layout, threads):
     q = synth.queries(19, n, 100_003)
     q4 = synth.queries(20, n4, 100_003)
     cv = synth.symbols(21, q4.size, 4)
-    idx = build(words, n, 2, layout)
+    idx = build(words, n, 2, layout if layout in BI_LAYOUTS else 0)
     capi.qr_set_tuning(idx, k, threads, load, 0)
     assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
     if layout in DNA_LAYOUTS:
@@ -396,11 +400,12 @@ def test_autotune_and_build_tuned():
     assert t["queries_per_thread"] in (1, 2, 4, 8) and t["load_mode"] in (0, 1, 2, 3, 4)
     assert capi.qr_get_tuning(idx) == t
     assert np.array_equal(rank(idx, q, 1), oracle.rank(words, n, 2, q, 1)[0])
-    # a 5% space budget admits only BiRank16 (3.28%); 7% admits BiRank16x2 (6.72%) too
+    # a 5% space budget admits only BiRank16 (3.28%); 7% admits BiRank16x2 (6.72%)
+    # and BiRank32 (6.67%) too, and the fastest of the three on this batch wins
     idx5, lay5 = capi.qr_build_tuned(dev_u64(words), n, 2, dq, scratch, c=1, max_overhead=0.05)
     assert lay5 == 0
     idx7, lay7 = capi.qr_build_tuned(dev_u64(words), n, 2, dq, scratch, c=0, max_overhead=0.07)
-    assert lay7 in (0, 1)
+    assert lay7 in (0, 1, 3)
     for i in (idx5, idx7):
         assert np.array_equal(rank(i, q, 0), oracle.rank(words, n, 2, q, 0)[0])
     with pytest.raises(capi.QRError):
@@ -524,13 +529,15 @@ def test_prefix_rank(layout):
         capi.qr_prefix_rank(build(synth.bits(1, 100, 0.5), 100, 2), dq, 0, out)
 
 
-@pytest.mark.parametrize("layout", BI_LAYOUTS)
+@pytest.mark.parametrize("layout", sorted(set(BI_LAYOUTS) | set(DNA_LAYOUTS)))
 @pytest.mark.parametrize("sigma", [2, 4])
 def test_rank_chain(layout, sigma):
     import torch
     from paper_2602_04103_gb300 import capi
     if sigma == 4 and layout not in DNA_LAYOUTS:
         pytest.skip("BiRank32x2 is sigma 2 only")
+    if sigma == 2 and layout not in BI_LAYOUTS:
+        pytest.skip("QuadRank24_8 is sigma 4 only")
     n = 4 * S2 + 99 if sigma == 2 else 4 * S4 + 99
     words = synth.bits(91, n, 0.5) if sigma == 2 else synth.dna_uniform(92, n)
     idx = build(words, n, sigma, layout)
@@ -689,6 +696,100 @@ def test_inline_layout_matches_definitions_dna():
             assert lo | (hi << 1) == (int(codes[c]) if c < n else 0), (j, d)
 
 
+def quad24_fields(lines):
+    """QuadRank24_8's per-symbol words (word 0 = w0 | w1 << 32, word 1 = w2 |
+    w3 << 32) split into a (low 24 bits) and b (high 8 bits), [nb, 4] each."""
+    w0, w1 = lines[:, 0], lines[:, 1]
+    w = np.stack([w0 & np.uint64(0xFFFFFFFF), w0 >> np.uint64(32), w1 & np.uint64(0xFFFFFFFF),
+                  w1 >> np.uint64(32)], axis=1)
+    return w & np.uint64(0xFFFFFF), w >> np.uint64(24)
+
+
+def test_quad24_layout_matches_definitions():
+    """QuadRank24_8 (Sec. 4.1): chars of QuadRank32 (words 2 + 2g / 3 + 2g =
+    ~low / ~high bits of chars 64 g .. 64 g + 63); per symbol c,
+    a_c = rank(192 j + 64, c) minus the rank of c at the start of the line's
+    L0 block (2^16 lines) and b_c = the count of c in chars 64 .. 191 of the
+    line, so that a_c + b_c = rank(192 j + 192, c) minus the same.  The text
+    spans four L0 blocks, and the L0 table holds the rank at each start."""
+    n = 3 * L0_24 * B4W + 5 * B4W + 77
+    words = synth.dna_uniform(227, n)
+    idx = build(words, n, 4, 5)
+    info, lines, l0 = read_inline(idx)
+    nb = n // B4W + 1
+    assert info["nblocks"] == nb and info["super_blocks"] == L0_24 and info["nsuper"] == 4
+    js = np.arange(nb, dtype=np.uint64)
+    starts = np.minimum(np.arange(4, dtype=np.uint64) * np.uint64(L0_24 * B4W), np.uint64(n))
+    want_l0, rc = oracle.rank4(words, n, starts, threads=4)
+    assert rc == 0 and np.array_equal(l0.reshape(4, 4), want_l0)
+    base = want_l0[(js // np.uint64(L0_24)).astype(np.int64)]
+    a, b = quad24_fields(lines)
+    for off, got in ((64, a), (192, a + b)):
+        pos = js * np.uint64(B4W) + np.uint64(off)
+        r4, rc = oracle.rank4(words, n, np.minimum(pos, np.uint64(n)), threads=4)
+        r4[:, 0] += pos - np.minimum(pos, np.uint64(n))              # padding chars are A (code 0)
+        assert rc == 0 and np.array_equal(got, r4 - base), off
+    assert int(b.max()) <= 128 and int(a.max()) < L0_24 * B4W
+    codes = synth.unpack2(words, n)
+    for j in [0, 1, L0_24 - 1, L0_24, nb - 1]:
+        for d in range(B4W):
+            g, k = d // 64, d % 64
+            lo = (~int(lines[j, 2 + 2 * g]) >> k) & 1
+            hi = (~int(lines[j, 3 + 2 * g]) >> k) & 1
+            c = j * B4W + d
+            assert lo | (hi << 1) == (int(codes[c]) if c < n else 0), (j, d)
+
+
+def test_quad24_l0_boundaries():
+    """QuadRank24_8 over four L0 blocks: every query within 700 positions of
+    each block start and of each group boundary of the lines there, plus
+    2^20 uniform ones, against the oracle (rank with per-query symbols and
+    rank_4), direct and region-batched."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 4 * L0_24 * B4W - 3
+    words = synth.dna_gc_runs(synth.base_seed(305), n, 0.45, 0.05, 10, 2000)
+    idx = build(words, n, 4, 5)
+    starts = np.arange(1, 4) * (L0_24 * B4W)
+    edges = np.concatenate([np.arange(b - 700, b + 700) for b in starts])
+    q = np.concatenate([edges, synth.queries(synth.base_seed(306), n, 1 << 20), [0, n - 1, n]]).astype(np.uint64)
+    want4, rc = oracle.rank4(words, n, q, threads=8)
+    assert rc == 0
+    cv = synth.symbols(synth.base_seed(307), q.size, 4)
+    dq = dev_u64(q)
+    for mode in (capi.QR_BATCH_DIRECT, capi.QR_BATCH_REGIONS):
+        capi.qr_set_batch_mode(idx, mode)
+        out4 = torch.empty((q.size, 4), dtype=torch.int64, device="cuda")
+        capi.qr_rank4(idx, dq, out4)
+        assert np.array_equal(host_u64(out4).reshape(-1, 4), want4), mode
+        out = torch.empty_like(dq)
+        capi.qr_rank_c(idx, dq, dev_u8(cv), out)
+        assert np.array_equal(host_u64(out), want4[np.arange(q.size), cv]), mode
+    assert capi.qr_status(idx) == 0
+    idx.free()
+
+
+def test_quad24_values_near_their_bound():
+    """An all-T text over a whole L0 block: the last line's a_T reaches
+    (2^16 - 1) * 192 + 64, the largest a 24-bit value holds here, and every
+    b_T is 128; ranks around the next block's start are q for T, 0 for the
+    rest."""
+    n = L0_24 * B4W + 3000
+    codes = np.full(n, 3, dtype=np.uint8)
+    words = synth.pack2(codes)
+    idx = build(words, n, 4, 5)
+    info, lines, l0 = read_inline(idx)
+    a, b = quad24_fields(lines)
+    assert l0.reshape(-1, 4).tolist() == [[0, 0, 0, 0], [0, 0, 0, L0_24 * B4W]]
+    assert int(a[L0_24 - 1, 3]) == (L0_24 - 1) * B4W + 64 < 1 << 24
+    full = n // B4W                                            # lines before the partial last one
+    assert (b[:full, 3] == 128).all() and (b[:full, :3] == 0).all()
+    q = np.concatenate([np.arange(L0_24 * B4W - 1000, L0_24 * B4W + 1000), [n]]).astype(np.uint64)
+    r4 = rank4(idx, q)
+    assert np.array_equal(r4[:, 3], q) and not r4[:, :3].any()
+    idx.free()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("layout,sigma", [(3, 2), (4, 2), (3, 4)])
 def test_inline_l0_blocks(layout, sigma):
@@ -779,3 +880,13 @@ def test_inline_sizes_and_overheads():
     assert abs(over4 * 100 - 33.33) < 0.01
     with pytest.raises(capi.QRError):
         build(synth.dna_uniform(2, 1000), 1000, 4, 4)              # BiRank32x2 is sigma 2 only
+    # QuadRank24_8 (Sec. 4.1): 33.3% as QuadRank32, its L0 table one 32-byte
+    # entry per 2^16 lines
+    idx5 = build(synth.dna_uniform(3, 1000), 1000, 4, 5)
+    info5 = capi.qr_info(idx5)
+    assert info5["bytes_blocks"] == 64 * (1000 // B4W + 1) and info5["bytes_super"] == 32
+    assert info5["block_chars"] == B4W and info5["super_blocks"] == L0_24
+    over5 = (64 * nb4 + 32 * ((nb4 + L0_24 - 1) // L0_24)) * 8 / (2 * n4) - 1
+    assert abs(over5 * 100 - 33.33) < 0.01
+    with pytest.raises(capi.QRError):
+        build(synth.bits(2, 1000, 0.5), 1000, 2, 5)                # QuadRank24_8 is sigma 4 only

@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 
 TILE = 8192
 B2, S2, B4, S4 = 496, 496 * 128, 224, 224 * 256
-# the paper, sector and 32-bit inline layouts (the 128-byte line layout always runs direct);
-# QR_LAYOUT_INLINE32X2 (4) is sigma 2 only
+# the paper, sector and inline layouts (the 128-byte line layout always runs direct);
+# QR_LAYOUT_INLINE32X2 (4) is sigma 2 only, QR_LAYOUT_INLINE24_8 (5) sigma 4 only
 LAYOUTS = [0, 1, 3, 4]
-DNA_LAYOUTS = [0, 1, 3]
+DNA_LAYOUTS = [0, 1, 3, 5]
 U64MAX = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -126,12 +126,14 @@ def test_prefix_rank_tiles_ragged(layout):
         assert capi.qr_status(idx) == capi.QR_ERANGE
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", sorted(set(LAYOUTS) | set(DNA_LAYOUTS)))
 @pytest.mark.parametrize("sigma", [2, 4])
 def test_bad_queries_inside_batch(layout, sigma):
     from paper_2602_04103_gb300 import capi
     if sigma == 4 and layout not in DNA_LAYOUTS:
         pytest.skip("BiRank32x2 is sigma 2 only")
+    if sigma == 2 and layout not in LAYOUTS:
+        pytest.skip("QuadRank24_8 is sigma 4 only")
     n = 2 * (S2 if sigma == 2 else S4) + 999
     words = synth.bits(7, n, 0.3) if sigma == 2 else synth.dna_uniform(8, n)
     idx = regions_index(words, n, sigma, layout)
@@ -173,15 +175,16 @@ def test_degenerate_orders(layout, order):
     check(idx, words, n, 2, q, 1)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", sorted(set(LAYOUTS) | set(DNA_LAYOUTS)))
 @pytest.mark.parametrize("n", [0, 1, 2, 255, 256, 257, 495, 496, 497, 1000])
 def test_tiny_texts(layout, n):
     """Texts shorter than 256 regions: a region is one or a few positions."""
-    words = synth.bits(n + 11, n, 0.5)
-    idx = regions_index(words, n, 2, layout)
     q = np.concatenate([np.arange(n + 1, dtype=np.uint64), synth.queries(n + 12, n, 3000)])
-    for c in (0, 1):
-        check(idx, words, n, 2, q, c)
+    if layout in LAYOUTS:
+        words = synth.bits(n + 11, n, 0.5)
+        idx = regions_index(words, n, 2, layout)
+        for c in (0, 1):
+            check(idx, words, n, 2, q, c)
     if layout in DNA_LAYOUTS:
         dwords = synth.dna_uniform(n + 13, n)
         idx4 = regions_index(dwords, n, 4, layout)

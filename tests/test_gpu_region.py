@@ -76,6 +76,47 @@ def check(idx, words, n, sigma, q, c, status=0):
     assert capi.qr_status(idx) == status
 
 
+RANK_VARIANTS = range(4)   # qr_set_region_tuning
+
+
+@pytest.mark.parametrize("variant", RANK_VARIANTS)
+@pytest.mark.parametrize("tiles", [1, 38, 32])
+def test_every_rank_pass_variant(variant, tiles):
+    """Every rank-pass variant, on batches whose tile count is 1, not a
+    multiple of the 16 runs of a step, and a multiple of it; every
+    region-batched layout, both alphabets, bad queries and symbols inside."""
+    from paper_2602_04103_gb300 import capi
+    m = tiles * TILE - (123 if tiles > 1 else 0)
+    n2, n4 = 7 * S2 + 11, 5 * S4 + 13
+    words = synth.bits(synth.base_seed(70), n2, 0.5)
+    dwords = synth.dna_uniform(synth.base_seed(71), n4)
+    q2 = synth.queries(synth.base_seed(72) + tiles, n2, m)
+    q2[::1009] = n2 + 3
+    q4 = synth.queries(synth.base_seed(73) + tiles, n4, m)
+    cv = synth.symbols(synth.base_seed(74) + tiles, m, 4)
+    cv[::997] = 4
+    for layout in sorted(set(LAYOUTS) | set(DNA_LAYOUTS)):
+        if layout in LAYOUTS:
+            idx = regions_index(words, n2, 2, layout)
+            capi.qr_set_region_tuning(idx, variant)
+            check(idx, words, n2, 2, q2, 1, status=capi.QR_ERANGE)
+            idx.free()
+        if layout in DNA_LAYOUTS:
+            idx = regions_index(dwords, n4, 4, layout)
+            capi.qr_set_region_tuning(idx, variant)
+            check(idx, dwords, n4, 4, q4, cv, status=capi.QR_EBADSYM)
+            idx.free()
+
+
+def test_region_tuning_range():
+    from paper_2602_04103_gb300 import capi
+    idx = build(synth.bits(1, 1000, 0.5), 1000, 2, 1)
+    for v in (-1, 4):
+        with pytest.raises(capi.QRError):
+            capi.qr_set_region_tuning(idx, v)
+    idx.free()
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_bits_tiles_ragged(layout):
     n = 3 * S2 + 1234

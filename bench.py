@@ -633,7 +633,37 @@ def run_quadrank(args, stream, peak):
     idx4.free()
     del dq, dc, o4, d4
     torch.cuda.empty_cache()
+    res["quadrank_gc_runs"] = run_quadrank_gc(args, stream)
     return res
+
+
+def run_quadrank_gc(args, stream):
+    """The second QuadRank text: GC 40 %, homopolymer runs of 10..1000 over 5 %
+    of it; rank with random symbols and rank_4, each on its tuned layout."""
+    import torch
+    from paper_2602_04103_gb300 import capi, workloads
+    m = 1 << args.log_m
+    n4 = 1 << args.log_n4
+    t4, q4, c4 = workloads.quadrank_inputs(args.log_n4, args.log_m, "gc_runs")
+    dq, dc = dev_u64(q4), torch.from_numpy(c4).cuda()
+    d4 = dev_u64(t4)
+    del t4
+    row = {"text": "gc_runs: P(C) = P(G) = 0.2, P(A) = P(T) = 0.3, runs of one symbol (10..1000) over 5 %"}
+    idx4, layout, _ = workloads.build_tuned(d4, n4, 4, dq, c=dc)
+    o = torch.empty_like(dq)
+    ms = best_ms(lambda: capi.qr_rank_c(idx4, dq, dc, o), stream)
+    row["rank_random_c"] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "layout": layout}
+    idx4.free()
+    del o
+    o4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
+    idx4, layout, _ = workloads.build_tuned(d4, n4, 4, dq, rank4=True)
+    ms = best_ms(lambda: capi.qr_rank4(idx4, dq, o4), stream)
+    row["rank4"] = {"Gq_s": round(m / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "layout": layout}
+    idx4.free()
+    del dq, dc, o4, d4
+    torch.cuda.empty_cache()
+    log(f"[bench] quadrank gc_runs: {row['rank_random_c']['Gq_s']} / {row['rank4']['Gq_s']} Gq/s")
+    return row
 
 
 def run_fm(args, stream, part="all"):

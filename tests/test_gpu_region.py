@@ -260,6 +260,37 @@ def test_unaligned_query_array(layout):
     assert capi.qr_status(idx) == 0
 
 
+@pytest.mark.parametrize("layout", [1, 3])
+@pytest.mark.parametrize("m", [TILE, 3 * TILE + 17])
+def test_unaligned_output_array(layout, m):
+    """Output arrays 16-byte aligned and 8 bytes past a 16-byte boundary agree
+    with the oracle, on full and partial tiles, for rank and prefix_rank."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 3 * S2 + 99
+    words = synth.bits(synth.base_seed(64), n, 0.5)
+    idx = regions_index(words, n, 2, layout)
+    q = synth.queries(synth.base_seed(65) + m, n, m)
+    q[::501] = n + 7
+    dq = dev_u64(q)
+    for off in (0, 1):
+        out = torch.empty(m + 1, dtype=torch.int64, device="cuda")[off:off + m]
+        assert out.data_ptr() % 16 == 8 * off
+        capi.qr_rank(idx, dq, 0, out)
+        assert np.array_equal(host_u64(out), expect(words, n, 2, q, 0)), off
+        assert capi.qr_status(idx) == capi.QR_ERANGE
+    n4 = 2 * S4 + 5
+    w4 = synth.dna_uniform(synth.base_seed(66), n4)
+    idx4 = regions_index(w4, n4, 4, layout)
+    q4 = synth.queries(synth.base_seed(67) + m, n4, m)
+    dq4 = dev_u64(q4)
+    for off in (0, 1):
+        out = torch.empty(m + 1, dtype=torch.int64, device="cuda")[off:off + m]
+        capi.qr_prefix_rank(idx4, dq4, 2, out)
+        want, rc = oracle.prefix_rank(w4, n4, 4, q4, 2)
+        assert rc == 0 and np.array_equal(host_u64(out), want), off
+
+
 def test_empty_batch():
     import torch
     from paper_2602_04103_gb300 import capi

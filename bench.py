@@ -137,6 +137,31 @@ def best_ms(fn, stream, reps=3):
     return float(np.median(per))
 
 
+def host_copy_bound(qh, oh, dev_out, stream, reps: int = 2):
+    """The e2e path's own ceiling on this host: the pinned query buffer copied
+    in and the result buffer copied out at once, on two streams, as the
+    pipeline overlaps them; 16 bytes per query cross the link."""
+    import torch
+    d_in = torch.empty_like(dev_out)
+    s2 = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            d_in.copy_(qh, non_blocking=True)
+        s2.wait_event(a)
+        with torch.cuda.stream(s2):
+            oh.copy_(dev_out, non_blocking=True)
+    stream.wait_stream(s2)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    gbs = reps * (qh.numel() + oh.numel()) * 8 / (ms * 1e-3) / 1e9
+    del d_in
+    return {"h2d_plus_d2h_GB_s": round(gbs, 1), "Gq_s": round(gbs / 16, 3)}
+
+
 def barrier_sync(ws):
     import torch
     torch.cuda.synchronize()
@@ -403,6 +428,7 @@ def run_ours(args):
     e2e_val = ws * m * e_steps / (e_ms * 1e-3) / 1e9
     torch.cuda.synchronize()
     assert np.array_equal(oh[: 1 << 16].numpy(), out[: 1 << 16].cpu().numpy())
+    copy_bound = host_copy_bound(qh, oh, out, stream)
 
     extra = {}
     if not args.no_extra and rank == 0:
@@ -431,7 +457,8 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": {"value": round(e2e_val, 3), "unit": "Gqueries/s", "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 8 * m,
-                "api": "qr_rank_host: pinned host q/out, chunks of 2^23 on four streams"},
+                "api": "qr_rank_host: pinned host q/out, chunks of 2^23 on four streams",
+                "copy_bound": dict(copy_bound, frac=round(e2e_val / (ws * copy_bound["Gq_s"]), 4))},
         "gpu_launches": args.steps * launches,
         "gpu_launches_e2e_per_step": (m + CHUNK_HOST - 1) // CHUNK_HOST,
         "clocks": clk.summary(),

@@ -380,6 +380,14 @@ def run_ours(args):
             roofline["rank_pass_l2_requests"] = {
                 "requests_per_query": tr["l2_read_requests_per_query"], "G_requests_per_s": round(rq / 1e9, 1),
                 "l2_probe_G_requests_per_s": round(2 * rec_s / 1e9, 1), "frac": round(rq / (2 * rec_s), 4)}
+            if "l2_read_sectors_per_query" in tr:
+                # the same in 32-byte sectors: a request of the key stream or
+                # of a warp's coalesced loads carries several (the probe's
+                # requests carry one each)
+                sq = tr["l2_read_sectors_per_query"] * m / (roofline["passes_ms"]["rank"] * 1e-3)
+                roofline["rank_pass_l2_requests"].update(
+                    sectors_per_query=tr["l2_read_sectors_per_query"], G_sectors_per_s=round(sq / 1e9, 1),
+                    frac_sectors=round(sq / (2 * rec_s), 4))
         # the direct kernels on the same index and queries, for comparison
         capi.qr_set_batch_mode(idx, capi.QR_BATCH_DIRECT)
         ms_d = best_ms(step, stream)

@@ -1271,6 +1271,17 @@ int region_shift(uint64_t n) {
     return shift;
 }
 
+// Regions in use.  Regions of 9-11 MB of index measured best on the full
+// workloads (the lines of the one or two regions in flight stay in L2): an
+// index below about 1.7 GB (181 regions of 9.5 MB, midway between 128 and
+// 256 in log scale) takes a shift one larger, so that its queries fall in
+// the first 128 regions and the rank pass walks only those.  Returns the
+// extra shift (0 or 1).
+int region_extra(const qr_index* idx, int shift) {
+    const uint64_t bytes = line_bytes(idx->layout) * idx->nblocks;
+    return shift < kMaxShift && bytes < 181ull * (19ull << 19) ? 1 : 0;
+}
+
 }  // namespace
 
 bool region_supported(const qr_index* idx, int rank4) {
@@ -1296,8 +1307,11 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
                         int rank4, cudaStream_t s, cudaEvent_t* marks, const DirectLaunch* direct) {
     if (m == 0) return QR_OK;
     if (m >= (1ull << 32)) return fail(QR_EINVAL, "region batch: m must be below 2^32");
-    const int shift = region_shift(idx->n);
-    if (shift > kMaxShift) return fail(QR_EINVAL, "region batch: n must be below 2^37");
+    const int shift0 = region_shift(idx->n);
+    if (shift0 > kMaxShift) return fail(QR_EINVAL, "region batch: n must be below 2^37");
+    const int extra = region_extra(idx, shift0);
+    const int shift = shift0 + extra;
+    const uint64_t used = (uint64_t)(kRegions >> extra);  // regions that hold valid queries
     const int mode = rank4 == 1 ? kModeRank4 : rank4 == 2 ? kModePrefix : kModeRank;
     const uint64_t tiles = (m + kTile - 1) / kTile;
     const uint64_t nseg = (uint64_t)kRegions * tiles;
@@ -1403,7 +1417,11 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRankThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;
-        const uint64_t nsteps = (nseg + 7) / 8;
+        // the segment table is region-major: the runs of the regions in use
+        // come first (out-of-range queries, in the last region, are never
+        // answered)
+        const uint64_t nseg_used = used * tiles;
+        const uint64_t nsteps = (nseg_used + 7) / 8;
         const uint64_t need = (nsteps + kRankThreads / 32 - 1) / (kRankThreads / 32);
         uint64_t grid = (uint64_t)per_sm * sms;
         if (grid > need) grid = need;
@@ -1411,7 +1429,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
         ra.keys = keys;
         ra.res16 = res16;
         ra.seg = seg;
-        ra.nseg = nseg;
+        ra.nseg = nseg_used;
         ra.tiles = tiles;
         ra.lines = idx->lines;
         ra.supers = idx->supers;

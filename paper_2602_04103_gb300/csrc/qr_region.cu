@@ -12,9 +12,11 @@
 // rank_4); only the order in which lines are visited changes, so results are
 // identical.
 //
-// Passes over a batch cut into tiles of 8192 queries and 256 regions
-// (region = q >> shift, the smallest shift that maps [0, n] onto 256; the
-// path needs shift <= 29, i.e. n < 2^37):
+// Passes over a batch cut into tiles of 8192 queries and at most 256 regions
+// (region = q >> shift, at least the smallest shift that maps [0, n] onto 256,
+// and one more where longer regions pay, see region_extra; n = 2^34 bits
+// gives 129 regions of 2^27 positions; the path needs shift <= 29, i.e.
+// n < 2^37):
 //   sort    tile t sorts its queries by region in shared memory (a counting
 //           sort) and writes them back to its own slice of two arrays: a
 //           4-byte key (the position inside its region, its symbol, a bad
@@ -39,7 +41,7 @@
 // and dropped: a scattered 32-byte row, even written by one 32-byte store,
 // made the L2 read ~99 bytes from DRAM per query (ncu, 2^24 queries over
 // 2^30 characters) against the ~27 the pass needs.  The sort and unsort passes read and write whole tiles
-// (coalesced); the rank pass reads runs of ~32 keys per (region, tile).  The
+// (coalesced); the rank pass reads runs of ~64 keys per (region, tile).  The
 // scratch arrays come from a memory pool of the library that keeps them for
 // later calls.  Measured on GB300 and kept out: a count pass plus a global
 // scan to place runs region-major (one more read of the queries, and
@@ -53,6 +55,7 @@
 // tiles; such batches are sent to the direct kernels by the probe (see Gate).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "qr_common.cuh"
@@ -1271,15 +1274,20 @@ int region_shift(uint64_t n) {
     return shift;
 }
 
-// Regions in use.  Regions of 9-11 MB of index measured best on the full
-// workloads (the lines of the one or two regions in flight stay in L2): an
-// index below about 1.7 GB (181 regions of 9.5 MB, midway between 128 and
-// 256 in log scale) takes a shift one larger, so that its queries fall in
-// the first 128 regions and the rank pass walks only those.  Returns the
-// extra shift (0 or 1).
-int region_extra(const qr_index* idx, int shift) {
-    const uint64_t bytes = line_bytes(idx->layout) * idx->nblocks;
-    return shift < kMaxShift && bytes < 181ull * (19ull << 19) ? 1 : 0;
+// Regions in use.  The rank pass keeps about 2.4 regions in flight per 2^28
+// queries (its ~4900 resident warps over the 2^11 steps of 16 runs that one
+// region of a 2^28-query batch holds; fewer queries, proportionally more).
+// Longer regions give longer runs per tile, which every pass pays for per
+// run, until the lines in flight outgrow what the L2 keeps: measured on the
+// full workloads, regions of up to 22 MB of index at 2^28 queries gained and
+// 36 MB lost badly.  So the shift grows by one when the doubled region stays
+// within 24 MiB of index per 2^28 queries of the batch.  Returns the extra
+// shift (0 or 1).
+int region_extra(const qr_index* idx, int shift, uint64_t m) {
+    if (shift >= kMaxShift) return 0;
+    const double bytes = (double)line_bytes(idx->layout) * (double)idx->nblocks;
+    const double doubled = bytes * std::ldexp(1.0, shift + 1) / ((double)idx->n + 1.0);
+    return doubled * std::ldexp(1.0, 28) <= (double)(24u << 20) * (double)m ? 1 : 0;
 }
 
 }  // namespace
@@ -1309,7 +1317,7 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     if (m >= (1ull << 32)) return fail(QR_EINVAL, "region batch: m must be below 2^32");
     const int shift0 = region_shift(idx->n);
     if (shift0 > kMaxShift) return fail(QR_EINVAL, "region batch: n must be below 2^37");
-    const int extra = region_extra(idx, shift0);
+    const int extra = region_extra(idx, shift0, m);
     const int shift = shift0 + extra;
     const uint64_t used = (uint64_t)(kRegions >> extra);  // regions that hold valid queries
     const int mode = rank4 == 1 ? kModeRank4 : rank4 == 2 ? kModePrefix : kModeRank;

@@ -556,8 +556,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
 // because results of one region exceed their base by less than 2^shift <=
 // 2^29.  The region of each sorted place comes from the tile's segment
 // entries: every warp writes the region number over the places of its
-// regions' runs (reg8), then every thread restores its results and puts
-// them at their index inside the tile, and the tile is written out in order.
+// regions' runs (reg8; only the first nreg regions, the ones that can hold a
+// valid query: the places of out-of-range queries keep a stale region, which
+// their UINT64_MAX result ignores), then every thread restores its results
+// and puts them at their index inside the tile, and the tile is written out
+// in order.
 constexpr int kUnsortThreads = 512;
 constexpr int kUnsortPer = kTile / kUnsortThreads;
 constexpr int kUnsortChunks = kUnsortPer / 4;  // chunks of four consecutive sorted places per thread
@@ -568,8 +571,8 @@ __global__ void __launch_bounds__(kUnsortThreads, 2) region_unsort(const uint32_
                                                                    const uint16_t* __restrict__ idxs,
                                                                    const uint32_t* __restrict__ segt,
                                                                    const uint64_t* __restrict__ bases, uint64_t m,
-                                                                   uint64_t tiles, uint64_t* __restrict__ out,
-                                                                   Gate gate) {
+                                                                   uint64_t tiles, uint32_t nreg,
+                                                                   uint64_t* __restrict__ out, Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* res = (uint64_t*)smem;                        // the tile's results in query order
     uint64_t* btab = res + kTile;                           // bases[kRegions * 4]
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(kUnsortThreads, 2) region_unsort(const uint32_
             if (tn < tiles) e_next = __ldg(segt + tn * kRegions + threadIdx.x);
         }
         __syncthreads();
-        for (uint32_t r = warp; r < kRegions; r += kUnsortThreads / 32) {
+        for (uint32_t r = warp; r < nreg; r += kUnsortThreads / 32) {
             const uint32_t e = tseg[r];
             const uint32_t st = e & 0xFFFFu, ln = e >> 16;
             for (uint32_t k = lane; k < ln; k += 32) reg8[st + k] = (uint8_t)r;
@@ -662,8 +665,9 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
                                                                      const uint16_t* __restrict__ idxs,
                                                                      const uint32_t* __restrict__ segt,
                                                                      const uint64_t* __restrict__ bases, uint64_t m,
-                                                                     uint64_t tiles, uint64_t* __restrict__ out4,
-                                                                     int out4_32, Gate gate) {
+                                                                     uint64_t tiles, uint32_t nreg,
+                                                                     uint64_t* __restrict__ out4, int out4_32,
+                                                                     Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4* rel = (uint4*)smem;                               // the tile's low 32 bits of the counts, query order
     uint64_t* btab = (uint64_t*)(rel + kTile);               // bases[kRegions * 4]
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
             if (tn < tiles) e_next = __ldg(segt + tn * kRegions + threadIdx.x);
         }
         __syncthreads();
-        for (uint32_t r = warp; r < kRegions; r += kUnsort4Threads / 32) {
+        for (uint32_t r = warp; r < nreg; r += kUnsort4Threads / 32) {
             const uint32_t e = tseg[r];
             const uint32_t st = e & 0xFFFFu, ln = e >> 16;
             for (uint32_t k = lane; k < ln; k += 32) reg8[st + k] = (uint8_t)r;
@@ -1319,7 +1323,9 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     if (shift0 > kMaxShift) return fail(QR_EINVAL, "region batch: n must be below 2^37");
     const int extra = region_extra(idx, shift0, m);
     const int shift = shift0 + extra;
-    const uint64_t used = (uint64_t)(kRegions >> extra);  // regions that hold valid queries
+    // regions that can hold valid queries (q <= n); out-of-range ones fall in the
+    // last region and are never answered
+    const uint64_t used = (idx->n >> shift) + 1 < kRegions ? (idx->n >> shift) + 1 : kRegions;
     const int mode = rank4 == 1 ? kModeRank4 : rank4 == 2 ? kModePrefix : kModeRank;
     const uint64_t tiles = (m + kTile - 1) / kTile;
     const uint64_t nseg = (uint64_t)kRegions * tiles;
@@ -1452,15 +1458,15 @@ int launch_rank_regions(const qr_index* idx, const uint64_t* q, const uint8_t* c
     if (!rc && marks) cudaEventRecord(marks[2], s);
     if (!rc && mode != kModeRank4) {
         const uint64_t grid = tiles < (uint64_t)sms * 2 ? tiles : (uint64_t)sms * 2;
-        region_unsort<<<(unsigned)grid, kUnsortThreads, kUnsortSmem, s>>>(keys, idxs, segt, bases, m, tiles, out,
-                                                                          gate);
+        region_unsort<<<(unsigned)grid, kUnsortThreads, kUnsortSmem, s>>>(keys, idxs, segt, bases, m, tiles,
+                                                                          (uint32_t)used, out, gate);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort");
     }
     if (!rc && mode == kModeRank4) {
         const uint64_t grid = tiles < (uint64_t)sms ? tiles : (uint64_t)sms;
         region_unsort4<<<(unsigned)grid, kUnsort4Threads, kUnsort4Smem, s>>>(
-            res16, idxs, segt, bases, m, tiles, out, ((uintptr_t)out & 31) == 0, gate);
+            res16, idxs, segt, bases, m, tiles, (uint32_t)used, out, ((uintptr_t)out & 31) == 0, gate);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "region_unsort4");
     }

@@ -434,22 +434,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         const bool pipe = len == kTile;
         uint32_t rr[kTmaPer], rk[kTmaPer];  // (pipe) region of each item and its rank inside the region
         if (pipe) {
-            bool u[kTmaPer];
-            uint32_t v[kTmaPer];
 #pragma unroll
             for (int k = 0; k < kTmaPer; k++) rr[k] = region_of(raw[threadIdx.x + k * kTmaThreads], shift);
+            // a warp whose items all share one region (a clustered tile) takes
+            // 32 places per atomic; otherwise every item takes its own.  One
+            // vote for all the items keeps the shuffle and vote traffic off the
+            // shared-memory pipe this pass is bound by.
+            const uint32_t r0 = __shfl_sync(kAll, rr[0], 0);
+            bool same = true;
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) u[k] = __all_sync(kAll, rr[k] == __shfl_sync(kAll, rr[k], 0));
-            // a warp whose 32 items share a region takes 32 places with one atomic
+            for (int k = 0; k < kTmaPer; k++) same &= rr[k] == r0;
+            if (__all_sync(kAll, same)) {
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) {
-                v[k] = 0;
-                if (!u[k] || lane == 0) v[k] = atomicAdd(&h[rr[k]], u[k] ? 32u : 1u);
-            }
+                for (int k = 0; k < kTmaPer; k++) {
+                    uint32_t v = 0;
+                    if (lane == 0) v = atomicAdd(&h[r0], 32u);
+                    rk[k] = __shfl_sync(kAll, v, 0) + (uint32_t)lane;
+                }
+            } else {
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) {
-                const uint32_t w = __shfl_sync(kAll, v[k], 0);
-                rk[k] = u[k] ? w + (uint32_t)lane : v[k];
+                for (int k = 0; k < kTmaPer; k++) rk[k] = atomicAdd(&h[rr[k]], 1u);
             }
         }
         if (!pipe) {

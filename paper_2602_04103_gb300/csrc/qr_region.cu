@@ -674,12 +674,16 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
                                                                      Gate gate) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4* rel = (uint4*)smem;                               // the tile's low 32 bits of the counts, query order
-    uint64_t* btab = (uint64_t*)(rel + kTile);               // bases[kRegions * 4]
+    uint64_t* btab = (uint64_t*)(rel + kTile);               // bases[4][kRegions]
     uint16_t* qreg = (uint16_t*)(btab + kRegions * kBaseSyms);  // region of every query (kRowBad: bad)
     uint32_t* tseg = (uint32_t*)(qreg + kTile);              // the tile's segment entries
     uint8_t* reg8 = (uint8_t*)(tseg + kRegions);             // region of every sorted place
     if (!regions_chosen(gate)) return;
-    for (uint32_t i = threadIdx.x; i < kRegions * kBaseSyms; i += blockDim.x) btab[i] = bases[i];
+    // bases by symbol, then region: a row's four lookups below then spread
+    // over the banks (region-major rows of 32 bytes put every region of a
+    // warp on one of four bank groups for each symbol)
+    for (uint32_t i = threadIdx.x; i < kRegions * kBaseSyms; i += blockDim.x)
+        btab[(i % kBaseSyms) * kRegions + i / kBaseSyms] = bases[i];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t e_next = 0;
     if (threadIdx.x < kRegions && blockIdx.x < tiles) e_next = __ldg(segt + blockIdx.x * kRegions + threadIdx.x);
@@ -729,7 +733,7 @@ __global__ void __launch_bounds__(kUnsort4Threads, 1) region_unsort4(const uint3
                     const uint32_t lo[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
-                        const uint64_t b = btab[r * kBaseSyms + c];
+                        const uint64_t b = btab[c * kRegions + r];
                         v[c] = b + (uint32_t)(lo[c] - (uint32_t)b);
                     }
                 }

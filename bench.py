@@ -428,9 +428,13 @@ def run_ours(args):
     def e2e_step():
         capi.qr_rank_host(idx, qh, 1, oh)
 
-    e2e_step()
+    # the first calls on freshly pinned buffers run 4-8x slower on GB300 (87,
+    # 112, 53 ms against a steady 13.4 ms, measured): the warm-up takes the
+    # same W steps as the kernel timing, at least three
+    for _ in range(max(3, args.warmup)):
+        e2e_step()
     barrier_sync(ws)
-    e_steps = max(1, min(args.steps, 3))
+    e_steps = max(1, min(args.steps, 5))
     e_ms, _ = time_launches(e2e_step, e_steps, stream)
     e_ms = max_over_ranks(e_ms, ws)
     e2e_val = ws * m * e_steps / (e_ms * 1e-3) / 1e9

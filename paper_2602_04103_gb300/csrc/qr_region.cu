@@ -432,10 +432,18 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         if (s_abort) break;
         if (full(t) && threadIdx.x != 0) mbar_try_wait(&bar[b], (j >> 1) & 1);  // (completed: acquire the data)
         const bool pipe = len == kTile;
-        uint32_t rr[kTmaPer], rk[kTmaPer];  // (pipe) region of each item and its rank inside the region
+        // (pipe) region of each item | its rank inside the region << 8; with one
+        // symbol for the batch also its position inside the region |
+        // out-of-range bit, so that the scatter reads no query again (with
+        // per-query symbols the extra registers cost more than the read)
+        uint32_t rr[kTmaPer], wq[kTmaPer];
         if (pipe) {
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) rr[k] = region_of(raw[threadIdx.x + k * kTmaThreads], shift);
+            for (int k = 0; k < kTmaPer; k++) {
+                const uint64_t x = raw[threadIdx.x + k * kTmaThreads];
+                rr[k] = region_of(x, shift);
+                if (!VEC) wq[k] = x > n ? kKeyBad : (uint32_t)(x & ((1ull << shift) - 1));
+            }
             // a warp whose items all share one region (a clustered tile) takes
             // 32 places per atomic; otherwise every item takes its own.  One
             // vote for all the items keeps the shuffle and vote traffic off the
@@ -449,11 +457,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
                 for (int k = 0; k < kTmaPer; k++) {
                     uint32_t v = 0;
                     if (lane == 0) v = atomicAdd(&h[r0], 32u);
-                    rk[k] = __shfl_sync(kAll, v, 0) + (uint32_t)lane;
+                    rr[k] |= (__shfl_sync(kAll, v, 0) + (uint32_t)lane) << 8;
                 }
             } else {
 #pragma unroll
-                for (int k = 0; k < kTmaPer; k++) rk[k] = atomicAdd(&h[rr[k]], 1u);
+                for (int k = 0; k < kTmaPer; k++) rr[k] |= atomicAdd(&h[rr[k]], 1u) << 8;
             }
         }
         if (!pipe) {
@@ -488,20 +496,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1) region_sort_tma(const uint64_t
         __syncthreads();
         if (pipe) {
             uint32_t pos[kTmaPer], cc[kTmaPer];
-            uint64_t x[kTmaPer];
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) pos[k] = h[rr[k]] + rk[k];
+            for (int k = 0; k < kTmaPer; k++) pos[k] = h[rr[k] & 0xFFu] + (rr[k] >> 8);
 #pragma unroll
-            for (int k = 0; k < kTmaPer; k++) {
-                x[k] = raw[threadIdx.x + k * kTmaThreads];
-                cc[k] = VEC ? (uint32_t)csym[threadIdx.x + k * kTmaThreads] : c0;
-            }
+            for (int k = 0; k < kTmaPer; k++) cc[k] = VEC ? (uint32_t)csym[threadIdx.x + k * kTmaThreads] : c0;
 #pragma unroll
             for (int k = 0; k < kTmaPer; k++) {
                 const uint32_t i = threadIdx.x + k * kTmaThreads;
-                const bool range_bad = x[k] > n, sym_bad = cc[k] >= sigma;
+                bool range_bad;
+                uint32_t w;
+                if (VEC) {
+                    const uint64_t x = raw[i];
+                    range_bad = x > n;
+                    w = (uint32_t)(x & ((1ull << shift) - 1));
+                } else {
+                    range_bad = wq[k] & kKeyBad;
+                    w = wq[k];
+                }
+                const bool sym_bad = cc[k] >= sigma;
                 flags |= (range_bad ? kStatusRange : 0u) | (sym_bad ? kStatusBadSym : 0u);
-                key_st[pos[k]] = make_key(x[k], cc[k], range_bad || sym_bad, shift);
+                key_st[pos[k]] = range_bad || sym_bad ? kKeyBad : w | (cc[k] << kKeySymShift);
                 idx_st[pos[k]] = make_idx(i, cc[k], range_bad || sym_bad);
             }
         }

@@ -27,7 +27,9 @@
 //           every region, for every symbol (1024 queries);
 //   rank    warps take steps of 16 segments of the table, in table order,
 //           from a device work queue, i.e. region after region, so the lines
-//           of the one or two regions in flight stay in L2; rank and
+//           of the two or three regions in flight stay in L2 (only the
+//           regions that can hold a valid query: out-of-range queries sit in
+//           the last region and are never answered); rank and
 //           prefix_rank replace each key by the low 32 bits of its result,
 //           rank_4 writes the low 32 bits of its four counts (16 bytes) at
 //           the key's place in an array of its own;
@@ -40,8 +42,9 @@
 // per batch.  Writing rank_4's rows straight from the rank pass was measured
 // and dropped: a scattered 32-byte row, even written by one 32-byte store,
 // made the L2 read ~99 bytes from DRAM per query (ncu, 2^24 queries over
-// 2^30 characters) against the ~27 the pass needs.  The sort and unsort passes read and write whole tiles
-// (coalesced); the rank pass reads runs of ~64 keys per (region, tile).  The
+// 2^30 characters) against the ~27 the pass needs.  The sort and unsort
+// passes read and write whole tiles (coalesced); the rank pass reads runs of
+// ~64 keys per (region, tile).  The
 // scratch arrays come from a memory pool of the library that keeps them for
 // later calls.  Measured on GB300 and kept out: a count pass plus a global
 // scan to place runs region-major (one more read of the queries, and

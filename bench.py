@@ -753,13 +753,13 @@ def run_fm(args, stream, part="all"):
                                       "ms": round(ms_b, 3)},
            "qfm_speedup_persistent_vs_stepwise": round(ms_s / ms_p, 2),
            "qfm_build_s": round(t_build, 3), "qfm_index_bytes": info["bytes_rank"] + info["bytes_table"]}
-    work = ROOT / "tests" / "golden" / "fm_work_config4.json"
+    work = ROOT / "tests" / "golden" / "fm_work_2p26_1e7.json"
     if work.exists() and args.fm_log_n == 26 and args.fm_m == 10_000_000:
         w = json.loads(work.read_text())
         steps = w["mean_lf_steps"] * m
         res["qfm_count_persistent"]["lf_steps_per_s"] = round(steps / (ms_p * 1e-3))
         res["qfm_count_persistent"]["rank_queries_per_s"] = round(2 * steps / (ms_p * 1e-3))
-        res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_config4.json)"
+        res["qfm_lf_steps_source"] = "oracle mean over the first 10^6 patterns (tests/golden/fm_work_2p26_1e7.json)"
         res["qfm_count_persistent"]["roofline"] = fm_roofline(steps / (ms_p * 1e-3),
                                                               info["bytes_rank"] + info["bytes_table"], stream)
     log(f"[bench] qfm: persistent {m / ms_p / 1e3:.1f} M/s, stepwise {m / ms_s / 1e3:.1f} M/s")

@@ -1,14 +1,14 @@
 """Write the expected values of the full-size QuadFm parity tests, computed by
 the oracle only (count-only FM-index, QuadRank paper App. D):
 
-fm_full_config4.json -- the count workload: 2^26-char text with 20% planted
+fm_full_2p26_1e7.json -- the count workload: 2^26-char text with 20% planted
   repeats, 10^7 patterns of length 16..150.
   * sha256 of the suffix array of T$ (textbook comparison sort, as uint32),
   * sha256 of all 10^7 counts (suffix-array interval sizes, as uint64),
   * sha256 of the counts of the reverse complements of 10^5 sampled patterns
     (both-strand counting, App. D counts each read in both directions),
   * plain sums and a few leading values, for a readable diff.
-fm_serving_config5.json -- the serving workload: 2^28-char text, the first
+fm_serving_2p28.json -- the serving workload: 2^28-char text, the first
   256 requests of the trace; brute-force counts (direct comparison at every
   text position) of 2000 sampled patterns of those requests.
 
@@ -60,7 +60,7 @@ def threaded(fn, m: int, threads: int) -> np.ndarray:
     return np.concatenate(parts) if parts else np.zeros(0, np.uint64)
 
 
-def config4(threads: int) -> dict:
+def count_workload(threads: int) -> dict:
     t0 = time.time()
     text, pats, off = workloads.fm_inputs()
     m = off.size - 1
@@ -96,7 +96,7 @@ def config4(threads: int) -> dict:
     }
 
 
-def config5(threads: int) -> dict:
+def serving_workload(threads: int) -> dict:
     t0 = time.time()
     text, pats, off, first = workloads.serving_inputs(SERVE_REQUESTS, 28)
     npat = int(first[-1])
@@ -117,11 +117,11 @@ def config5(threads: int) -> dict:
 
 def main():
     threads = os.cpu_count() or 1
-    which = sys.argv[1:] or ["4", "5"]
+    which = sys.argv[1:] or ["count", "serving"]
     for w in which:
-        d = config4(threads) if w == "4" else config5(threads)
+        d = count_workload(threads) if w == "count" else serving_workload(threads)
         d["written_by"] = "tests/golden/make_fm_full.py (oracle only)"
-        name = "fm_full_config4.json" if w == "4" else "fm_serving_config5.json"
+        name = "fm_full_2p26_1e7.json" if w == "count" else "fm_serving_2p28.json"
         (HERE / name).write_text(json.dumps(d, indent=1) + "\n")
         print(name, json.dumps({k: v for k, v in d.items() if k not in ("sample_ids", "sample_counts")}), flush=True)
 

@@ -1,4 +1,4 @@
-"""Write fm_work_config4.json: LF-step statistics of the QuadFm count workload
+"""Write fm_work_2p26_1e7.json: LF-step statistics of the QuadFm count workload
 (2^26-char text with planted repeats, patterns of length 16..150, half
 sampled with 1% substitutions), computed by the oracle only.
 
@@ -47,7 +47,7 @@ def main():
         "seconds": round(time.time() - t0, 1),
         "written_by": "tests/golden/make_fm_work.py (oracle only)",
     }
-    (Path(__file__).parent / "fm_work_config4.json").write_text(json.dumps(out, indent=1) + "\n")
+    (Path(__file__).parent / "fm_work_2p26_1e7.json").write_text(json.dumps(out, indent=1) + "\n")
     print(json.dumps(out, indent=1))
 
 

@@ -9,13 +9,13 @@ sample of outputs is checked against the oracle bit-exactly.
   the direct kernels agree on every output of both.
 * QuadFm count (2^26-char text, 10^7 patterns): the GPU suffix array row by
   row, all 10^7 counts and the reverse-complement counts of 10^5 sampled
-  patterns against the oracle (tests/golden/fm_full_config4.json holds
+  patterns against the oracle (tests/golden/fm_full_2p26_1e7.json holds
   sha256 digests of the oracle's arrays, written by make_fm_full.py, which
   calls only the oracle; on a mismatch the oracle is run here to name the
   first differing row), plus the per-step baseline on every pattern.
 * QuadFm serving (2^28-char text): 256 requests (489,363 patterns) served by
   the continuous-batching server; 2000 sampled counts against the oracle's
-  brute-force counts (tests/golden/fm_serving_config5.json).
+  brute-force counts (tests/golden/fm_serving_2p28.json).
 """
 import hashlib
 import json
@@ -117,7 +117,7 @@ def first_diff(got: np.ndarray, want: np.ndarray):
 def test_fm_full_size():
     import torch
     from paper_2602_04103_gb300 import capi
-    g = json.loads((GOLDEN / "fm_full_config4.json").read_text())
+    g = json.loads((GOLDEN / "fm_full_2p26_1e7.json").read_text())
     text, pats, off = workloads.fm_inputs()
     m = off.size - 1
     assert (text.size, m) == (g["n"], g["patterns"])
@@ -171,7 +171,7 @@ def test_fm_serving_full_size():
     equals a plain qfm_count over the whole trace."""
     import torch
     from paper_2602_04103_gb300 import capi
-    g = json.loads((GOLDEN / "fm_serving_config5.json").read_text())
+    g = json.loads((GOLDEN / "fm_serving_2p28.json").read_text())
     text, pats, off, first = workloads.serving_inputs(g["requests"], 28)
     npat = int(first[-1])
     assert (text.size, npat) == (g["n"], g["patterns"])

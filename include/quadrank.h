@@ -283,11 +283,12 @@ int qr_build_tuned(const uint64_t* text, uint64_t n, int sigma, int text_on_devi
  * modes).  On GB300 a random 64-byte line costs a whole 128-byte DRAM fill,
  * so a batch that holds several queries per line of the index is answered
  * faster by moving the queries instead: the batch is cut into tiles of 8192
- * queries, every tile is sorted by text region in shared memory (256
- * regions, region = q >> shift), the sorted runs are answered region after
- * region (the lines of the region in flight stay in L2, each line is read
- * from DRAM about once per batch) and every tile's results are put back in
- * query order.  Every result is computed by the same query arithmetic from
+ * queries, every tile is sorted by text region in shared memory (at most
+ * 256 regions, region = q >> shift; the shift grows by one for an index that
+ * is small against the batch, so that regions hold more queries), the sorted
+ * runs are answered region after region (the lines of the regions in flight
+ * stay in L2, each line is read from DRAM about once per batch) and every
+ * tile's results are put back in query order.  Every result is computed by the same query arithmetic from
  * the same line, so the outputs are those of the direct kernels, bit for
  * bit.  This is this library's own addition; the paper has no counterpart.
  *   QR_BATCH_AUTO     (default) region batching when the index is not

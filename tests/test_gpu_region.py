@@ -108,6 +108,36 @@ def test_every_rank_pass_variant(variant, tiles):
             idx.free()
 
 
+@pytest.mark.parametrize("layout", DNA_LAYOUTS)
+def test_region_length_rule_both_sides(layout):
+    """The region length grows by one doubling when the doubled region holds
+    at most 24 MiB of index per 2^28 queries of the batch: over this ~96 KB
+    sigma-4 index a batch of 4096 queries keeps the plain shift and one of
+    2^16 takes the doubled one.  Both give the oracle's results (rank with
+    per-query symbols, rank_4), bad positions and symbols included."""
+    import torch
+    from paper_2602_04103_gb300 import capi
+    n = 5 * S4 + 17
+    words = synth.dna_uniform(synth.base_seed(80), n)
+    idx = regions_index(words, n, 4, layout)
+    for m in (4096, 1 << 16):
+        q = synth.queries(synth.base_seed(81) + m, n, m)
+        q[::733] = n + 1
+        cv = synth.symbols(synth.base_seed(82) + m, m, 4)
+        cv[::977] = 9
+        check(idx, words, n, 4, q, cv, status=capi.QR_ERANGE | capi.QR_EBADSYM)
+        ok = q <= n
+        want4, rc = oracle.rank4(words, n, q[ok])
+        dq = dev_u64(q)
+        out4 = torch.empty((m, 4), dtype=torch.int64, device="cuda")
+        capi.qr_rank4(idx, dq, out4)
+        got4 = host_u64(out4).reshape(-1, 4)
+        assert rc == 0 and np.array_equal(got4[ok], want4), m
+        assert (got4[~ok] == U64MAX).all()
+        assert capi.qr_status(idx) == capi.QR_ERANGE
+    idx.free()
+
+
 def test_region_tuning_range():
     from paper_2602_04103_gb300 import capi
     idx = build(synth.bits(1, 1000, 0.5), 1000, 2, 1)
